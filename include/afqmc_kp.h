@@ -1,0 +1,214 @@
+/*
+ * afqmc_kp.h -- C ABI of the k-point phaseless AFQMC walker step on one GPU.
+ *
+ * The library implements the data-parallel hot path of phaseless auxiliary-field
+ * quantum Monte Carlo with momentum-blocked Cholesky vectors (Malone, Zhang and
+ * Morales, "Accelerating AFQMC simulations of solids with GPUs",
+ * arXiv:2003.09468): one walker step over a batch of Slater-determinant walkers
+ * (Green's function, force bias, vHS, Taylor exponential, one-body halves,
+ * hybrid weight, optional re-orthonormalisation) and the mixed local energy with
+ * its adjoint.  Every step runs in the library's own CUDA kernels (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im) pairs of IEEE doubles ("c128");
+ *   arrays are row-major (C order), with the shapes stated per argument.
+ * - Symbols: Nk = kgrid[0]*kgrid[1]*kgrid[2] k-points (Gamma-centred grid,
+ *   k index in C order over the three axes), M orbitals per k, n = nocc occupied
+ *   orbitals per k per spin, NM = Nk*M, N = Nk*n, G = nchol Cholesky vectors
+ *   per momentum transfer Q, W = nwalkers.  k - Q is taken modulo the grid.
+ * - Array pointers passed to calls other than afqmc_kp_create are DEVICE pointers
+ *   on the current device, owned by the caller, and must stay valid until the
+ *   work enqueued on `stream` has finished.  `stream` is a cudaStream_t (NULL
+ *   means the legacy default stream).  Calls are asynchronous: they enqueue
+ *   kernels and return without synchronising, except where stated.
+ * - After afqmc_kp_create returns, no call allocates device memory, so every
+ *   call may be captured in a CUDA graph.
+ * - No C++ exception crosses the ABI.  Invalid arguments are rejected with
+ *   AFQMC_ERR_INVALID before any work is enqueued.  A failed kernel launch
+ *   returns AFQMC_ERR_CUDA; an asynchronous fault surfaces as AFQMC_ERR_CUDA from
+ *   a later call or from afqmc_kp_last_error.
+ * - A handle is not thread safe: calls on one handle must not overlap in time
+ *   (they share its workspace), whatever stream they use.
+ */
+#ifndef AFQMC_KP_H
+#define AFQMC_KP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AFQMC_OK = 0,
+  AFQMC_ERR_INVALID = 1,     /* bad argument: NULL pointer, size out of range   */
+  AFQMC_ERR_OOM = 2,         /* device allocation failed in afqmc_kp_create     */
+  AFQMC_ERR_CUDA = 3,        /* a CUDA call or kernel launch failed             */
+  AFQMC_ERR_SINGULAR = 4,    /* at least one walker had a singular overlap      */
+  AFQMC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
+  AFQMC_ERR_UNSUPPORTED = 6  /* valid request this build does not implement     */
+} afqmc_status;
+
+typedef enum {
+  /* Every contraction in complex128 on the FP64 pipes. */
+  AFQMC_FP64 = 0,
+  /* L-contractions (force bias, vHS, Taylor products, exchange) on the tensor
+   * cores with FP32 accumulation; overlap, inverse, log-det, weights, QR and the
+   * energy sums stay FP64. */
+  AFQMC_MIXED = 1
+} afqmc_precision;
+
+/* Sizes and parameters of one system; copied by afqmc_kp_create. */
+typedef struct {
+  int kgrid[3];        /* Monkhorst-Pack grid, each >= 1                          */
+  int M;               /* orbitals per k-point, 1..128                            */
+  int nocc;            /* occupied orbitals per k-point per spin, 1..M            */
+  int nchol;           /* Cholesky vectors per Q, >= 1                            */
+  int nwalkers;        /* walkers per call, >= 1                                  */
+  double dt;           /* imaginary time step, > 0                                */
+  int taylor_order;    /* terms of the exp(V) series beyond the identity, 1..16   */
+  afqmc_precision prec;
+  size_t workspace_cap_bytes; /* 0 = no cap; else create fails with OOM above it */
+} afqmc_kp_desc;
+
+typedef struct afqmc_kp* afqmc_kp_t;
+
+/*
+ * afqmc_kp_create -- upload a Hamiltonian and trial, precompute static data.
+ *
+ * Paper: Sec. 2.3, Eqs. kp_h1 and kp_h2 define h[k] and L[Q,k]; the half-rotated
+ * Cholesky vectors LH[Q,k,g,a,r] = sum_p conj(A[k,p,a]) L[Q,k,g,p,r] are formed
+ * once (Sec. 2.3, below Eq. kp_vhs); the one-body propagator exp(-dt/2 H1') with
+ * H1' = h + v0 and v0[k] = -1/2 sum_{Q,g} L[Q,k,g] L[Q,k,g]^dagger (Sec. 2.1,
+ * below Eq. hsq, and Eq. propagator) is formed by FP64 kernels.
+ *
+ *   desc   sizes and parameters (host pointer, copied).
+ *   L      HOST or DEVICE c128 [Nk][Nk][G][M][M]: L[Q][k][g][p][r], p at k,
+ *          r at k - Q.  Must satisfy L[-Q][k-Q][g] = L[Q][k][g]^dagger (Sec. 2.3);
+ *          the library uses both members of each pair as given.
+ *   h1     HOST or DEVICE c128 [Nk][M][M]: Hermitian one-body blocks h[k].
+ *   trial  HOST or DEVICE c128 [Nk][M][n]: occupied trial orbitals A[k]
+ *          (block diagonal in k, the same for both spins).
+ *   stream stream used for the set-up kernels; create synchronises it before
+ *          returning, so the caller's buffers may be freed afterwards.
+ *   out    receives the handle; untouched on failure.
+ * The library copies everything it needs and owns all its device memory.
+ * Returns AFQMC_ERR_INVALID for bad sizes, AFQMC_ERR_OOM if the workspace does
+ * not fit (or exceeds workspace_cap_bytes), AFQMC_ERR_UNSUPPORTED for a
+ * precision mode this build lacks.
+ */
+afqmc_status afqmc_kp_create(const afqmc_kp_desc* desc, const void* L, const void* h1,
+                             const void* trial, void* stream, afqmc_kp_t* out);
+
+/* Frees every device buffer of the handle (synchronises the device first). */
+afqmc_status afqmc_kp_destroy(afqmc_kp_t h);
+
+/*
+ * afqmc_kp_set_one_body -- replace h[k] (e.g. h + lambda V1 for a response).
+ * Recomputes A[k]^dagger h[k] (energy) and exp(-dt/2 (h + v0)) (propagation).
+ *   h1  DEVICE c128 [Nk][M][M].
+ */
+afqmc_status afqmc_kp_set_one_body(afqmc_kp_t h, const void* h1, void* stream);
+
+/*
+ * afqmc_kp_force_bias -- xbar = -sqrt(dt) <psi_T|v|phi>/<psi_T|phi>.
+ *
+ * Paper: Sec. 2.1 (force-bias shift), Sec. 2.2 Eq. fb, Sec. 2.3 Eq. kp_vbias.
+ * With X[w,Q,g] = sum_s sum_k sum_{a,r} LH[Q,k,g,a,r] Gh_s[(k,a),(k-Q,r)] and the
+ * half-rotated Green's function Gh_s = (phi_s (A^dagger phi_s)^-1)^T (Eq. gfhrot):
+ *   xbar[w][0][Q][g] = -sqrt(dt) * i (X[Q,g] + X[-Q,g]) / 2     ("+" fields)
+ *   xbar[w][1][Q][g] = -sqrt(dt) * -(X[Q,g] - X[-Q,g]) / 2      ("-" fields)
+ *   phi   DEVICE c128 [W][2][NM][N] walker orbitals, row (k,p), column (k',a).
+ *   xbar  DEVICE c128 [W][2][Nk][G] output.
+ */
+afqmc_status afqmc_kp_force_bias(afqmc_kp_t h, const void* phi, void* xbar, void* stream);
+
+/*
+ * afqmc_kp_propagate -- one phaseless "hybrid" step of every walker.
+ *
+ * Paper: Sec. 2.1 Eqs. propagator and iterate_imp, the importance function I,
+ * the hybrid weight and the phase; Sec. 2.2 Eq. vhs and the truncated Taylor
+ * series; Sec. 2.3 Eq. kp_vhs.  Per walker:
+ *   xbar from phi (as afqmc_kp_force_bias);
+ *   V = sqrt(dt) sum_{Q,g} L^{Q g} y[Q,g],
+ *       y = (i xt+_Q - xt-_Q)/2 + (i xt+_{-Q} + xt-_{-Q})/2,  xt = x - xbar;
+ *   phi <- E * (sum_{j=0}^{taylor_order} V^j / j!) * E * phi,  E = exp(-dt/2 H1');
+ *   R = prod_s det(A^dagger phi_s') / det(A^dagger phi_s), dtheta = arg R,
+ *   w <- w * |R exp(sum_f x_f xbar_f - xbar_f^2 / 2)| * max(0, cos dtheta);
+ *   if do_qr: phi_s <- Q of the QR factorisation with diag(R) real positive.
+ *   phi     DEVICE c128 [W][2][NM][N], updated in place.
+ *   x       DEVICE double [W][2][Nk][G] auxiliary fields (+ then -).
+ *   weight  DEVICE double [W], updated in place.
+ *   logdet  DEVICE c128 [W][2] output: log det(A^dagger phi_s) of the new
+ *           walker (after QR if done), or NULL.
+ *   do_qr   0 or 1.
+ * A walker whose overlap matrix is singular gets weight 0 and a zero Green's
+ * function; it is counted in the sticky flags read by afqmc_kp_last_error.
+ */
+afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double* weight,
+                                void* logdet, int do_qr, void* stream);
+
+/*
+ * afqmc_kp_orthonormalise -- phi_s <- Q factor of phi_s with diag(R) > 0
+ * (the walker orthogonalisation done once per block, Sec. 3.1).
+ *   phi     DEVICE c128 [W][2][NM][N], in place.
+ *   logdet  DEVICE c128 [W][2] output (log det(A^dagger phi_s) after), or NULL.
+ */
+afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void* stream);
+
+/*
+ * afqmc_kp_local_energy -- mixed local energy of every walker.
+ *
+ * Paper: Sec. 2.2 Eq. local_energy (E1 + E_C + E_X with X, X-bar, T, T-bar),
+ * Sec. 2.3 Eq. kp_el, Sec. 3.2 energy steps 1-3.
+ *   E1 = sum_s sum_k sum_{a,q} (A[k]^dagger h[k])[a,q] Gh_s[(k,a),(k,q)]
+ *   EC = 1/2 sum_{Q,g} X[Q,g] X[-Q,g]
+ *   EX = -1/2 sum_s sum_{Q,k,k'} sum_{g,a,b} T1[g,a,b] T2[g,b,a],
+ *        T1 = sum_r LH[Q,k,g,a,r] Gh_s[(k'-Q,b),(k-Q,r)],
+ *        T2 = sum_s LH[-Q,k'-Q,g,b,s] Gh_s[(k,a),(k',s)].
+ *   phi   DEVICE c128 [W][2][NM][N].
+ *   eloc  DEVICE c128 [W][3] output: (E1, EC, EX) per walker.
+ */
+afqmc_status afqmc_kp_local_energy(afqmc_kp_t h, const void* phi, void* eloc, void* stream);
+
+/*
+ * afqmc_kp_local_energy_backward -- adjoint of afqmc_kp_local_energy.
+ *
+ * Derived from Sec. 2.3 Eq. kp_el (the paper has no adjoint).  E is holomorphic
+ * in phi; with upstream weights g[w][part] = dLoss/dconj(E_part) (PyTorch's
+ * convention for complex tensors) the outputs are
+ *   grad_phi[w] = sum_part g[w][part] * conj(dE_part[w] / dphi[w])
+ *   grad_h1[k]  = sum_w g[w][0] * conj(dE1[w] / dh[k])
+ *   phi       DEVICE c128 [W][2][NM][N].
+ *   grad_e    DEVICE c128 [W][3].
+ *   grad_phi  DEVICE c128 [W][2][NM][N] output, or NULL to skip.
+ *   grad_h1   DEVICE c128 [Nk][M][M] output, or NULL to skip.
+ * Exchange intermediates T2 are recomputed, never stored.
+ */
+afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const void* grad_e,
+                                            void* grad_phi, void* grad_h1, void* stream);
+
+/*
+ * afqmc_kp_last_error -- synchronise `stream`, read and clear the handle's
+ * sticky device flags.  Returns AFQMC_ERR_SINGULAR if any walker had a singular
+ * overlap since the last call (their count goes to *n_singular if non-NULL),
+ * AFQMC_ERR_TIMEOUT if a bounded device wait gave up, AFQMC_ERR_CUDA on an
+ * asynchronous CUDA fault, else AFQMC_OK.
+ */
+afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular);
+
+/* Device bytes owned by the handle (static data plus workspace). */
+afqmc_status afqmc_kp_memory_bytes(afqmc_kp_t h, size_t* bytes);
+
+/* Number of kernel launches the last entry point call enqueued. */
+afqmc_status afqmc_kp_launch_count(afqmc_kp_t h, int* launches);
+
+/* Static, NUL-terminated description of a status code. */
+const char* afqmc_status_string(afqmc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFQMC_KP_H */

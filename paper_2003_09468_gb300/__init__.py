@@ -1,0 +1,8 @@
+"""GB300-native k-point phaseless AFQMC walker step (arXiv:2003.09468).
+
+The compute lives in libafqmc_kp.so (hand-written CUDA for sm_103a behind the C
+ABI in include/afqmc_kp.h); this package only marshals arguments.
+"""
+from .binding import (AfqmcError, KPointAFQMC, LocalEnergy, LIB_PATH, SIGNATURES, load_library)  # noqa: F401
+
+__all__ = ["AfqmcError", "KPointAFQMC", "LocalEnergy", "LIB_PATH", "SIGNATURES", "load_library"]

@@ -1,0 +1,234 @@
+"""ctypes binding of libafqmc_kp.so (argument marshalling only).
+
+Every operation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current stream.  If the library is missing or cannot be loaded
+the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libafqmc_kp.so")
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "singular walker overlap",
+          5: "timeout", 6: "unsupported"}
+FP64, MIXED = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+
+# Entry points declared in include/afqmc_kp.h, with their ctypes signatures.
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "afqmc_kp_create": [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "afqmc_kp_destroy": [_VP],
+    "afqmc_kp_set_one_body": [_VP, _VP, _VP],
+    "afqmc_kp_force_bias": [_VP, _VP, _VP, _VP],
+    "afqmc_kp_propagate": [_VP, _VP, _VP, _VP, _VP, _I, _VP],
+    "afqmc_kp_orthonormalise": [_VP, _VP, _VP, _VP],
+    "afqmc_kp_local_energy": [_VP, _VP, _VP, _VP],
+    "afqmc_kp_local_energy_backward": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "afqmc_kp_last_error": [_VP, _VP, ctypes.POINTER(_I)],
+    "afqmc_kp_memory_bytes": [_VP, ctypes.POINTER(ctypes.c_size_t)],
+    "afqmc_kp_launch_count": [_VP, ctypes.POINTER(_I)],
+    "afqmc_status_string": [_I],
+}
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("kgrid", ctypes.c_int * 3), ("M", _I), ("nocc", _I), ("nchol", _I), ("nwalkers", _I),
+                ("dt", _D), ("taylor_order", _I), ("prec", _I), ("workspace_cap_bytes", ctypes.c_size_t)]
+
+
+class AfqmcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "afqmc_status_string" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise AfqmcError(status, where)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor, dtype, shape, name) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _as_c128(a) -> torch.Tensor:
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))
+    return a.to(torch.complex128).contiguous()
+
+
+class KPointAFQMC:
+    """One k-point Hamiltonian + trial on the current CUDA device (a library handle)."""
+
+    def __init__(self, grid, L, h1, trial, nwalkers: int, dt: float, taylor_order: int = 6,
+                 precision: str = "fp64", workspace_cap_bytes: int = 0, stream=None):
+        lib = load_library()
+        self.lib = lib
+        L = _as_c128(L)
+        h1 = _as_c128(h1)
+        trial = _as_c128(trial)
+        nk, _, G, M, _ = L.shape
+        n = trial.shape[2]
+        self.grid = tuple(int(g) for g in grid)
+        if int(np.prod(self.grid)) != nk:
+            raise ValueError("grid does not match L")
+        self.nk, self.M, self.n, self.G, self.W = nk, M, n, G, int(nwalkers)
+        self.NM, self.N = nk * M, nk * n
+        self.dt = float(dt)
+        self.precision = precision
+        d = Desc()
+        d.kgrid[:] = list(self.grid)
+        d.M, d.nocc, d.nchol, d.nwalkers = M, n, G, self.W
+        d.dt = self.dt
+        d.taylor_order = int(taylor_order)
+        d.prec = PRECISIONS[precision]
+        d.workspace_cap_bytes = int(workspace_cap_bytes)
+        # host inputs are passed as host pointers (the library copies them)
+        keep = [t if t.is_cuda else t.contiguous() for t in (L, h1, trial)]
+        handle = ctypes.c_void_p()
+        _check(lib.afqmc_kp_create(ctypes.byref(d), keep[0].data_ptr(), keep[1].data_ptr(), keep[2].data_ptr(),
+                                   _stream(stream), ctypes.byref(handle)), "afqmc_kp_create")
+        self.handle = handle
+        self.h1 = h1.cuda() if not h1.is_cuda else h1
+
+    # shapes -------------------------------------------------------------
+    @property
+    def phi_shape(self):
+        return (self.W, 2, self.NM, self.N)
+
+    @property
+    def field_shape(self):
+        return (self.W, 2, self.nk, self.G)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(self.lib.afqmc_kp_destroy(self.handle), "afqmc_kp_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # calls --------------------------------------------------------------
+    def set_one_body(self, h1: torch.Tensor, stream=None):
+        p = _ptr(h1, torch.complex128, (self.nk, self.M, self.M), "h1")
+        _check(self.lib.afqmc_kp_set_one_body(self.handle, p, _stream(stream)), "afqmc_kp_set_one_body")
+
+    def force_bias(self, phi: torch.Tensor, xbar: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        if xbar is None:
+            xbar = torch.empty((self.W, 2, self.nk, self.G), dtype=torch.complex128, device=phi.device)
+        _check(self.lib.afqmc_kp_force_bias(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                            _ptr(xbar, torch.complex128, xbar.shape, "xbar"), _stream(stream)),
+               "afqmc_kp_force_bias")
+        return xbar
+
+    def propagate(self, phi, x, weight, logdet=None, do_qr=False, stream=None):
+        lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
+        _check(self.lib.afqmc_kp_propagate(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                           _ptr(x, torch.float64, self.field_shape, "x"),
+                                           _ptr(weight, torch.float64, (self.W,), "weight"), lp,
+                                           1 if do_qr else 0, _stream(stream)), "afqmc_kp_propagate")
+
+    def orthonormalise(self, phi, logdet=None, stream=None):
+        lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
+        _check(self.lib.afqmc_kp_orthonormalise(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                                lp, _stream(stream)), "afqmc_kp_orthonormalise")
+
+    def local_energy(self, phi, eloc=None, stream=None) -> torch.Tensor:
+        if eloc is None:
+            eloc = torch.empty((self.W, 3), dtype=torch.complex128, device=phi.device)
+        _check(self.lib.afqmc_kp_local_energy(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                              _ptr(eloc, torch.complex128, (self.W, 3), "eloc"), _stream(stream)),
+               "afqmc_kp_local_energy")
+        return eloc
+
+    def local_energy_backward(self, phi, grad_e, want_phi=True, want_h1=True, stream=None
+                              ) -> Tuple[Optional[torch.Tensor], Optional[torch.Tensor]]:
+        gphi = torch.empty(self.phi_shape, dtype=torch.complex128, device=phi.device) if want_phi else None
+        gh1 = torch.empty((self.nk, self.M, self.M), dtype=torch.complex128, device=phi.device) if want_h1 else None
+        _check(self.lib.afqmc_kp_local_energy_backward(
+            self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+            _ptr(grad_e, torch.complex128, (self.W, 3), "grad_e"),
+            0 if gphi is None else gphi.data_ptr(), 0 if gh1 is None else gh1.data_ptr(), _stream(stream)),
+            "afqmc_kp_local_energy_backward")
+        return gphi, gh1
+
+    def last_error(self, stream=None) -> Tuple[int, int]:
+        n = ctypes.c_int(0)
+        s = self.lib.afqmc_kp_last_error(self.handle, _stream(stream), ctypes.byref(n))
+        return s, n.value
+
+    def memory_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(self.lib.afqmc_kp_memory_bytes(self.handle, ctypes.byref(b)), "afqmc_kp_memory_bytes")
+        return b.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int(0)
+        _check(self.lib.afqmc_kp_launch_count(self.handle, ctypes.byref(n)), "afqmc_kp_launch_count")
+        return n.value
+
+
+class LocalEnergy(torch.autograd.Function):
+    """E_L parts (W, 3) as a differentiable function of the walkers and of h[k].
+
+    Forward installs h1 in the handle (afqmc_kp_set_one_body) and evaluates the
+    local energy; backward calls the library's adjoint kernels.
+    """
+
+    @staticmethod
+    def forward(ctx, phi, h1, sys: KPointAFQMC):
+        sys.set_one_body(h1.detach().contiguous())
+        ctx.sys = sys
+        ctx.save_for_backward(phi.detach())
+        return sys.local_energy(phi.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_e):
+        (phi,) = ctx.saved_tensors
+        sys = ctx.sys
+        gphi, gh1 = sys.local_energy_backward(phi, grad_e.contiguous(), want_phi=ctx.needs_input_grad[0],
+                                              want_h1=ctx.needs_input_grad[1])
+        return gphi, gh1, None

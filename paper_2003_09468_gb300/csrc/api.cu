@@ -1,0 +1,316 @@
+// C ABI entry points of the k-point AFQMC library (declared in include/afqmc_kp.h).
+// Argument validation, device memory ownership and dispatch to the FP64 or the
+// tensor-core (mixed) kernels.  No exception crosses this file's boundary.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "handle.hpp"
+#include "mixed.hpp"
+
+namespace {
+
+afqmc_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return AFQMC_OK;
+  if (e == cudaErrorMemoryAllocation) return AFQMC_ERR_OOM;
+  return AFQMC_ERR_CUDA;
+}
+
+void free_all(afqmc_kp* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+template <typename T>
+cudaError_t alloc(afqmc_kp* h, T** p, size_t count) {
+  void* q = nullptr;
+  size_t b = count * sizeof(T);
+  if (b == 0) b = 16;
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  h->bytes += b;
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+// k - Q and -Q on the Gamma-centred grid, C order over the three axes.
+void momentum_tables(const int g[3], std::vector<int>& kminus, std::vector<int>& minus) {
+  const int nk = g[0] * g[1] * g[2];
+  kminus.assign((size_t)nk * nk, 0);
+  minus.assign(nk, 0);
+  auto coords = [&](int i, int c[3]) { c[2] = i % g[2]; c[1] = (i / g[2]) % g[1]; c[0] = i / (g[1] * g[2]); };
+  auto lin = [&](const int c[3]) { return (c[0] * g[1] + c[1]) * g[2] + c[2]; };
+  for (int k = 0; k < nk; ++k)
+    for (int Q = 0; Q < nk; ++Q) {
+      int ck[3], cq[3], r[3];
+      coords(k, ck);
+      coords(Q, cq);
+      for (int d = 0; d < 3; ++d) r[d] = ((ck[d] - cq[d]) % g[d] + g[d]) % g[d];
+      kminus[(size_t)k * nk + Q] = lin(r);
+    }
+  for (int Q = 0; Q < nk; ++Q) {
+    int cq[3], r[3];
+    coords(Q, cq);
+    for (int d = 0; d < 3; ++d) r[d] = (g[d] - cq[d]) % g[d];
+    minus[Q] = lin(r);
+  }
+}
+
+bool valid_desc(const afqmc_kp_desc* d) {
+  if (!d) return false;
+  for (int i = 0; i < 3; ++i)
+    if (d->kgrid[i] < 1 || d->kgrid[i] > 64) return false;
+  const long nk = (long)d->kgrid[0] * d->kgrid[1] * d->kgrid[2];
+  if (nk > 4096) return false;
+  if (d->M < 1 || d->M > 128) return false;
+  if (d->nocc < 1 || d->nocc > d->M) return false;
+  if (d->nchol < 1 || d->nchol > 8192) return false;
+  if (d->nwalkers < 1 || d->nwalkers > 65535) return false;
+  if (!(d->dt > 0.0)) return false;
+  if (d->taylor_order < 1 || d->taylor_order > 16) return false;
+  if (d->prec != AFQMC_FP64 && d->prec != AFQMC_MIXED) return false;
+  if (nk * d->nocc > 1024) return false;  // N per spin
+  return true;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* afqmc_status_string(afqmc_status s) {
+  switch (s) {
+    case AFQMC_OK: return "ok";
+    case AFQMC_ERR_INVALID: return "invalid argument";
+    case AFQMC_ERR_OOM: return "out of device memory (or over workspace cap)";
+    case AFQMC_ERR_CUDA: return "CUDA error";
+    case AFQMC_ERR_SINGULAR: return "singular walker overlap";
+    case AFQMC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case AFQMC_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+afqmc_status afqmc_kp_create(const afqmc_kp_desc* desc, const void* L, const void* h1, const void* trial,
+                             void* stream, afqmc_kp_t* out) {
+  if (!valid_desc(desc) || !L || !h1 || !trial || !out) return AFQMC_ERR_INVALID;
+  if ((long)desc->nocc * desc->M > 1024) return AFQMC_ERR_UNSUPPORTED;
+  afqmc_kp* h = new (std::nothrow) afqmc_kp();
+  if (!h) return AFQMC_ERR_OOM;
+  try {
+    h->d = *desc;
+    h->nk = desc->kgrid[0] * desc->kgrid[1] * desc->kgrid[2];
+    h->M = desc->M;
+    h->n = desc->nocc;
+    h->G = desc->nchol;
+    h->W = desc->nwalkers;
+    h->NM = h->nk * h->M;
+    h->N = h->nk * h->n;
+    h->order = desc->taylor_order;
+    h->dt = desc->dt;
+    h->sqdt = sqrt(desc->dt);
+    momentum_tables(desc->kgrid, h->h_kminus, h->h_minus);
+    cudaStream_t st = as_stream(stream);
+    const size_t nk = h->nk, M = h->M, n = h->n, G = h->G, W = h->W, NM = h->NM, N = h->N;
+    cudaError_t e = cudaSuccess;
+#define TRY(x)                         \
+  do {                                 \
+    if ((e = (x)) != cudaSuccess) {    \
+      afqmc_status s_ = from_cuda(e);  \
+      free_all(h);                     \
+      delete h;                        \
+      cudaGetLastError();              \
+      return s_;                       \
+    }                                  \
+  } while (0)
+    TRY(alloc(h, &h->kminus, nk * nk));
+    TRY(alloc(h, &h->minus, nk));
+    TRY(alloc(h, &h->L, nk * nk * G * M * M));
+    TRY(alloc(h, &h->LH, nk * nk * G * n * M));
+    TRY(alloc(h, &h->A, nk * M * n));
+    TRY(alloc(h, &h->h1, nk * M * M));
+    TRY(alloc(h, &h->AhH, nk * n * M));
+    TRY(alloc(h, &h->v0, nk * M * M));
+    TRY(alloc(h, &h->Ehalf, nk * M * M));
+    TRY(alloc(h, &h->expm_tmp, nk * 3 * M * M));
+    TRY(alloc(h, &h->S, W * 2 * N * N));
+    TRY(alloc(h, &h->Sinv, W * 2 * N * N));
+    TRY(alloc(h, &h->Gh, W * 2 * N * NM));
+    TRY(alloc(h, &h->X, W * nk * G));
+    TRY(alloc(h, &h->xbar, W * 2 * nk * G));
+    TRY(alloc(h, &h->y, W * nk * G));
+    TRY(alloc(h, &h->ld_old, W * 2));
+    TRY(alloc(h, &h->ld_new, W * 2));
+    TRY(alloc(h, &h->sing_old, W * 2));
+    TRY(alloc(h, &h->sing_new, W * 2));
+    TRY(alloc(h, &h->epart, W * 2 * nk * nk));
+    TRY(alloc(h, &h->Gam, W * 2 * N * NM));
+    TRY(alloc(h, &h->P, W * 2 * N * N));
+    TRY(alloc(h, &h->flags, 4));
+    if (desc->prec == AFQMC_FP64) {
+      TRY(alloc(h, &h->V, W * NM * NM));
+      TRY(alloc(h, &h->T0, W * 2 * NM * N));
+      TRY(alloc(h, &h->T1, W * 2 * NM * N));
+      TRY(alloc(h, &h->acc, W * 2 * NM * N));
+    }
+    if (desc->workspace_cap_bytes && h->bytes > desc->workspace_cap_bytes) {
+      free_all(h);
+      delete h;
+      return AFQMC_ERR_OOM;
+    }
+    TRY(cudaMemcpyAsync(h->kminus, h->h_kminus.data(), sizeof(int) * nk * nk, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(h->minus, h->h_minus.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(h->L, L, sizeof(zc) * nk * nk * G * M * M, cudaMemcpyDefault, st));
+    TRY(cudaMemcpyAsync(h->h1, h1, sizeof(zc) * nk * M * M, cudaMemcpyDefault, st));
+    TRY(cudaMemcpyAsync(h->A, trial, sizeof(zc) * nk * M * n, cudaMemcpyDefault, st));
+    TRY(cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st));
+    TRY(cudaMemsetAsync(h->sing_old, 0, sizeof(int) * W * 2, st));
+    TRY(cudaMemsetAsync(h->sing_new, 0, sizeof(int) * W * 2, st));
+    TRY(fp64::setup_static(h, st));
+    if (desc->prec == AFQMC_MIXED) {
+      afqmc_status ms = mixed::create(h, st);
+      if (ms != AFQMC_OK) {
+        cudaStreamSynchronize(st);
+        mixed::destroy(h);
+        free_all(h);
+        delete h;
+        return ms;
+      }
+      if (desc->workspace_cap_bytes && h->bytes > desc->workspace_cap_bytes) {
+        cudaStreamSynchronize(st);
+        mixed::destroy(h);
+        free_all(h);
+        delete h;
+        return AFQMC_ERR_OOM;
+      }
+    }
+    TRY(cudaStreamSynchronize(st));
+#undef TRY
+    *out = h;
+    return AFQMC_OK;
+  } catch (...) {
+    free_all(h);
+    delete h;
+    return AFQMC_ERR_OOM;
+  }
+}
+
+afqmc_status afqmc_kp_destroy(afqmc_kp_t h) {
+  if (!h) return AFQMC_ERR_INVALID;
+  cudaError_t e = cudaDeviceSynchronize();
+  mixed::destroy(h);
+  free_all(h);
+  delete h;
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_set_one_body(afqmc_kp_t h, const void* h1, void* stream) {
+  if (!h || !h1) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(h->h1, h1, sizeof(zc) * (size_t)h->nk * h->M * h->M, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = fp64::set_one_body(h, st);
+  if (e == cudaSuccess && h->mixed) e = mixed::set_one_body(h, st);
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_force_bias(afqmc_kp_t h, const void* phi, void* xbar, void* stream) {
+  if (!h || !phi || !xbar) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  if (h->mixed) {
+    e = mixed::force_bias(h, static_cast<const zc*>(phi), static_cast<zc*>(xbar), st);
+  } else {
+    e = fp64::green(h, static_cast<const zc*>(phi), st);
+    if (e == cudaSuccess) e = fp64::cholesky_trace(h, st);
+    if (e == cudaSuccess) e = fp64::force_bias(h, nullptr, static_cast<zc*>(xbar), st);
+  }
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double* weight, void* logdet,
+                                int do_qr, void* stream) {
+  if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1)) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  if (h->mixed)
+    e = mixed::propagate(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(logdet), do_qr, st);
+  else
+    e = fp64::propagate(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(logdet), do_qr, st);
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void* stream) {
+  if (!h || !phi) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  if (h->mixed)
+    e = mixed::orthonormalise(h, static_cast<zc*>(phi), static_cast<zc*>(logdet), st);
+  else
+    e = fp64::orthonormalise(h, static_cast<zc*>(phi), static_cast<zc*>(logdet), st);
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_local_energy(afqmc_kp_t h, const void* phi, void* eloc, void* stream) {
+  if (!h || !phi || !eloc) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  if (h->mixed)
+    e = mixed::local_energy(h, static_cast<const zc*>(phi), static_cast<zc*>(eloc), st);
+  else
+    e = fp64::local_energy(h, static_cast<const zc*>(phi), static_cast<zc*>(eloc), st);
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const void* grad_e, void* grad_phi,
+                                            void* grad_h1, void* stream) {
+  if (!h || !phi || !grad_e) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  if (h->mixed)
+    e = mixed::local_energy_backward(h, static_cast<const zc*>(phi), static_cast<const zc*>(grad_e),
+                                     static_cast<zc*>(grad_phi), static_cast<zc*>(grad_h1), st);
+  else
+    e = fp64::local_energy_backward(h, static_cast<const zc*>(phi), static_cast<const zc*>(grad_e),
+                                    static_cast<zc*>(grad_phi), static_cast<zc*>(grad_h1), st);
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular) {
+  if (!h) return AFQMC_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return AFQMC_ERR_CUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return AFQMC_ERR_CUDA;
+  int f[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return AFQMC_ERR_CUDA;
+  if (cudaMemset(h->flags, 0, sizeof(f)) != cudaSuccess) return AFQMC_ERR_CUDA;
+  if (n_singular) *n_singular = f[0];
+  if (f[1]) return AFQMC_ERR_TIMEOUT;
+  if (f[0]) return AFQMC_ERR_SINGULAR;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_memory_bytes(afqmc_kp_t h, size_t* bytes) {
+  if (!h || !bytes) return AFQMC_ERR_INVALID;
+  *bytes = h->bytes;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_launch_count(afqmc_kp_t h, int* launches) {
+  if (!h || !launches) return AFQMC_ERR_INVALID;
+  *launches = h->launches;
+  return AFQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal state of one afqmc_kp handle (not part of the ABI).
+#pragma once
+
+#include <vector>
+
+#include "afqmc_kp.h"
+#include "common.cuh"
+
+struct MixedState;  // tensor-core path buffers (mixed.cu)
+
+struct afqmc_kp {
+  afqmc_kp_desc d;
+  int nk, M, n, G, W, NM, N, order;
+  double dt, sqdt;
+  std::vector<int> h_kminus, h_minus;  // host copies of the momentum tables
+  int* kminus = nullptr;               // device [Nk][Nk]: index of k - Q
+  int* minus = nullptr;                // device [Nk]: index of -Q
+
+  // static data, complex128
+  zc* L = nullptr;      // [Q][k][g][p][r]
+  zc* LH = nullptr;     // [Q][k][g][a][r]  half-rotated
+  zc* A = nullptr;      // [k][p][a]        trial
+  zc* h1 = nullptr;     // [k][p][q]
+  zc* AhH = nullptr;    // [k][a][q]        A[k]^dagger h[k]
+  zc* v0 = nullptr;     // [k][p][q]        mean-field term
+  zc* Ehalf = nullptr;  // [k][p][q]        exp(-dt/2 (h + v0))
+  zc* expm_tmp = nullptr;  // [k][3][M][M]
+
+  // workspace
+  zc* S = nullptr;      // [W][2][N][N]    overlap, then LU factors
+  zc* Sinv = nullptr;   // [W][2][N][N]
+  zc* Gh = nullptr;     // [W][2][N][NM]   half-rotated Green's function
+  zc* X = nullptr;      // [W][Nk][G]
+  zc* xbar = nullptr;   // [W][2][Nk][G]
+  zc* y = nullptr;      // [W][Nk][G]      sqrt(dt) * vHS coefficients
+  zc* V = nullptr;      // [W][NM][NM]
+  zc* T0 = nullptr;     // [W][2][NM][N]
+  zc* T1 = nullptr;     // [W][2][NM][N]
+  zc* acc = nullptr;    // [W][2][NM][N]
+  zc* ld_old = nullptr; // [W][2]
+  zc* ld_new = nullptr; // [W][2]
+  int* sing_old = nullptr;  // [W][2]
+  int* sing_new = nullptr;  // [W][2]
+  zc* epart = nullptr;  // [W][2][Nk][Nk] exchange partials
+  zc* Gam = nullptr;    // [W][2][N][NM]   dE/dGh
+  zc* P = nullptr;      // [W][2][N][N]
+  int* flags = nullptr; // [0] singular walkers, [1] timeouts
+
+  MixedState* mixed = nullptr;
+
+  int launches = 0;     // kernel launches of the current call
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+// Launch bookkeeping: every kernel launch goes through AFQMC_LAUNCHED(h).
+#define AFQMC_LAUNCHED(h) ((h)->launches++)
+
+// FP64 path (fp64.cu)
+namespace fp64 {
+cudaError_t setup_static(afqmc_kp* h, cudaStream_t st);
+cudaError_t set_one_body(afqmc_kp* h, cudaStream_t st);
+cudaError_t green(afqmc_kp* h, const zc* phi, cudaStream_t st);        // S, LU, Sinv, logdet, Gh
+cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st);              // X from Gh
+cudaError_t force_bias(afqmc_kp* h, const double* x, zc* xbar_out, cudaStream_t st);
+cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr,
+                      cudaStream_t st);
+cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st);
+cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st);
+cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi,
+                                  zc* grad_h1, cudaStream_t st);
+}  // namespace fp64
