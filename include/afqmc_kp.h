@@ -204,6 +204,14 @@ afqmc_status afqmc_kp_memory_bytes(afqmc_kp_t h, size_t* bytes);
 /* Number of kernel launches the last entry point call enqueued. */
 afqmc_status afqmc_kp_launch_count(afqmc_kp_t h, int* launches);
 
+/*
+ * afqmc_last_message -- NUL-terminated text of the most recent CUDA error the
+ * library saw on the calling thread ("" if none).  Valid until the next call
+ * on that thread; owned by the library.  The paper has no counterpart: this is
+ * a diagnostic of this library.
+ */
+const char* afqmc_last_message(void);
+
 /* Static, NUL-terminated description of a status code. */
 const char* afqmc_status_string(afqmc_status s);
 

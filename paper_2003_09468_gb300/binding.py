@@ -36,6 +36,7 @@ SIGNATURES = {
     "afqmc_kp_memory_bytes": [_VP, ctypes.POINTER(ctypes.c_size_t)],
     "afqmc_kp_launch_count": [_VP, ctypes.POINTER(_I)],
     "afqmc_status_string": [_I],
+    "afqmc_last_message": [],
 }
 
 
@@ -64,14 +65,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name, args in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "afqmc_status_string" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name in ("afqmc_status_string", "afqmc_last_message") else ctypes.c_int
     _lib = lib
     return lib
 
 
 def _check(status: int, where: str):
     if status != 0:
-        raise AfqmcError(status, where)
+        msg = _lib.afqmc_last_message().decode() if _lib is not None else ""
+        raise AfqmcError(status, where + (f" [{msg}]" if msg else ""))
 
 
 def _stream(stream=None) -> int:

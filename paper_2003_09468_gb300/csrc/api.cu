@@ -12,8 +12,11 @@
 
 namespace {
 
+thread_local char g_msg[512] = "";
+
 afqmc_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return AFQMC_OK;
+  snprintf(g_msg, sizeof(g_msg), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return AFQMC_ERR_OOM;
   return AFQMC_ERR_CUDA;
 }
@@ -81,6 +84,8 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 }  // namespace
 
 extern "C" {
+
+const char* afqmc_last_message(void) { return g_msg; }
 
 const char* afqmc_status_string(afqmc_status s) {
   switch (s) {

@@ -964,18 +964,20 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
   return cudaSuccess;
 }
 
-static cudaError_t configure_smem(afqmc_kp* h) {
-  const int big = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(vhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gamma_exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xtrace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  (void)h;
-  return e;
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Opt in to the dynamic shared memory each kernel needs at this system size.
+static cudaError_t configure_smem(afqmc_kp* h) {
+  cudaError_t e = set_smem((const void*)vhs_kernel, sizeof(zc) * VWC * h->G);
+  if (e == cudaSuccess)
+    e = set_smem((const void*)gamma_exchange_kernel, sizeof(zc) * (h->n * h->M + (size_t)h->G * h->n * h->n));
+  if (e == cudaSuccess) e = set_smem((const void*)xtrace_kernel, sizeof(zc) * XWC * h->n * h->M);
+  if (e == cudaSuccess) e = set_smem((const void*)qr_kernel, (size_t)h->N * (2 * sizeof(zc) + sizeof(double)));
+  if (e == cudaSuccess) e = set_smem((const void*)exchange_fp64_kernel, sizeof(zc) * 2 * h->n * h->M);
+  return e;
+}
 
 }  // namespace fp64
