@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Walker-step throughput of the k-point phaseless AFQMC hot path on GB300.
+
+One step = one hybrid propagation of every walker (Green's function, force
+bias, vHS, 6-term Taylor exp(V) with both one-body halves, weight update,
+Householder QR every 5th step) followed by the local energy (E1 + Coulomb +
+exchange) of every walker, for the 3x3x3 diamond-sized synthetic system
+(M = 26 orbitals per k, 4 occupied per k per spin, 208 Cholesky vectors per Q,
+64 walkers per GPU).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+Multi-GPU runs (torchrun, one process per GPU) are independent walker
+replicas: no collective on the data path, only the timing max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "walker-steps/s (propagate+E_L)"
+UNIT = "walker-steps/s"
+QR_PERIOD = 5
+WORKLOADS = {
+    "diamond-3x3x3": gen.DIAMOND_3x3x3,
+    "small-2x2x2": gen.SMALL_2x2x2,
+}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work (complex multiply-add = 8 real flops)
+# ---------------------------------------------------------------------------
+def exchange_flops(spec) -> float:
+    """E_X for all walkers and both spins: every T^Q_g = LH^{Qg} Gh^T element once
+    (N x N per (Q, g), M complex MACs each), plus the pairing products."""
+    nk, G, N, M = spec.nk, spec.nchol, spec.N, spec.M
+    return spec.nwalkers * 2 * 8.0 * nk * G * N * N * (M + 0.5)
+
+
+def step_flops(spec, order=6) -> dict:
+    nk, G, N, M, n, NM, W = spec.nk, spec.nchol, spec.N, spec.M, spec.nocc, spec.NM, spec.nwalkers
+    f = {
+        "overlap+inverse+green": W * 2 * 8.0 * (N * N * M + N ** 3 + N * N * NM) * 2,  # at step start and for E_L
+        "force_bias": W * 8.0 * nk * G * nk * n * M * 2,
+        "vhs": W * 8.0 * nk * nk * G * M * M,
+        "taylor": W * 8.0 * order * NM * NM * 2 * N,
+        "one_body": W * 2 * 8.0 * nk * M * M * 2 * N,
+        "exchange": exchange_flops(spec),
+    }
+    f["total"] = sum(f.values())
+    return f
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure; used only for cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+class OracleStepper:
+    """The FP64 CPU oracle, built once for a workload; times single walker-steps."""
+
+    def __init__(self, spec):
+        from oracle import afqmc_kp as ok
+        self.ok = ok
+        self.spec = spec
+        self.osys = ok.System(spec.grid, gen.cholesky(spec), gen.one_body(spec), gen.trial(spec), spec.dt)
+
+    def seconds(self, walker_index: int = 0, step: int = 0) -> float:
+        spec, ok = self.spec, self.ok
+        phi = gen.walkers(spec, 1, first=walker_index)[0]
+        x = gen.fields(spec, step, 1, first=walker_index)[0]
+        t0 = time.perf_counter()
+        phi_new, _, _, _, _ = ok.propagate_walker(self.osys, phi, x, 1.0)
+        ok.local_energy(self.osys, phi_new)
+        return time.perf_counter() - t0
+
+
+def cpu_cores() -> int:
+    return os.cpu_count() or 1
+
+
+def run_reference(args, spec, wl_name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    stepper = OracleStepper(spec)
+    for i in range(args.warmup + args.steps):
+        t = stepper.seconds(walker_index=i % spec.nwalkers, step=i)
+        if i >= args.warmup:
+            times.append(t)
+    mean_s = sum(times) / len(times)
+    value = 1.0 / mean_s
+    cb = {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+          "sample": f"1 walker x 1 step (propagate + E_L) of {wl_name} per timed step, FP64 NumPy"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": wl_name, "walkers": 1},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["auto", "mixed", "fp64"], default="auto")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="diamond-3x3x3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, spec, args.workload)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2003_09468_gb300 import KPointAFQMC, AfqmcError
+
+    L, h1, A = gen.cholesky(spec), gen.one_body(spec), gen.trial(spec)
+    precision = args.precision
+    sys_ = None
+    if precision in ("auto", "mixed"):
+        try:
+            sys_ = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="mixed")
+            precision = "mixed"
+        except AfqmcError as e:
+            if args.precision == "mixed":
+                raise
+            if e.status != 6:
+                raise
+    if sys_ is None:
+        precision = "fp64"
+        sys_ = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
+    del L
+
+    # walkers and fields: independent replicas per rank (disjoint walker indices)
+    first = rank * spec.nwalkers
+    phi0 = gen.walkers(spec, spec.nwalkers, first=first)
+    nsteps = args.warmup + args.steps
+    xs = [torch.from_numpy(gen.fields(spec, i, spec.nwalkers, first=first)).to(dev) for i in range(nsteps)]
+    phi = torch.from_numpy(phi0).to(dev)
+    w = torch.ones(spec.nwalkers, dtype=torch.float64, device=dev)
+    eloc = torch.empty((spec.nwalkers, 3), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+
+    launches = [0]
+
+    def step(i, x):
+        sys_.propagate(phi, x, w, do_qr=((i + 1) % QR_PERIOD == 0))
+        launches[0] += sys_.launch_count()
+        sys_.local_energy(phi, eloc)
+        launches[0] += sys_.launch_count()
+
+    for i in range(args.warmup):
+        step(i, xs[i])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    sys_.profile(True)
+    sys_.stage_times()
+    launches[0] = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.warmup, nsteps):
+        step(i, xs[i])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stages = sys_.stage_times()
+    sys_.profile(False)
+    gpu_launches = launches[0]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    value = world * spec.nwalkers * args.steps / (ms * 1e-3)
+    eloc_h = eloc.cpu().numpy()
+    finite = bool(np.all(np.isfinite(eloc_h)))
+
+    # end-to-end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xs_host = [x.cpu().pin_memory() for x in xs]
+        e_host = torch.empty((spec.nwalkers, 3), dtype=torch.complex128).pin_memory()
+        w_host = torch.empty(spec.nwalkers, dtype=torch.float64).pin_memory()
+        xdev = torch.empty_like(xs[0])
+        phi.copy_(torch.from_numpy(phi0).to(dev))
+        w.fill_(1.0)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.warmup, nsteps):
+            xdev.copy_(xs_host[i], non_blocking=True)
+            sys_.propagate(phi, xdev, w, do_qr=((i + 1) % QR_PERIOD == 0))
+            sys_.local_energy(phi, eloc)
+            e_host.copy_(eloc, non_blocking=True)
+            w_host.copy_(w, non_blocking=True)
+            stream.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * spec.nwalkers * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(xs[0].numel() * 8),
+               "d2h_bytes_per_step": int(e_host.numel() * 16 + w_host.numel() * 8)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peaks_kind = load_peaks()
+    ex_ms, ex_n = stages["exchange"]
+    ex_flops = exchange_flops(spec)
+    if precision == "fp64":
+        bound, peak, unit_r = "alu", 1.25, "TFLOP/s"
+        peak_note = "FP64 nominal 1.25 TFLOP/s (GB300 FP64 pipe); a DFMA probe measured 1.20"
+        dtype = "f64"
+    else:
+        bound, peak, unit_r = "tensor", peaks.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
+        peak_note = f"dense f16/bf16 tensor, sustained, {peaks_kind}"
+        dtype = "f16x2-split/f32-acc + f64"
+    achieved = ex_flops / (ex_ms / ex_n * 1e-3) / 1e12 if ex_n else None
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit_r,
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "exchange", "peak_source": peak_note,
+                "algorithmic_flops_per_launch": ex_flops,
+                "launch_ms": ex_ms / ex_n if ex_n else None}
+
+    cpu_baseline = None
+    if not args.no_cpu_baseline and world == 1:
+        t = OracleStepper(spec).seconds(0, 0)
+        cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                        "sample": f"1 walker x 1 step (propagate + E_L) of {args.workload}, FP64 NumPy, "
+                                  f"{t:.1f} s"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(spec.grid), "M": spec.M, "nocc": spec.nocc,
+                   "nchol": spec.nchol, "walkers_per_gpu": spec.nwalkers, "taylor_order": 6,
+                   "qr_period": QR_PERIOD, "precision": precision, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (Cholesky tensor alone exceeds 129 MB)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu_baseline,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "stages_ms": {k: round(v[0], 3) for k, v in stages.items() if v[1]},
+        "finite": finite,
+    }
+    print(json.dumps(out))
+    sys_.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -201,6 +201,33 @@ afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular);
 /* Device bytes owned by the handle (static data plus workspace). */
 afqmc_status afqmc_kp_memory_bytes(afqmc_kp_t h, size_t* bytes);
 
+/*
+ * Per-stage timing with CUDA events recorded on the caller's stream around each
+ * stage's kernels (the paper times its operations per block, Sec. 3.1-3.2; the
+ * mechanism here is this library's own).  Stages:
+ */
+typedef enum {
+  AFQMC_STAGE_GREEN = 0,       /* overlap, LU / inverse / log det, Green's function */
+  AFQMC_STAGE_FORCE_BIAS = 1,  /* Cholesky trace X and xbar                         */
+  AFQMC_STAGE_VHS = 2,         /* vHS build                                         */
+  AFQMC_STAGE_TAYLOR = 3,      /* one-body halves and the Taylor series             */
+  AFQMC_STAGE_WEIGHT = 4,      /* new overlap, log det and hybrid weight            */
+  AFQMC_STAGE_QR = 5,          /* re-orthonormalisation                             */
+  AFQMC_STAGE_ENERGY = 6,      /* E1, EC and the final sums                         */
+  AFQMC_STAGE_EXCHANGE = 7,    /* the exchange contraction kernel alone             */
+  AFQMC_STAGE_BACKWARD = 8,    /* adjoint kernels                                   */
+  AFQMC_NSTAGES = 9
+} afqmc_stage;
+
+/* enable != 0 starts recording (allocates CUDA events on the host side as
+ * needed; do not enable while capturing a graph); 0 stops.  */
+afqmc_status afqmc_kp_profile(afqmc_kp_t h, int enable);
+
+/* Synchronises the device, then writes for every stage the summed event time
+ * in milliseconds (ms[AFQMC_NSTAGES]) and the number of recorded intervals
+ * (count[AFQMC_NSTAGES]) since the last read, and clears them. */
+afqmc_status afqmc_kp_stage_times(afqmc_kp_t h, double* ms, int* count);
+
 /* Number of kernel launches the last entry point call enqueued. */
 afqmc_status afqmc_kp_launch_count(afqmc_kp_t h, int* launches);
 

@@ -35,6 +35,8 @@ SIGNATURES = {
     "afqmc_kp_last_error": [_VP, _VP, ctypes.POINTER(_I)],
     "afqmc_kp_memory_bytes": [_VP, ctypes.POINTER(ctypes.c_size_t)],
     "afqmc_kp_launch_count": [_VP, ctypes.POINTER(_I)],
+    "afqmc_kp_profile": [_VP, _I],
+    "afqmc_kp_stage_times": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "afqmc_status_string": [_I],
     "afqmc_last_message": [],
 }
@@ -206,6 +208,18 @@ class KPointAFQMC:
         b = ctypes.c_size_t(0)
         _check(self.lib.afqmc_kp_memory_bytes(self.handle, ctypes.byref(b)), "afqmc_kp_memory_bytes")
         return b.value
+
+    STAGES = ("green", "force_bias", "vhs", "taylor", "weight", "qr", "energy", "exchange", "backward")
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.afqmc_kp_profile(self.handle, 1 if enable else 0), "afqmc_kp_profile")
+
+    def stage_times(self):
+        """{stage: (milliseconds, intervals)} recorded since the last read (synchronises)."""
+        ms = (ctypes.c_double * len(self.STAGES))()
+        cnt = (ctypes.c_int * len(self.STAGES))()
+        _check(self.lib.afqmc_kp_stage_times(self.handle, ms, cnt), "afqmc_kp_stage_times")
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(self.STAGES)}
 
     def launch_count(self) -> int:
         n = ctypes.c_int(0)

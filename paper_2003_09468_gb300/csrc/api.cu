@@ -209,6 +209,8 @@ afqmc_status afqmc_kp_destroy(afqmc_kp_t h) {
   cudaError_t e = cudaDeviceSynchronize();
   mixed::destroy(h);
   free_all(h);
+  for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto ev : h->event_pool) cudaEventDestroy(ev);
   delete h;
   return from_cuda(e);
 }
@@ -309,6 +311,30 @@ afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular) {
 afqmc_status afqmc_kp_memory_bytes(afqmc_kp_t h, size_t* bytes) {
   if (!h || !bytes) return AFQMC_ERR_INVALID;
   *bytes = h->bytes;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_profile(afqmc_kp_t h, int enable) {
+  if (!h) return AFQMC_ERR_INVALID;
+  h->prof_on = enable != 0;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_stage_times(afqmc_kp_t h, double* ms, int* count) {
+  if (!h || !ms || !count) return AFQMC_ERR_INVALID;
+  for (int i = 0; i < AFQMC_NSTAGES; ++i) { ms[i] = 0.0; count[i] = 0; }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return from_cuda(e);
+  for (auto& r : h->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && r.stage >= 0 && r.stage < AFQMC_NSTAGES) {
+      ms[r.stage] += t;
+      count[r.stage] += 1;
+    }
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->recs.clear();
   return AFQMC_OK;
 }
 

@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256) lu_kernel(zc* S, zc* Sinv, zc* logdet, in
 }
 
 // Gh[w][s] = (phi S^-1)^T = S^-T phi^T  (N x NM)
-cudaError_t green(afqmc_kp* h, const zc* phi, cudaStream_t st) {
+static cudaError_t green_impl(afqmc_kp* h, const zc* phi, cudaStream_t st) {
   cudaError_t e = overlap(h, phi, st);
   if (e != cudaSuccess) return e;
   // perm workspace lives in the Gam buffer (unused until the backward pass)
@@ -392,6 +392,13 @@ cudaError_t green(afqmc_kp* h, const zc* phi, cudaStream_t st) {
   g.C = h->Gh; g.ldc = NM; g.sC[0] = (long)N * NM;
   g.nb[0] = 2 * h->W;
   return gemm_launch(h, g, st);
+}
+
+cudaError_t green(afqmc_kp* h, const zc* phi, cudaStream_t st) {
+  prof_begin(h, AFQMC_STAGE_GREEN, st);
+  cudaError_t e = green_impl(h, phi, st);
+  prof_end(h, st);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -660,20 +667,25 @@ static cudaError_t logdet_only(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cu
   return cudaGetLastError();
 }
 
-cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr,
-                      cudaStream_t st) {
+#define STAGE(stage, body)          \
+  do {                              \
+    prof_begin(h, stage, st);       \
+    cudaError_t e_ = (body);        \
+    prof_end(h, st);                \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+static cudaError_t vhs_build(afqmc_kp* h, cudaStream_t st) {
+  dim3 grid(h->nk * h->nk, (h->W + VWC - 1) / VWC);
+  vhs_kernel<<<grid, 256, sizeof(zc) * VWC * h->G, st>>>(h->L, h->y, h->V, h->kminus, h->nk, h->G, h->M, h->W);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+// T0 = E phi ; acc = T0 ; T_j = V T_{j-1} / j ; acc += T_j ; phi = E acc
+static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   cudaError_t e;
   const int NM = h->NM, N = h->N, W = h->W;
-  if ((e = green(h, phi, st)) != cudaSuccess) return e;
-  if ((e = cholesky_trace(h, st)) != cudaSuccess) return e;
-  if ((e = force_bias(h, x, h->xbar, st)) != cudaSuccess) return e;
-  {
-    dim3 grid(h->nk * h->nk, (W + VWC - 1) / VWC);
-    vhs_kernel<<<grid, 256, sizeof(zc) * VWC * h->G, st>>>(h->L, h->y, h->V, h->kminus, h->nk, h->G, h->M, W);
-    AFQMC_LAUNCHED(h);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // T0 = E phi ; acc = T0 ; T_j = V T_{j-1} / j ; acc += T_j ; phi = E acc
   if ((e = one_body(h, phi, h->T0, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(h->acc, h->T0, sizeof(zc) * (size_t)W * 2 * NM * N, cudaMemcpyDeviceToDevice, st)) !=
       cudaSuccess)
@@ -691,22 +703,45 @@ cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logd
     if ((e = gemm_launch(h, g, st)) != cudaSuccess) return e;
     zc* t = cur; cur = nxt; nxt = t;
   }
-  if ((e = one_body(h, h->acc, phi, st)) != cudaSuccess) return e;
+  return one_body(h, h->acc, phi, st);
+}
+
+static cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st) {
+  cudaError_t e;
   if ((e = logdet_only(h, phi, h->ld_new, h->sing_new, st)) != cudaSuccess) return e;
-  weight_kernel<<<W, 256, 0, st>>>(x, h->xbar, h->ld_old, h->ld_new, h->sing_old, h->sing_new, w,
-                                   do_qr ? nullptr : logdet, 2 * h->nk * h->G);
+  weight_kernel<<<h->W, 256, 0, st>>>(x, h->xbar, h->ld_old, h->ld_new, h->sing_old, h->sing_new, w, logdet,
+                                      2 * h->nk * h->G);
   AFQMC_LAUNCHED(h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+static cudaError_t trace_and_bias(afqmc_kp* h, const double* x, zc* xbar, cudaStream_t st) {
+  cudaError_t e = cholesky_trace(h, st);
+  if (e != cudaSuccess) return e;
+  return force_bias(h, x, xbar, st);
+}
+
+cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr,
+                      cudaStream_t st) {
+  cudaError_t e;
+  if ((e = green(h, phi, st)) != cudaSuccess) return e;
+  STAGE(AFQMC_STAGE_FORCE_BIAS, trace_and_bias(h, x, h->xbar, st));
+  STAGE(AFQMC_STAGE_VHS, vhs_build(h, st));
+  STAGE(AFQMC_STAGE_TAYLOR, taylor(h, phi, st));
+  STAGE(AFQMC_STAGE_WEIGHT, weights(h, phi, x, w, do_qr ? nullptr : logdet, st));
   if (do_qr) return orthonormalise(h, phi, logdet, st);
   return cudaSuccess;
 }
 
-cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
+static cudaError_t qr_and_logdet(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
   cudaError_t e = qr(h, phi, st);
   if (e != cudaSuccess) return e;
-  if (logdet) {
-    if ((e = logdet_only(h, phi, logdet, h->sing_new, st)) != cudaSuccess) return e;
-  }
+  if (logdet) return logdet_only(h, phi, logdet, h->sing_new, st);
+  return cudaSuccess;
+}
+
+cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
+  STAGE(AFQMC_STAGE_QR, qr_and_logdet(h, phi, logdet, st));
   return cudaSuccess;
 }
 
@@ -798,21 +833,34 @@ __global__ void ex_reduce_kernel(const zc* epart, zc* eloc, int per_walker) {
   if (threadIdx.x == 0) eloc[3 * w + 2] = s;
 }
 
-cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) {
-  cudaError_t e;
-  if ((e = green(h, phi, st)) != cudaSuccess) return e;
-  if ((e = cholesky_trace(h, st)) != cudaSuccess) return e;
+static cudaError_t e1_ec(afqmc_kp* h, zc* eloc, cudaStream_t st) {
   e1_ec_kernel<<<h->W, 256, 0, st>>>(h->AhH, h->Gh, h->X, h->minus, eloc, h->nk, h->M, h->n, h->G);
   AFQMC_LAUNCHED(h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+static cudaError_t exchange(afqmc_kp* h, cudaStream_t st) {
   dim3 grid(2 * h->W, h->nk, h->nk);
   exchange_fp64_kernel<<<grid, 256, sizeof(zc) * 2 * h->n * h->M, st>>>(h->LH, h->Gh, h->kminus, h->minus,
                                                                         h->epart, h->nk, h->G, h->M, h->n);
   AFQMC_LAUNCHED(h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+static cudaError_t ex_reduce(afqmc_kp* h, zc* eloc, cudaStream_t st) {
   ex_reduce_kernel<<<h->W, 256, 0, st>>>(h->epart, eloc, 2 * h->nk * h->nk);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
+}
+
+cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = green(h, phi, st)) != cudaSuccess) return e;
+  STAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+  STAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
+  STAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
+  STAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -915,11 +963,9 @@ __global__ void grad_h1_kernel(const zc* A, const zc* Gh, const zc* grad_e, zc* 
   }
 }
 
-cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
-                                  cudaStream_t st) {
+static cudaError_t backward_impl(afqmc_kp* h, const zc* grad_e, zc* grad_phi, zc* grad_h1, cudaStream_t st) {
   cudaError_t e;
   const int nk = h->nk, M = h->M, n = h->n, N = h->N, NM = h->NM, W = h->W;
-  if ((e = green(h, phi, st)) != cudaSuccess) return e;
   if (grad_h1) {
     grad_h1_kernel<<<nk, 256, 0, st>>>(h->A, h->Gh, grad_e, grad_h1, nk, M, n, W);
     AFQMC_LAUNCHED(h);
@@ -961,6 +1007,14 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
     g.nb[0] = 2 * W;
     if ((e = gemm_launch(h, g, st)) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
+                                  cudaStream_t st) {
+  cudaError_t e;
+  if ((e = green(h, phi, st)) != cudaSuccess) return e;
+  STAGE(AFQMC_STAGE_BACKWARD, backward_impl(h, grad_e, grad_phi, grad_h1, st));
   return cudaSuccess;
 }
 

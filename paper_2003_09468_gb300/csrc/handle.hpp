@@ -48,6 +48,14 @@ struct afqmc_kp {
 
   MixedState* mixed = nullptr;
 
+  // stage timing (afqmc_kp_profile)
+  bool prof_on = false;
+  struct Rec { int stage; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
+  int open_stage = -1;
+  cudaEvent_t open_event = nullptr;
+
   int launches = 0;     // kernel launches of the current call
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -55,6 +63,35 @@ struct afqmc_kp {
 
 // Launch bookkeeping: every kernel launch goes through AFQMC_LAUNCHED(h).
 #define AFQMC_LAUNCHED(h) ((h)->launches++)
+
+// Stage timing: no-ops unless afqmc_kp_profile enabled recording.
+inline cudaEvent_t prof_event(afqmc_kp* h) {
+  cudaEvent_t e = nullptr;
+  if (!h->event_pool.empty()) {
+    e = h->event_pool.back();
+    h->event_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  return e;
+}
+inline void prof_begin(afqmc_kp* h, int stage, cudaStream_t st) {
+  if (!h->prof_on) return;
+  cudaEvent_t e = prof_event(h);
+  if (!e) return;
+  cudaEventRecord(e, st);
+  h->open_stage = stage;
+  h->open_event = e;
+}
+inline void prof_end(afqmc_kp* h, cudaStream_t st) {
+  if (!h->prof_on || h->open_stage < 0) return;
+  cudaEvent_t e = prof_event(h);
+  if (!e) return;
+  cudaEventRecord(e, st);
+  h->recs.push_back({h->open_stage, h->open_event, e});
+  h->open_stage = -1;
+  h->open_event = nullptr;
+}
 
 // FP64 path (fp64.cu)
 namespace fp64 {
