@@ -382,7 +382,7 @@ static cudaError_t green_impl(afqmc_kp* h, const zc* phi, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   // perm workspace lives in the Gam buffer (unused until the backward pass)
   lu_kernel<<<2 * h->W, 256, 0, st>>>(h->S, h->Sinv, h->ld_old, h->sing_old, h->flags, h->N, 1,
-                                      reinterpret_cast<int*>(h->Gam));
+                                      reinterpret_cast<int*>(h->P));
   AFQMC_LAUNCHED(h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int N = h->N, NM = h->NM;
@@ -640,6 +640,13 @@ __global__ void __launch_bounds__(256) qr_kernel(zc* phi, zc* Qm_ws, int NM, int
   }
 }
 
+cudaError_t qr_with(afqmc_kp* h, zc* phi, zc* scratch, cudaStream_t st) {
+  size_t smem = (size_t)h->N * (2 * sizeof(zc) + sizeof(double));
+  qr_kernel<<<2 * h->W, 256, smem, st>>>(phi, scratch, h->NM, h->N);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
 static cudaError_t qr(afqmc_kp* h, zc* phi, cudaStream_t st) {
   size_t smem = (size_t)h->N * (2 * sizeof(zc) + sizeof(double));
   qr_kernel<<<2 * h->W, 256, smem, st>>>(phi, h->T1, h->NM, h->N);
@@ -658,13 +665,17 @@ static cudaError_t one_body(afqmc_kp* h, const zc* in, zc* out, cudaStream_t st)
   return gemm_launch(h, g, st);
 }
 
-static cudaError_t logdet_only(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+cudaError_t overlap_lu(afqmc_kp* h, const zc* phi, zc* ld, int* sing, int want_inv, cudaStream_t st) {
   cudaError_t e = overlap(h, phi, st);
   if (e != cudaSuccess) return e;
-  lu_kernel<<<2 * h->W, 256, 0, st>>>(h->S, h->Sinv, ld, sing, h->flags, h->N, 0,
-                                      reinterpret_cast<int*>(h->Gam));
+  lu_kernel<<<2 * h->W, 256, 0, st>>>(h->S, h->Sinv, ld, sing, h->flags, h->N, want_inv,
+                                      reinterpret_cast<int*>(h->P));
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
+}
+
+static cudaError_t logdet_only(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+  return overlap_lu(h, phi, ld, sing, 0, st);
 }
 
 #define STAGE(stage, body)          \
@@ -706,7 +717,7 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   return one_body(h, h->acc, phi, st);
 }
 
-static cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st) {
+cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st) {
   cudaError_t e;
   if ((e = logdet_only(h, phi, h->ld_new, h->sing_new, st)) != cudaSuccess) return e;
   weight_kernel<<<h->W, 256, 0, st>>>(x, h->xbar, h->ld_old, h->ld_new, h->sing_old, h->sing_new, w, logdet,

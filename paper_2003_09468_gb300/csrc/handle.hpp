@@ -106,4 +106,8 @@ cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st);
 cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st);
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi,
                                   zc* grad_h1, cudaStream_t st);
+// pieces shared with the mixed path
+cudaError_t overlap_lu(afqmc_kp* h, const zc* phi, zc* ld, int* sing, int want_inv, cudaStream_t st);
+cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st);
+cudaError_t qr_with(afqmc_kp* h, zc* phi, zc* scratch, cudaStream_t st);
 }  // namespace fp64

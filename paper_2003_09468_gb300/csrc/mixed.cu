@@ -1,16 +1,1028 @@
-// Tensor-core ("mixed") path: not yet built in this revision; create reports
-// AFQMC_ERR_UNSUPPORTED so callers fall back to nothing silently.
+// Tensor-core ("mixed") path of the k-point AFQMC walker step.
+//
+// Every contraction with the Cholesky vectors, the Taylor products and the
+// Green's-function product run as complex GEMMs on the tcgen05 tensor cores
+// with an fp16 hi/lo operand split and fp32 accumulation (tc_gemm.cuh).  The
+// overlap matrix, its LU factorisation, inverse and log-determinant, the
+// weights, the QR and every energy sum stay in FP64.  The identity part of both
+// one-body half steps and of the Taylor series is carried exactly in FP64;
+// only the corrections pass through reduced precision.
+//
+// Exchange energy.  Sec. 2.2 notes that a half-rotated two-electron tensor can
+// be precontracted to cut the cost of the energy by at least n_gamma, at an
+// O(N^2 M^2) memory price the paper's 16 GB GPUs could not pay.  With 288 GB of
+// HBM that tensor fits, so it is built once at create time, in FP64, for the
+// canonical member of every pair of terms (Q, k, k') <-> (-Q, k'-Q, k) of Eq.
+// kp_el (the pair contributes twice the same value):
+//   Z_t[(a,s)][(b,r)] = sum_g LH[Q,k,g,a,r] LH[-Q,kx,g,b,s],   kx = k' - Q,
+// and the exchange becomes, per walker-spin ws,
+//   EX = -1/2 sum_t w_t sum_{(a,s)} ( sum_{(b,r)} Gh[(kx,b),(k-Q,r)] Z_t[(a,s),(b,r)] ) Gh[(k,a),(kx+Q,s)]
+// i.e. one tensor-core GEMM per triple (rows = walker-spins) with a dot-product
+// epilogue.  Expanding T1 and T2 of Sec. 3.2 steps 2(a)-(c) gives exactly this
+// sum.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
 #include "mixed.hpp"
+#include "tc_gemm.cuh"
+
+struct MixedState {
+  int Np, NMp, Mp, Gp, nMp, nM, WS, T;
+  // walker-dependent operands (split planes, fp16) and their scales
+  __half* phi_sp = nullptr;   float* s_phi = nullptr;   // [WS][4][NM][Np]
+  __half* sinvt_sp = nullptr; float* s_sinv = nullptr;  // [WS][4][N][Np]
+  float2* g32 = nullptr;                                 // [Nk][Nk][WS][n][Mp]
+  __half* g_sp = nullptr;     float* s_g = nullptr;     // [4][Nk][Nk][WS][n][Mp]
+  __half* gsum_sp = nullptr;  float* s_gsum = nullptr;  // [4][Nk][Nk][W][n][Mp]
+  __half* y_sp = nullptr;     float* s_y = nullptr;     // [4][Nk][W][Gp], s_y[Q][W]
+  __half* v_sp = nullptr;                                // [W][4][NM][NMp]
+  __half* t_sp[2] = {nullptr, nullptr}; float* s_t = nullptr;  // [W][4][2N][NMp]
+  double2* acc = nullptr;                                // [W][2N][NM]
+  double2* xpart = nullptr;                              // [T][ntile][WS]
+  double2* xk = nullptr;                                 // [Nk][W][Nk][G] per-k-block Cholesky traces
+  // static operands
+  __half* lh_sp = nullptr;    float* s_lh = nullptr;    // [4][Nk][Nk][G][n][Mp], s_lh[Q][G]
+  __half* lt_sp = nullptr;    float* s_l = nullptr;     // [4][Nk][Nk][M*M][Gp], s_l[Q][G]
+  __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][T][nM][n*Mp]
+  int4* tri = nullptr;                                   // [T] (Q, k, kx, weight)
+  float2* dhalf = nullptr;                               // [Nk][M][M] exp(-dt/2 H1') - I
+  zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
+  CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
+  std::vector<void*> allocs;
+};
 
 namespace mixed {
-afqmc_status create(afqmc_kp*, cudaStream_t) { return AFQMC_ERR_UNSUPPORTED; }
-void destroy(afqmc_kp*) {}
-cudaError_t set_one_body(afqmc_kp*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t force_bias(afqmc_kp*, const zc*, zc*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t propagate(afqmc_kp*, zc*, const double*, double*, zc*, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t orthonormalise(afqmc_kp*, zc*, zc*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t local_energy(afqmc_kp*, const zc*, zc*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t local_energy_backward(afqmc_kp*, const zc*, const zc*, zc*, zc*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+// Output tile width of the precise GEMM (tc_gemm.cuh): 64 columns.
+constexpr int BN = tcg::BNP;
+constexpr int STAGES = 4;
+constexpr float SCALE_TARGET = 4096.f;
+constexpr float V_SCALE = 1024.f;   // fixed scale of vHS entries (|V| < 64 fits fp16 hi)
+constexpr int ZCTAS = 304;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pow2_scale(double maxabs) {
+  if (!(maxabs > 0.0) || !isfinite(maxabs)) return 1.f;
+  int e;
+  frexp((double)SCALE_TARGET / maxabs, &e);  // 2^(e-1) <= target/max < 2^e
+  e -= 1;
+  e = max(-100, min(100, e));
+  return (float)ldexp(1.0, e);
 }
+
+// x*s split into hi = fp16(x*s) and lo = fp16(x*s - hi)
+__device__ __forceinline__ void split_val(double v, float s, __half& hi, __half& lo) {
+  const double xs = v * (double)s;
+  hi = __double2half(xs);
+  lo = __double2half(xs - (double)__half2float(hi));
+}
+__device__ __forceinline__ void put4(__half* base, size_t plane_stride, size_t idx, double re, double im, float s) {
+  __half h, l;
+  split_val(re, s, h, l);
+  base[idx] = h;
+  base[plane_stride + idx] = l;
+  split_val(im, s, h, l);
+  base[2 * plane_stride + idx] = h;
+  base[3 * plane_stride + idx] = l;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) m = fmax(m, red[i]);
+  return m;
+}
+__device__ __forceinline__ double cabs_d(zc v) { return fmax(fabs(v.x), fabs(v.y)); }
+__device__ __forceinline__ double cabs_f(float2 v) { return fmax(fabs((double)v.x), fabs((double)v.y)); }
+
+template <typename T>
+static cudaError_t dalloc(afqmc_kp* h, T** p, size_t count, bool zero, cudaStream_t st) {
+  void* q = nullptr;
+  size_t b = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) return e;
+  h->mixed->allocs.push_back(q);
+  h->bytes += b;
+  *p = static_cast<T*>(q);
+  if (zero) return cudaMemsetAsync(q, 0, b, st);
+  return cudaSuccess;
+}
+
+static inline int rup(int x, int m) { return (x + m - 1) / m * m; }
+static inline int cdiv(int x, int m) { return (x + m - 1) / m; }
+
+}  // namespace mixed
+
+// ---------------------------------------------------------------------------
+// tensor maps (driver entry point fetched through the runtime)
+// ---------------------------------------------------------------------------
+namespace tcg {
+cudaError_t make_map(CUtensorMap* map, void* base, const MapSpec& s) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  for (int i = 0; i < 5; ++i) { dims[i] = s.dims[i]; box[i] = s.box[i]; }
+  for (int i = 0; i < 4; ++i) strides[i] = s.strides[i];
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace tcg
+
+namespace mixed {
+
+// Build a map for an array of fp16 elements with logical dims d[0..4] (d[0]
+// contiguous) and element strides e[1..4].
+static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64_t> d,
+                        std::initializer_list<uint64_t> estride, uint32_t rows) {
+  tcg::MapSpec s;
+  auto di = d.begin();
+  auto ei = estride.begin();
+  for (int i = 0; i < 5; ++i) s.dims[i] = di[i];
+  for (int i = 0; i < 4; ++i) s.strides[i] = ei[i] * sizeof(__half);
+  s.box[0] = 32;
+  s.box[1] = rows;
+  s.box[2] = 4;
+  s.box[3] = 1;
+  s.box[4] = 1;
+  return tcg::make_map(m, base, s);
+}
+
+// ---------------------------------------------------------------------------
+// GEMM policies
+// ---------------------------------------------------------------------------
+struct NoRow {};
+
+// Gh[ws] = S^-T phi^T : rows i = (k1, a), cols (k2, p); written to g32 in tile layout.
+struct GreenP {
+  int tiles, kchunks;
+  int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
+  const float* s_sinv;
+  const float* s_phi;
+  float2* g32;
+  typedef float Row;  // inverse scale of the row's walker-spin
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
+    tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, b, 0}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int b, int, int, int) const { st = 1.f / (s_sinv[b] * s_phi[b]); }
+  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
+    const int i = mt * 128 + r;
+    if (i >= N) return;
+    const int k1 = i / n, a = i % n;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int col = nt * BN + c0 + c;
+      if (col < NM) {
+        const int k2 = col / M, p = col % M;
+        g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2(re[c] * st, im[c] * st);
+      }
+    }
+  }
+  __device__ void row_end(Row&, int, int, int, int) const {}
+};
+
+// Partial Cholesky trace of one k block: Xk[k][w][Q][g] = sum_{a,r} LH[Q,k,g,a,r] Gsum_w[(k,a),(k-Q,r)].
+// Splitting the k sum across tiles keeps every fp32 running sum short; the k
+// blocks are summed in FP64 by xsum_kernel.
+struct ForceBiasP {
+  int tiles, kchunks;
+  int mt_n, nt_n, W, G, nk;
+  const int* kminus;
+  const float* s_gsum;
+  const float* s_lh;
+  double2* Xk;  // [Nk(k)][W][Nk(Q)][G]
+  typedef float Row;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);   // b = Q * nk + k
+  }
+  __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
+    const int Q = b / nk, k = b % nk, c0 = kc * 32;
+    tcg::Coords c = {{c0, mt * 128, 0, kminus[k * nk + Q], k}, {c0, nt * BN, 0, k, Q}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int, int mt, int, int r) const {
+    const int w = mt * 128 + r;
+    st = w < W ? 1.f / s_gsum[w] : 0.f;
+  }
+  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
+    const int w = mt * 128 + r;
+    if (w >= W) return;
+    const int Q = b / nk, k = b % nk;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int g = nt * BN + c0 + c;
+      if (g < G) {
+        const double f = (double)st / (double)s_lh[Q * G + g];
+        Xk[(((size_t)k * W + w) * nk + Q) * G + g] = make_double2(re[c] * f, im[c] * f);
+      }
+    }
+  }
+  __device__ void row_end(Row&, int, int, int, int) const {}
+};
+
+// X[w][Q][g] = sum_k Xk[k][w][Q][g]  (FP64, fixed order)
+__global__ void xsum_kernel(const double2* Xk, zc* X, int nk, size_t per) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < per; e += (size_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < nk; ++k) {
+      const double2 v = Xk[(size_t)k * per + e];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    X[e] = s;
+  }
+}
+
+// V[w][(k,p)][(k-Q,r)] = sum_g y[w,Q,g] L[Q,k,g,p,r]  -> split planes with a fixed scale
+struct VhsP {
+  int tiles, kchunks;
+  int mt_n, nt_n, W, M, nk, NM, NMp;
+  const int* kminus;
+  const float* s_y;  // [Q][W]
+  __half* v_sp;
+  int* overflow;
+  typedef float Row;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
+    const int Q = b / nk, k = b % nk;
+    tcg::Coords c = {{kc * 32, mt * 128, 0, Q, 0}, {kc * 32, nt * BN, 0, k, Q}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int b, int mt, int, int r) const {
+    const int Q = b / nk, w = mt * 128 + r;
+    st = w < W ? V_SCALE / s_y[Q * W + w] : 0.f;
+  }
+  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
+    const int w = mt * 128 + r;
+    if (w >= W) return;
+    const int Q = b / nk, k = b % nk, kq = kminus[k * nk + Q];
+    const size_t ps = (size_t)NM * NMp;
+    __half* base = v_sp + (size_t)w * 4 * ps;
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int pr = nt * BN + c0 + c;
+      if (pr < M * M) {
+        const int p = pr / M, rr = pr % M;
+        const size_t idx = (size_t)(k * M + p) * NMp + kq * M + rr;
+        const float vr = re[c] * st, vi = im[c] * st;
+        bad |= !(fabsf(vr) < 60000.f && fabsf(vi) < 60000.f);
+        put4(base, ps, idx, vr, vi, 1.f);
+      }
+    }
+    if (bad) atomicExch(overflow, 1);
+  }
+  __device__ void row_end(Row&, int, int, int, int) const {}
+};
+
+// One Taylor term: T_j[w] = V[w] T_{j-1}[w] / j in transposed form (rows j' = (spin, column)).
+struct TaylorP {
+  int tiles, kchunks;
+  int mt_n, nt_n, R, NM, NMp;
+  float inv_j;
+  const float* s_t;
+  double2* acc;       // [W][R][NM]
+  __half* t_next;     // [W][4][R][NMp]
+  typedef float Row;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
+    tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, b, 0}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int b, int, int, int) const { st = inv_j / V_SCALE; }
+  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
+    const int j = mt * 128 + r;
+    if (j >= R) return;
+    const float s = s_t[b];
+    const size_t ps = (size_t)R * NMp;
+    __half* tb = t_next + (size_t)b * 4 * ps;
+    double2* ab = acc + ((size_t)b * R + j) * NM;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int i = nt * BN + c0 + c;
+      if (i < NM) {
+        // D carries the operand scales s_t (A) and V_SCALE (B); st removes V_SCALE and applies 1/j
+        const double tr = (double)re[c] * st, ti = (double)im[c] * st;   // = T_j * s_t
+        double2 a = ab[i];
+        a.x += tr / s;
+        a.y += ti / s;
+        ab[i] = a;
+        put4(tb, ps, (size_t)j * NMp + i, tr, ti, 1.f);
+      }
+    }
+  }
+  __device__ void row_end(Row&, int, int, int, int) const {}
+};
+
+// Exchange: rows = walker-spins, cols = (a, s) of Z_t; epilogue dots with Gh[(k,a),(kx+Q,s)].
+struct ExchangeRow {
+  double re, im;
+  float inv;
+  const float2* g2;
+};
+struct ExchangeP {
+  int tiles, kchunks;
+  int mt_n, nt_n, WS, nk, n, M, Mp, nM;
+  const int* kminus;
+  const int* minus;
+  const int4* tri;
+  const float* s_g;
+  const float* s_z;
+  const float2* g32;
+  double2* xpart;  // [T][nt_n][WS]
+  typedef ExchangeRow Row;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ tcg::Coords coords(int t, int mt, int nt, int kc) const {
+    const int4 q = tri[t];  // (Q, k, kx, weight)
+    tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, t, 0}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int t, int mt, int, int r) const {
+    const int ws = mt * 128 + r;
+    st.re = st.im = 0.0;
+    if (ws >= WS) { st.inv = 0.f; st.g2 = nullptr; return; }
+    const int4 q = tri[t];
+    const int kxq = kminus[q.z * nk + minus[q.x]];  // kx + Q
+    st.inv = 1.f / (s_g[ws] * s_z[t]);
+    st.g2 = g32 + (((size_t)q.y * nk + kxq) * WS + ws) * n * Mp;
+  }
+  __device__ void chunk(Row& st, int, int, int nt, int, int c0, const float* re, const float* im) const {
+    if (!st.g2) return;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int col = nt * BN + c0 + c;
+      if (col < nM) {
+        const int a = col / M, s = col % M;
+        const float2 g = st.g2[a * Mp + s];
+        const double yr = (double)re[c] * st.inv, yi = (double)im[c] * st.inv;
+        st.re += yr * g.x - yi * g.y;
+        st.im += yr * g.y + yi * g.x;
+      }
+    }
+  }
+  __device__ void row_end(Row& st, int t, int mt, int nt, int r) const {
+    const int ws = mt * 128 + r;
+    if (ws < WS) xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2(st.re, st.im);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// conversion kernels
+// ---------------------------------------------------------------------------
+
+// phi [WS][NM][N] (FP64) -> phi_sp [WS][4][NM][Np]
+__global__ void split_phi_kernel(const zc* phi, __half* out, float* scale, int NM, int N, int Np) {
+  const int ws = blockIdx.x;
+  __shared__ double red[32];
+  const zc* p = phi + (size_t)ws * NM * N;
+  double m = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)NM * N; e += blockDim.x) m = fmax(m, cabs_d(p[e]));
+  m = block_max(m, red);
+  const float s = pow2_scale(m);
+  if (threadIdx.x == 0) scale[ws] = s;
+  const size_t ps = (size_t)NM * Np;
+  __half* o = out + (size_t)ws * 4 * ps;
+  for (size_t e = threadIdx.x; e < (size_t)NM * N; e += blockDim.x) {
+    const size_t i = e / N, j = e % N;
+    put4(o, ps, i * Np + j, p[e].x, p[e].y, s);
+  }
+}
+
+// Sinv [WS][N][N] (FP64) -> split planes of Sinv^T [WS][4][N][Np]
+__global__ void split_sinvT_kernel(const zc* Sinv, __half* out, float* scale, int N, int Np) {
+  const int ws = blockIdx.x;
+  __shared__ double red[32];
+  const zc* p = Sinv + (size_t)ws * N * N;
+  double m = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) m = fmax(m, cabs_d(p[e]));
+  m = block_max(m, red);
+  const float s = pow2_scale(m);
+  if (threadIdx.x == 0) scale[ws] = s;
+  const size_t ps = (size_t)N * Np;
+  __half* o = out + (size_t)ws * 4 * ps;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i = e / N, j = e % N;   // out row i, col j = Sinv[j][i]
+    const zc v = p[(size_t)j * N + i];
+    put4(o, ps, (size_t)i * Np + j, v.x, v.y, s);
+  }
+}
+
+// g32 [Nk][Nk][WS][n][Mp] -> g_sp (per walker-spin scale) and gsum_sp (spin sum, per walker scale)
+__global__ void split_green_kernel(const float2* g32, __half* gsp, float* s_g, __half* gsum, float* s_gsum, int nk,
+                                   int W, int nMp) {
+  const int w = blockIdx.x;
+  const int WS = 2 * W;
+  __shared__ double red[32];
+  const size_t per = (size_t)nk * nk * nMp;
+  double m0 = 0.0, m1 = 0.0, ms = 0.0;
+  for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+    const size_t blk = e / nMp, off = e % nMp;
+    const float2 a = g32[(blk * WS + 2 * w) * nMp + off];
+    const float2 b = g32[(blk * WS + 2 * w + 1) * nMp + off];
+    m0 = fmax(m0, cabs_f(a));
+    m1 = fmax(m1, cabs_f(b));
+    ms = fmax(ms, fmax(fabs((double)a.x + b.x), fabs((double)a.y + b.y)));
+  }
+  m0 = block_max(m0, red);
+  m1 = block_max(m1, red);
+  ms = block_max(ms, red);
+  const float s0 = pow2_scale(m0), s1 = pow2_scale(m1), ss = pow2_scale(ms);
+  if (threadIdx.x == 0) {
+    s_g[2 * w] = s0;
+    s_g[2 * w + 1] = s1;
+    s_gsum[w] = ss;
+  }
+  const size_t psg = (size_t)nk * nk * WS * nMp, pss = (size_t)nk * nk * W * nMp;
+  for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+    const size_t blk = e / nMp, off = e % nMp;
+    const float2 a = g32[(blk * WS + 2 * w) * nMp + off];
+    const float2 b = g32[(blk * WS + 2 * w + 1) * nMp + off];
+    put4(gsp, psg, (blk * WS + 2 * w) * nMp + off, a.x, a.y, s0);
+    put4(gsp, psg, (blk * WS + 2 * w + 1) * nMp + off, b.x, b.y, s1);
+    put4(gsum, pss, (blk * W + w) * nMp + off, (double)a.x + b.x, (double)a.y + b.y, ss);
+  }
+}
+
+// y [W][Nk][G] (zc, carries sqrt(dt)) -> y_sp [4][Nk][W][Gp] of y / s_l[Q][g], scale s_y[Q][W]
+__global__ void split_y_kernel(const zc* y, const float* s_l, __half* out, float* s_y, int nk, int W, int G, int Gp) {
+  const int Q = blockIdx.x, w = blockIdx.y;
+  __shared__ double red[32];
+  const zc* yp = y + ((size_t)w * nk + Q) * G;
+  double m = 0.0;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const double f = 1.0 / (double)s_l[Q * G + g];
+    m = fmax(m, cabs_d(yp[g]) * f);
+  }
+  m = block_max(m, red);
+  const float s = pow2_scale(m);
+  if (threadIdx.x == 0) s_y[Q * W + w] = s;
+  const size_t ps = (size_t)nk * W * Gp;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const double f = 1.0 / (double)s_l[Q * G + g];
+    put4(out, ps, ((size_t)Q * W + w) * Gp + g, yp[g].x * f, yp[g].y * f, s);
+  }
+}
+
+// acc[w][s*N + j][(k,p)] = phi[w][s][(k,p)][j] + sum_q D[k][p][q] phi[w][s][(k,q)][j]
+// grid (k, ws, j-chunk of 64); the correction runs in fp32, the identity part in FP64.
+__global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* acc, int nk, int M, int N, int NM) {
+  const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
+  const int w = ws >> 1, sp = ws & 1;
+  const int jn = min(64, N - j0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  zc* blk = reinterpret_cast<zc*>(smraw);               // [M][64]   (16-byte entries first)
+  float2* D = reinterpret_cast<float2*>(blk + M * 64);  // [M][M]
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
+  const zc* src = phi + (size_t)ws * NM * N;
+  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
+    const int q = e / jn, j = e % jn;
+    blk[q * 64 + j] = src[(size_t)(k * M + q) * N + j0 + j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
+    const int j = e / M, p = e % M;
+    float cr = 0.f, ci = 0.f;
+    for (int q = 0; q < M; ++q) {
+      const float2 d = D[p * M + q];
+      const zc b = blk[q * 64 + j];
+      const float br = (float)b.x, bi = (float)b.y;
+      cr = fmaf(d.x, br, fmaf(-d.y, bi, cr));
+      ci = fmaf(d.x, bi, fmaf(d.y, br, ci));
+    }
+    const zc id = blk[p * 64 + j];
+    acc[((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p] = make_double2(id.x + cr, id.y + ci);
+  }
+}
+
+// acc [W][R][NM] -> t_sp [W][4][R][NMp] with a per-walker scale
+__global__ void split_acc_kernel(const double2* acc, __half* out, float* s_t, int R, int NM, int NMp) {
+  const int w = blockIdx.x;
+  __shared__ double red[32];
+  const double2* a = acc + (size_t)w * R * NM;
+  double m = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)R * NM; e += blockDim.x) m = fmax(m, fmax(fabs(a[e].x), fabs(a[e].y)));
+  m = block_max(m, red);
+  const float s = pow2_scale(m);
+  if (threadIdx.x == 0) s_t[w] = s;
+  const size_t ps = (size_t)R * NMp;
+  __half* o = out + (size_t)w * 4 * ps;
+  for (size_t e = threadIdx.x; e < (size_t)R * NM; e += blockDim.x) {
+    const size_t j = e / NM, i = e % NM;
+    put4(o, ps, j * NMp + i, a[e].x, a[e].y, s);
+  }
+}
+
+// phi[w][s][(k,p)][j] = acc + sum_q D[k][p][q] acc[(k,q)] with acc[w][s*N + j][(k, .)]
+__global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* phi, int nk, int M, int N, int NM) {
+  const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
+  const int w = ws >> 1, sp = ws & 1;
+  const int jn = min(64, N - j0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* blk = reinterpret_cast<double2*>(smraw);       // [64][M]   (16-byte entries first)
+  float2* D = reinterpret_cast<float2*>(blk + 64 * M);    // [M][M]
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
+  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
+    const int j = e / M, q = e % M;
+    blk[j * M + q] = acc[((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + q];
+  }
+  __syncthreads();
+  zc* dst = phi + (size_t)ws * NM * N;
+  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
+    const int p = e / jn, j = e % jn;
+    float cr = 0.f, ci = 0.f;
+    for (int q = 0; q < M; ++q) {
+      const float2 d = D[p * M + q];
+      const double2 b = blk[j * M + q];
+      const float br = (float)b.x, bi = (float)b.y;
+      cr = fmaf(d.x, br, fmaf(-d.y, bi, cr));
+      ci = fmaf(d.x, bi, fmaf(d.y, br, ci));
+    }
+    const double2 id = blk[j * M + p];
+    dst[(size_t)(k * M + p) * N + j0 + j] = make_double2(id.x + cr, id.y + ci);
+  }
+}
+
+// dhalf = Ehalf - I in fp32
+__global__ void dhalf_kernel(const zc* Ehalf, float2* d, int nk, int M) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nk * M * M;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)((e / M) % M), q = (int)(e % M);
+    d[e] = make_float2((float)(Ehalf[e].x - (p == q ? 1.0 : 0.0)), (float)Ehalf[e].y);
+  }
+}
+
+// E1 and EC per walker from the fp32 Green's function and the FP64 X.
+__global__ void e1_ec_mixed_kernel(const zc* AhH, const float2* g32, const zc* X, const int* minus, zc* eloc, int nk,
+                                   int M, int n, int Mp, int G, int WS) {
+  const int w = blockIdx.x;
+  __shared__ zc red[32];
+  zc s = zzero();
+  for (int e = threadIdx.x; e < 2 * nk * n * M; e += blockDim.x) {
+    const int q = e % M, a = (e / M) % n, k = (e / (M * n)) % nk, sp = e / (M * n * nk);
+    const float2 g = g32[((((size_t)k * nk + k) * WS + 2 * w + sp) * n + a) * Mp + q];
+    s = zfma(AhH[((size_t)k * n + a) * M + q], zmake(g.x, g.y), s);
+  }
+  const zc e1 = block_zsum(s, red);
+  zc c = zzero();
+  for (int e = threadIdx.x; e < nk * G; e += blockDim.x) {
+    const int g = e % G, Q = e / G;
+    c = zfma(X[((size_t)w * nk + Q) * G + g], X[((size_t)w * nk + minus[Q]) * G + g], c);
+  }
+  const zc ec = block_zsum(c, red);
+  if (threadIdx.x == 0) {
+    eloc[3 * w + 0] = e1;
+    eloc[3 * w + 1] = zscale(ec, 0.5);
+  }
+}
+
+// EX[w] = -1/2 sum_t weight_t sum_nt sum_s xpart[t][nt][2w+s]
+__global__ void ex_reduce_mixed_kernel(const double2* xpart, const int4* tri, zc* eloc, int T, int nt_n, int WS) {
+  const int w = blockIdx.x;
+  __shared__ zc red[32];
+  zc s = zzero();
+  for (int e = threadIdx.x; e < T * nt_n; e += blockDim.x) {
+    const int t = e / nt_n;
+    const double wt = (double)tri[t].w;
+    const double2 a = xpart[(size_t)e * WS + 2 * w];
+    const double2 b = xpart[(size_t)e * WS + 2 * w + 1];
+    s = zadd(s, zmake(wt * (a.x + b.x), wt * (a.y + b.y)));
+  }
+  s = block_zsum(s, red);
+  if (threadIdx.x == 0) eloc[3 * w + 2] = zscale(s, -0.5);
+}
+
+// ---------------------------------------------------------------------------
+// create-time kernels
+// ---------------------------------------------------------------------------
+
+// s_lh[Q][g] from max over k, a, r of |LH|; s_l[Q][g] from max over k, p, r of |L|
+__global__ void static_scales_kernel(const zc* L, const zc* LH, float* s_l, float* s_lh, int nk, int G, int M, int n) {
+  const int Q = blockIdx.x, g = blockIdx.y;
+  __shared__ double red[32];
+  double ml = 0.0, mh = 0.0;
+  for (int k = 0; k < nk; ++k) {
+    const zc* lp = L + (((size_t)Q * nk + k) * G + g) * M * M;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) ml = fmax(ml, cabs_d(lp[e]));
+    const zc* hp = LH + (((size_t)Q * nk + k) * G + g) * n * M;
+    for (int e = threadIdx.x; e < n * M; e += blockDim.x) mh = fmax(mh, cabs_d(hp[e]));
+  }
+  ml = block_max(ml, red);
+  mh = block_max(mh, red);
+  if (threadIdx.x == 0) {
+    s_l[Q * G + g] = pow2_scale(ml);
+    s_lh[Q * G + g] = pow2_scale(mh);
+  }
+}
+
+// lh_sp[4][Q][k][g][a][Mp] and lt_sp[4][Q][k][(p,r)][Gp]; grid (Q*nk + k)
+__global__ void static_split_kernel(const zc* L, const zc* LH, const float* s_l, const float* s_lh, __half* lh_sp,
+                                    __half* lt_sp, int nk, int G, int Gp, int M, int Mp, int n) {
+  const int b = blockIdx.x, Q = b / nk;
+  const size_t lh_ps = (size_t)nk * nk * G * n * Mp, lt_ps = (size_t)nk * nk * M * M * Gp;
+  const zc* hp = LH + (size_t)b * G * n * M;
+  for (int e = threadIdx.x; e < G * n * M; e += blockDim.x) {
+    const int g = e / (n * M), a = (e / M) % n, r = e % M;
+    put4(lh_sp, lh_ps, (((size_t)b * G + g) * n + a) * Mp + r, hp[e].x, hp[e].y, s_lh[Q * G + g]);
+  }
+  const zc* lp = L + (size_t)b * G * M * M;
+  for (int e = threadIdx.x; e < G * M * M; e += blockDim.x) {
+    const int pr = e / G, g = e % G;  // g fastest in the output
+    const zc v = lp[(size_t)g * M * M + pr];
+    put4(lt_sp, lt_ps, ((size_t)b * M * M + pr) * Gp + g, v.x, v.y, s_l[Q * G + g]);
+  }
+}
+
+// Z_t[(a,s)][(b,r)] = sum_g LH[Q,k,g,a,r] LH[-Q,kx,g,b,s] in FP64, split per triple.
+__global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, zc* scratch, __half* z_sp,
+                               float* s_z, int T, int nk, int G, int M, int n, int Mp) {
+  const int nM = n * M;
+  const size_t per = (size_t)nM * nM;
+  zc* buf = scratch + (size_t)blockIdx.x * per;
+  __shared__ double red[32];
+  const size_t ps = (size_t)T * nM * n * Mp;
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const int4 q = tri[t];
+    const zc* L1 = LH + ((size_t)q.x * nk + q.y) * G * nM;            // LH[Q][k]
+    const zc* L2 = LH + ((size_t)minus[q.x] * nk + q.z) * G * nM;     // LH[-Q][kx]
+    double m = 0.0;
+    for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+      // e = ((a*M + s)*n + b)*M + r
+      const int r = (int)(e % M), b = (int)((e / M) % n), s = (int)((e / ((size_t)M * n)) % M),
+                a = (int)(e / ((size_t)M * n * M));
+      zc acc = zzero();
+      for (int g = 0; g < G; ++g)
+        acc = zfma(L1[(size_t)g * nM + a * M + r], L2[(size_t)g * nM + b * M + s], acc);
+      buf[e] = acc;
+      m = fmax(m, cabs_d(acc));
+    }
+    m = block_max(m, red);
+    const float sc = pow2_scale(m);
+    if (threadIdx.x == 0) s_z[t] = sc;
+    for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+      const int r = (int)(e % M), b = (int)((e / M) % n), s = (int)((e / ((size_t)M * n)) % M),
+                a = (int)(e / ((size_t)M * n * M));
+      const size_t idx = ((size_t)t * nM + a * M + s) * (n * Mp) + b * Mp + r;
+      put4(z_sp, ps, idx, buf[e].x, buf[e].y, sc);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+#define MTRY(x)                         \
+  do {                                  \
+    cudaError_t e_ = (x);               \
+    if (e_ != cudaSuccess) return e_;   \
+  } while (0)
+
+template <class P>
+static cudaError_t run_gemm(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
+  return tcg::launch_precise<STAGES>(a, b, p, err, st);
+}
+
+static cudaError_t set_smem_attr(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static size_t onebody_smem(const afqmc_kp* h) {
+  return sizeof(float2) * h->M * h->M + sizeof(zc) * h->M * 64;
+}
+
+static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  const int nk = h->nk, M = h->M, n = h->n, G = h->G, W = h->W, N = h->N, NM = h->NM;
+  m->Np = rup(N, 32);
+  m->NMp = rup(NM, 32);
+  m->Mp = rup(M, 32);
+  m->Gp = rup(G, 32);
+  m->nMp = n * m->Mp;
+  m->nM = n * M;
+  m->WS = 2 * W;
+  const int Np = m->Np, NMp = m->NMp, Mp = m->Mp, Gp = m->Gp, nMp = m->nMp, nM = m->nM, WS = m->WS;
+  // canonical triples (Q, k, kx) <-> (-Q, kx, k)
+  std::vector<int4> tri;
+  for (int Q = 0; Q < nk; ++Q)
+    for (int k = 0; k < nk; ++k)
+      for (int kx = 0; kx < nk; ++kx) {
+        const int mQ = h->h_minus[Q];
+        const bool self = (mQ == Q) && (kx == k);
+        const bool canon = (Q < mQ) || (Q == mQ && k <= kx);
+        if (canon) tri.push_back(make_int4(Q, k, kx, self ? 1 : 2));
+      }
+  m->T = (int)tri.size();
+  const int T = m->T;
+  const int ntx = cdiv(nM, BN);
+
+  MTRY(dalloc(h, &m->phi_sp, (size_t)WS * 4 * NM * Np, true, st));
+  MTRY(dalloc(h, &m->s_phi, WS, true, st));
+  MTRY(dalloc(h, &m->sinvt_sp, (size_t)WS * 4 * N * Np, true, st));
+  MTRY(dalloc(h, &m->s_sinv, WS, true, st));
+  MTRY(dalloc(h, &m->g32, (size_t)nk * nk * WS * nMp, true, st));
+  MTRY(dalloc(h, &m->g_sp, (size_t)4 * nk * nk * WS * nMp, true, st));
+  MTRY(dalloc(h, &m->s_g, WS, true, st));
+  MTRY(dalloc(h, &m->gsum_sp, (size_t)4 * nk * nk * W * nMp, true, st));
+  MTRY(dalloc(h, &m->s_gsum, W, true, st));
+  MTRY(dalloc(h, &m->y_sp, (size_t)4 * nk * W * Gp, true, st));
+  MTRY(dalloc(h, &m->s_y, (size_t)nk * W, true, st));
+  MTRY(dalloc(h, &m->v_sp, (size_t)W * 4 * NM * NMp, true, st));
+  MTRY(dalloc(h, &m->t_sp[0], (size_t)W * 4 * 2 * N * NMp, true, st));
+  MTRY(dalloc(h, &m->t_sp[1], (size_t)W * 4 * 2 * N * NMp, true, st));
+  MTRY(dalloc(h, &m->s_t, W, true, st));
+  MTRY(dalloc(h, &m->acc, (size_t)W * 2 * N * NM, true, st));
+  MTRY(dalloc(h, &m->xpart, (size_t)T * ntx * WS, true, st));
+  MTRY(dalloc(h, &m->xk, (size_t)nk * W * nk * G, true, st));
+  MTRY(dalloc(h, &m->lh_sp, (size_t)4 * nk * nk * G * nMp, true, st));
+  MTRY(dalloc(h, &m->s_lh, (size_t)nk * G, true, st));
+  MTRY(dalloc(h, &m->lt_sp, (size_t)4 * nk * nk * M * M * Gp, true, st));
+  MTRY(dalloc(h, &m->s_l, (size_t)nk * G, true, st));
+  MTRY(dalloc(h, &m->z_sp, (size_t)4 * T * nM * nMp, true, st));
+  MTRY(dalloc(h, &m->s_z, T, true, st));
+  MTRY(dalloc(h, &m->tri, T, false, st));
+  MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
+  const int zctas = std::min(T, ZCTAS);
+  MTRY(dalloc(h, &m->zscratch, (size_t)zctas * nM * nM, false, st));
+  MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
+
+  // static split operands and the precontracted exchange tensor
+  static_scales_kernel<<<dim3(nk, G), 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, nk, G, M, n);
+  AFQMC_LAUNCHED(h);
+  static_split_kernel<<<nk * nk, 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, m->lh_sp, m->lt_sp, nk, G, Gp, M, Mp,
+                                               n);
+  AFQMC_LAUNCHED(h);
+  z_build_kernel<<<zctas, 256, 0, st>>>(h->LH, m->tri, h->minus, m->zscratch, m->z_sp, m->s_z, T, nk, G, M, n, Mp);
+  AFQMC_LAUNCHED(h);
+  MTRY(cudaGetLastError());
+  MTRY(set_one_body(h, st));
+
+  // tensor maps
+  MTRY(map5(&m->m_sinvt, m->sinvt_sp, {(uint64_t)Np, (uint64_t)N, 4, (uint64_t)WS, 1},
+            {(uint64_t)Np, (uint64_t)N * Np, (uint64_t)4 * N * Np, (uint64_t)WS * 4 * N * Np}, 128));
+  MTRY(map5(&m->m_phi, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
+            {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, BN));
+  MTRY(map5(&m->m_gsum, m->gsum_sp, {(uint64_t)nMp, (uint64_t)W, 4, (uint64_t)nk, (uint64_t)nk},
+            {(uint64_t)nMp, (uint64_t)nk * nk * W * nMp, (uint64_t)W * nMp, (uint64_t)nk * W * nMp}, 128));
+  MTRY(map5(&m->m_lh, m->lh_sp, {(uint64_t)nMp, (uint64_t)G, 4, (uint64_t)nk, (uint64_t)nk},
+            {(uint64_t)nMp, (uint64_t)nk * nk * G * nMp, (uint64_t)G * nMp, (uint64_t)nk * G * nMp}, BN));
+  MTRY(map5(&m->m_y, m->y_sp, {(uint64_t)Gp, (uint64_t)W, 4, (uint64_t)nk, 1},
+            {(uint64_t)Gp, (uint64_t)nk * W * Gp, (uint64_t)W * Gp, (uint64_t)nk * W * Gp * 4}, 128));
+  MTRY(map5(&m->m_lt, m->lt_sp, {(uint64_t)Gp, (uint64_t)M * M, 4, (uint64_t)nk, (uint64_t)nk},
+            {(uint64_t)Gp, (uint64_t)nk * nk * M * M * Gp, (uint64_t)M * M * Gp, (uint64_t)nk * M * M * Gp}, BN));
+  for (int i = 0; i < 2; ++i)
+    MTRY(map5(&m->m_t[i], m->t_sp[i], {(uint64_t)NMp, (uint64_t)2 * N, 4, (uint64_t)W, 1},
+              {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, 128));
+  MTRY(map5(&m->m_v, m->v_sp, {(uint64_t)NMp, (uint64_t)NM, 4, (uint64_t)W, 1},
+            {(uint64_t)NMp, (uint64_t)NM * NMp, (uint64_t)4 * NM * NMp, (uint64_t)W * 4 * NM * NMp}, BN));
+  MTRY(map5(&m->m_g, m->g_sp, {(uint64_t)nMp, (uint64_t)WS, 4, (uint64_t)nk, (uint64_t)nk},
+            {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
+  MTRY(map5(&m->m_z, m->z_sp, {(uint64_t)nMp, (uint64_t)nM, 4, (uint64_t)T, 1},
+            {(uint64_t)nMp, (uint64_t)T * nM * nMp, (uint64_t)nM * nMp, (uint64_t)T * nM * nMp * 4}, BN));
+  MTRY(set_smem_attr((const void*)onebody_in_kernel, onebody_smem(h)));
+  MTRY(set_smem_attr((const void*)onebody_out_kernel, onebody_smem(h)));
+  return cudaSuccess;
+}
+
+afqmc_status create(afqmc_kp* h, cudaStream_t st) {
+  h->mixed = new (std::nothrow) MixedState();
+  if (!h->mixed) return AFQMC_ERR_OOM;
+  cudaError_t e = create_impl(h, st);
+  if (e == cudaErrorMemoryAllocation) return AFQMC_ERR_OOM;
+  if (e == cudaErrorNotSupported) return AFQMC_ERR_UNSUPPORTED;
+  return e == cudaSuccess ? AFQMC_OK : AFQMC_ERR_CUDA;
+}
+
+void destroy(afqmc_kp* h) {
+  if (!h->mixed) return;
+  for (void* p : h->mixed->allocs) cudaFree(p);
+  delete h->mixed;
+  h->mixed = nullptr;
+}
+
+cudaError_t set_one_body(afqmc_kp* h, cudaStream_t st) {
+  const size_t total = (size_t)h->nk * h->M * h->M;
+  dhalf_kernel<<<(int)std::min<size_t>((total + 255) / 256, 4096), 256, 0, st>>>(h->Ehalf, h->mixed->dhalf, h->nk,
+                                                                                  h->M);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+// overlap + LU + inverse (FP64), split operands, Gh GEMM, split Gh
+static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  int* err = h->flags + 1;
+  MTRY(fp64::overlap_lu(h, phi, ld, sing, 1, st));
+  split_phi_kernel<<<m->WS, 256, 0, st>>>(phi, m->phi_sp, m->s_phi, h->NM, h->N, m->Np);
+  AFQMC_LAUNCHED(h);
+  split_sinvT_kernel<<<m->WS, 256, 0, st>>>(h->Sinv, m->sinvt_sp, m->s_sinv, h->N, m->Np);
+  AFQMC_LAUNCHED(h);
+  MTRY(cudaGetLastError());
+  GreenP p;
+  p.mt_n = cdiv(h->N, 128);
+  p.nt_n = cdiv(h->NM, BN);
+  p.tiles = m->WS * p.mt_n * p.nt_n;
+  p.kchunks = m->Np / 32;
+  p.N = h->N; p.NM = h->NM; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nk = h->nk; p.WS = m->WS;
+  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.g32 = m->g32;
+  MTRY(run_gemm(m->m_sinvt, m->m_phi, p, err, st));
+  AFQMC_LAUNCHED(h);
+  split_green_kernel<<<h->W, 256, 0, st>>>(m->g32, m->g_sp, m->s_g, m->gsum_sp, m->s_gsum, h->nk, h->W, m->nMp);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+static cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  ForceBiasP p;
+  p.mt_n = cdiv(h->W, 128);
+  p.nt_n = cdiv(h->G, BN);
+  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
+  p.kchunks = m->nMp / 32;
+  p.W = h->W; p.G = h->G; p.nk = h->nk;
+  p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.s_lh = m->s_lh; p.Xk = m->xk;
+  MTRY(run_gemm(m->m_gsum, m->m_lh, p, h->flags + 1, st));
+  AFQMC_LAUNCHED(h);
+  const size_t per = (size_t)h->W * h->nk * h->G;
+  xsum_kernel<<<(int)std::min<size_t>((per + 255) / 256, 4096), 256, 0, st>>>(m->xk, h->X, h->nk, per);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+cudaError_t force_bias(afqmc_kp* h, const zc* phi, zc* xbar, cudaStream_t st) {
+  prof_begin(h, AFQMC_STAGE_GREEN, st);
+  cudaError_t e = green(h, phi, h->ld_old, h->sing_old, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_FORCE_BIAS, st);
+  e = cholesky_trace(h, st);
+  if (e == cudaSuccess) e = fp64::force_bias(h, nullptr, xbar, st);
+  prof_end(h, st);
+  return e;
+}
+
+static cudaError_t vhs(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  split_y_kernel<<<dim3(h->nk, h->W), 256, 0, st>>>(h->y, m->s_l, m->y_sp, m->s_y, h->nk, h->W, h->G, m->Gp);
+  AFQMC_LAUNCHED(h);
+  MTRY(cudaGetLastError());
+  VhsP p;
+  p.mt_n = cdiv(h->W, 128);
+  p.nt_n = cdiv(h->M * h->M, BN);
+  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
+  p.kchunks = m->Gp / 32;
+  p.W = h->W; p.M = h->M; p.nk = h->nk; p.NM = h->NM; p.NMp = m->NMp;
+  p.kminus = h->kminus; p.s_y = m->s_y; p.v_sp = m->v_sp; p.overflow = h->flags + 2;
+  MTRY(run_gemm(m->m_y, m->m_lt, p, h->flags + 1, st));
+  AFQMC_LAUNCHED(h);
+  return cudaSuccess;
+}
+
+static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  const int R = 2 * h->N;
+  dim3 g1(h->nk, m->WS, cdiv(h->N, 64));
+  onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, m->acc, h->nk, h->M, h->N, h->NM);
+  AFQMC_LAUNCHED(h);
+  split_acc_kernel<<<h->W, 256, 0, st>>>(m->acc, m->t_sp[0], m->s_t, R, h->NM, m->NMp);
+  AFQMC_LAUNCHED(h);
+  MTRY(cudaGetLastError());
+  for (int j = 1; j <= h->order; ++j) {
+    const int cur = (j - 1) & 1, nxt = j & 1;
+    TaylorP p;
+    p.mt_n = cdiv(R, 128);
+    p.nt_n = cdiv(h->NM, BN);
+    p.tiles = h->W * p.mt_n * p.nt_n;
+    p.kchunks = m->NMp / 32;
+    p.R = R; p.NM = h->NM; p.NMp = m->NMp;
+    p.inv_j = 1.f / (float)j;
+    p.s_t = m->s_t; p.acc = m->acc; p.t_next = m->t_sp[nxt];
+    MTRY(run_gemm(m->m_t[cur], m->m_v, p, h->flags + 1, st));
+    AFQMC_LAUNCHED(h);
+  }
+  onebody_out_kernel<<<g1, 256, onebody_smem(h), st>>>(m->acc, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr, cudaStream_t st) {
+  cudaError_t e;
+  prof_begin(h, AFQMC_STAGE_GREEN, st);
+  e = green(h, phi, h->ld_old, h->sing_old, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_FORCE_BIAS, st);
+  e = cholesky_trace(h, st);
+  if (e == cudaSuccess) e = fp64::force_bias(h, x, h->xbar, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_VHS, st);
+  e = vhs(h, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_TAYLOR, st);
+  e = taylor(h, phi, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_WEIGHT, st);
+  e = fp64::weights(h, phi, x, w, do_qr ? nullptr : logdet, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  if (do_qr) return orthonormalise(h, phi, logdet, st);
+  return cudaSuccess;
+}
+
+cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
+  prof_begin(h, AFQMC_STAGE_QR, st);
+  cudaError_t e = fp64::qr_with(h, phi, reinterpret_cast<zc*>(h->mixed->acc), st);
+  if (e == cudaSuccess && logdet) e = fp64::overlap_lu(h, phi, logdet, h->sing_new, 0, st);
+  prof_end(h, st);
+  return e;
+}
+
+cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  cudaError_t e;
+  prof_begin(h, AFQMC_STAGE_GREEN, st);
+  e = green(h, phi, h->ld_old, h->sing_old, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_FORCE_BIAS, st);
+  e = cholesky_trace(h, st);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_ENERGY, st);
+  e1_ec_mixed_kernel<<<h->W, 256, 0, st>>>(h->AhH, m->g32, h->X, h->minus, eloc, h->nk, h->M, h->n, m->Mp, h->G,
+                                            m->WS);
+  AFQMC_LAUNCHED(h);
+  e = cudaGetLastError();
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  ExchangeP p;
+  p.mt_n = cdiv(m->WS, 128);
+  p.nt_n = cdiv(m->nM, BN);
+  p.tiles = m->T * p.mt_n * p.nt_n;
+  p.kchunks = m->nMp / 32;
+  p.WS = m->WS; p.nk = h->nk; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nM = m->nM;
+  p.kminus = h->kminus; p.minus = h->minus; p.tri = m->tri; p.s_g = m->s_g; p.s_z = m->s_z; p.g32 = m->g32;
+  p.xpart = m->xpart;
+  prof_begin(h, AFQMC_STAGE_EXCHANGE, st);
+  e = run_gemm(m->m_g, m->m_z, p, h->flags + 1, st);
+  AFQMC_LAUNCHED(h);
+  prof_end(h, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, AFQMC_STAGE_ENERGY, st);
+  ex_reduce_mixed_kernel<<<h->W, 256, 0, st>>>(m->xpart, m->tri, eloc, m->T, p.nt_n, m->WS);
+  AFQMC_LAUNCHED(h);
+  e = cudaGetLastError();
+  prof_end(h, st);
+  return e;
+}
+
+cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
+                                  cudaStream_t st) {
+  // The adjoint runs on the FP64 kernels (exact); a tensor-core adjoint is not built yet.
+  return fp64::local_energy_backward(h, phi, grad_e, grad_phi, grad_h1, st);
+}
+
 }  // namespace mixed

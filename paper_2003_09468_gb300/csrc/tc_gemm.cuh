@@ -1,0 +1,445 @@
+// Complex GEMM on the 5th-generation tensor cores with an fp16 hi/lo split.
+//
+//   D[m][n] = sum_k A[m][k] * B[n][k]          (complex, no conjugation)
+//
+// Operands live in global memory as four fp16 "planes" of the same shape,
+// K-major (k contiguous), padded to a multiple of 32 complex elements in k:
+//   plane 0 = hi(Re x*s), 1 = lo(Re x*s), 2 = hi(Im x*s), 3 = lo(Im x*s)
+// with hi = fp16(x*s), lo = fp16(x*s - hi) and s a power-of-two scale chosen so
+// that |x*s| stays well inside the fp16 range.  Each real product is formed
+// from three fp16 products (hi*hi + hi*lo + lo*hi), accumulated in fp32 in
+// tensor memory, which keeps about 22 significant bits per operand.  The real
+// and imaginary parts of D use two accumulators:
+//   D_re = Ar Br - Ai Bi,   D_im = Ar Bi + Ai Br   (negation via the MMA's B-negate bit)
+//
+// One CTA computes one BM x BN tile: warp 0 issues TMA loads (one 5-D box per
+// operand per 32-wide k chunk, all four planes at once, 64-byte swizzle) into a
+// STAGES-deep ring; warp 1 allocates tensor memory and one of its threads
+// issues the tcgen05.mma chain; warps 2-5 read the accumulators back with
+// tcgen05.ld and hand each row to the policy's epilogue.  Every mbarrier wait
+// is bounded; on time-out the kernel records an error, drains its own copies
+// and MMAs, frees tensor memory and returns.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "tc.cuh"
+
+namespace tcg {
+
+constexpr int BM = 128;      // tile rows = TMEM lanes
+constexpr int BK = 32;       // complex k per stage: 64-byte fp16 rows
+constexpr int NPLANE = 4;
+constexpr int THREADS = 192; // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+
+struct Coords {
+  int a[5];
+  int b[5];
+};
+
+template <int BN, int STAGES>
+struct Layout {
+  static constexpr int A_BYTES = NPLANE * BM * 64;
+  static constexpr int B_BYTES = NPLANE * BN * 64;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;  // + alignment slack
+  static constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128
+                                        : (2 * BN <= 256) ? 256 : 512;
+};
+
+// Policy P provides:
+//   int tiles;                                   number of output tiles
+//   int kchunks;                                 k chunks of BK per tile
+//   __device__ void tile(int t, int& b, int& mt, int& nt) const;
+//   __device__ Coords coords(int b, int mt, int nt, int kc) const;
+//   struct Row;                                  per-thread epilogue state
+//   __device__ void row_begin(Row&, int b, int mt, int nt, int r) const;
+//   __device__ void chunk(Row&, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const;
+//   __device__ void row_end(Row&, int b, int mt, int nt, int r) const;
+// r is the row inside the tile (0..127), c0 the first of 16 columns inside the tile.
+template <int BN, int STAGES, class P>
+__global__ void __launch_bounds__(THREADS, 1)
+    cgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const P p,
+                 int* err) {
+  using Lay = Layout<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Lay::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accb = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(accb, 1);
+    *abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, Lay::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t d_re = tmem, d_im = tmem + BN;
+
+  int b, mt, nt;
+  p.tile(blockIdx.x, b, mt, nt);
+  const int KC = p.kchunks;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::tma_prefetch(&tmA);
+      tc::tma_prefetch(&tmB);
+      int issued = 0;
+      for (int kc = 0; kc < KC; ++kc) {
+        const int s = kc % STAGES;
+        const uint32_t ph = (kc / STAGES) & 1;
+        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort)) {
+          atomicCAS(err, 0, tc::ERR_TIMEOUT_EMPTY);
+          *abort = 1;
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
+        const Coords c = p.coords(b, mt, nt, kc);
+        uint8_t* sa = smem + s * Lay::STAGE_BYTES;
+        tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
+        tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
+        ++issued;
+      }
+      // drain: every issued copy must land before the CTA may exit
+      for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc) {
+        const int s = kc % STAGES;
+        const uint32_t ph = (kc / STAGES) & 1;
+        int zero = 0;
+        if (!tc::mbar_wait(&full[s], ph, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idp = tc::idesc_f16(BM, BN, false);
+      constexpr uint32_t idn = tc::idesc_f16(BM, BN, true);
+      for (int kc = 0; kc < KC; ++kc) {
+        const int s = kc % STAGES;
+        const uint32_t ph = (kc / STAGES) & 1;
+        if (!tc::mbar_wait(&full[s], ph, abort)) {
+          atomicCAS(err, 0, tc::ERR_TIMEOUT_FULL);
+          *abort = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
+        const uint32_t sb = sa + Lay::A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint32_t ko = kk * 32;  // 16 fp16 = 32 bytes
+          const uint64_t arh = tc::desc_kmajor_sw64(sa + 0 * BM * 64 + ko);
+          const uint64_t arl = tc::desc_kmajor_sw64(sa + 1 * BM * 64 + ko);
+          const uint64_t aih = tc::desc_kmajor_sw64(sa + 2 * BM * 64 + ko);
+          const uint64_t ail = tc::desc_kmajor_sw64(sa + 3 * BM * 64 + ko);
+          const uint64_t brh = tc::desc_kmajor_sw64(sb + 0 * BN * 64 + ko);
+          const uint64_t brl = tc::desc_kmajor_sw64(sb + 1 * BN * 64 + ko);
+          const uint64_t bih = tc::desc_kmajor_sw64(sb + 2 * BN * 64 + ko);
+          const uint64_t bil = tc::desc_kmajor_sw64(sb + 3 * BN * 64 + ko);
+          const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+          // D_re = Ar Br - Ai Bi
+          tc::mma_f16(d_re, arh, brh, idp, first);
+          tc::mma_f16(d_re, arh, brl, idp, 1);
+          tc::mma_f16(d_re, arl, brh, idp, 1);
+          tc::mma_f16(d_re, aih, bih, idn, 1);
+          tc::mma_f16(d_re, aih, bil, idn, 1);
+          tc::mma_f16(d_re, ail, bih, idn, 1);
+          // D_im = Ar Bi + Ai Br
+          tc::mma_f16(d_im, arh, bih, idp, first);
+          tc::mma_f16(d_im, arh, bil, idp, 1);
+          tc::mma_f16(d_im, arl, bih, idp, 1);
+          tc::mma_f16(d_im, aih, brh, idp, 1);
+          tc::mma_f16(d_im, aih, brl, idp, 1);
+          tc::mma_f16(d_im, ail, brh, idp, 1);
+        }
+        tc::mma_commit(&empty[s]);
+      }
+      tc::mma_commit(accb);
+      int zero = 0;  // wait for our own MMAs even when aborting
+      if (!tc::mbar_wait(accb, 0, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter accessible to this warp
+    const int r = q * 32 + lane;
+    const bool ok = tc::mbar_wait(accb, 0, abort);
+    if (!ok) {
+      if (lane == 0) atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
+    } else {
+      tc::fence_after_sync();
+      typename P::Row st;
+      p.row_begin(st, b, mt, nt, r);
+      const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float re[16], im[16];
+        tc::tmem_ld16(d_re + lane_off + c0, re);
+        tc::tmem_ld16(d_im + lane_off + c0, im);
+        tc::tmem_ld_wait();
+        p.chunk(st, b, mt, nt, r, c0, re, im);
+      }
+      p.row_end(st, b, mt, nt, r);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, Lay::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- precise variant
+// The tensor-core accumulator adds each MMA's partial sum with truncation, so a
+// long chain of MMAs into one accumulator loses accuracy in proportion to its
+// length.  This variant keeps four real accumulators per k-step,
+//   P_rr = Ar Br, P_ii = Ai Bi, P_ri = Ar Bi, P_ir = Ai Br   (each hi*hi + hi*lo + lo*hi),
+// restarts them on every 16-wide k step (two TMEM sets in ping-pong), and the
+// epilogue warps fold each step into fp32 register sums with round-to-nearest:
+//   re += P_rr - P_ii,  im += P_ri + P_ir.
+// Tile 128 x BNP (BNP = 64): 4 x 64 columns per set, 2 sets = all 512 TMEM columns.
+constexpr int BNP = 64;
+
+template <int STAGES>
+struct LayoutP {
+  static constexpr int A_BYTES = NPLANE * BM * 64;
+  static constexpr int B_BYTES = NPLANE * BNP * 64;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+  static constexpr uint32_t TMEM_COLS = 512;
+};
+
+template <int STAGES, class P>
+__global__ void __launch_bounds__(THREADS, 1)
+    cgemm_precise_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const P p, int* err) {
+  using Lay = LayoutP<STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Lay::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;   // [2] MMA -> epilogue: set holds a finished k step
+  uint64_t* acce = accf + 2;         // [2] epilogue -> MMA: set drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&accf[s], 1);
+      tc::mbar_init(&acce[s], 4);
+    }
+    *abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, Lay::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  int b, mt, nt;
+  p.tile(blockIdx.x, b, mt, nt);
+  const int KC = p.kchunks;
+  const int NSTEP = 2 * KC;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::tma_prefetch(&tmA);
+      tc::tma_prefetch(&tmB);
+      int issued = 0;
+      for (int kc = 0; kc < KC; ++kc) {
+        const int s = kc % STAGES;
+        const uint32_t ph = (kc / STAGES) & 1;
+        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort)) {
+          atomicCAS(err, 0, tc::ERR_TIMEOUT_EMPTY);
+          *abort = 1;
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
+        const Coords c = p.coords(b, mt, nt, kc);
+        uint8_t* sa = smem + s * Lay::STAGE_BYTES;
+        tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
+        tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
+        ++issued;
+      }
+      for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc) {
+        const int s = kc % STAGES;
+        const uint32_t ph = (kc / STAGES) & 1;
+        int zero = 0;
+        if (!tc::mbar_wait(&full[s], ph, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id = tc::idesc_f16(BM, BNP, false);
+      int step = 0;
+      bool failed = false;
+      for (int kc = 0; kc < KC && !failed; ++kc) {
+        const int s = kc % STAGES;
+        const uint32_t ph = (kc / STAGES) & 1;
+        if (!tc::mbar_wait(&full[s], ph, abort)) {
+          atomicCAS(err, 0, tc::ERR_TIMEOUT_FULL);
+          *abort = 1;
+          break;
+        }
+        const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
+        const uint32_t sb = sa + Lay::A_BYTES;
+        for (int kk = 0; kk < 2; ++kk, ++step) {
+          const int set = step & 1, use = step >> 1;
+          if (!tc::mbar_wait(&acce[set], (use & 1) ^ 1, abort)) {
+            atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
+            *abort = 1;
+            failed = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t d = tmem + set * 4 * BNP;
+          const uint32_t ko = kk * 32;
+          const uint64_t arh = tc::desc_kmajor_sw64(sa + 0 * BM * 64 + ko);
+          const uint64_t arl = tc::desc_kmajor_sw64(sa + 1 * BM * 64 + ko);
+          const uint64_t aih = tc::desc_kmajor_sw64(sa + 2 * BM * 64 + ko);
+          const uint64_t ail = tc::desc_kmajor_sw64(sa + 3 * BM * 64 + ko);
+          const uint64_t brh = tc::desc_kmajor_sw64(sb + 0 * BNP * 64 + ko);
+          const uint64_t brl = tc::desc_kmajor_sw64(sb + 1 * BNP * 64 + ko);
+          const uint64_t bih = tc::desc_kmajor_sw64(sb + 2 * BNP * 64 + ko);
+          const uint64_t bil = tc::desc_kmajor_sw64(sb + 3 * BNP * 64 + ko);
+          // P_rr, P_ii, P_ri, P_ir at column offsets 0, 64, 128, 192 of the set.  The two
+          // small cross products go first, so the only truncation at the full magnitude
+          // is the final hi*hi accumulate.
+          tc::mma_f16(d + 0 * BNP, arl, brh, id, 0);
+          tc::mma_f16(d + 0 * BNP, arh, brl, id, 1);
+          tc::mma_f16(d + 0 * BNP, arh, brh, id, 1);
+          tc::mma_f16(d + 1 * BNP, ail, bih, id, 0);
+          tc::mma_f16(d + 1 * BNP, aih, bil, id, 1);
+          tc::mma_f16(d + 1 * BNP, aih, bih, id, 1);
+          tc::mma_f16(d + 2 * BNP, arl, bih, id, 0);
+          tc::mma_f16(d + 2 * BNP, arh, bil, id, 1);
+          tc::mma_f16(d + 2 * BNP, arh, bih, id, 1);
+          tc::mma_f16(d + 3 * BNP, ail, brh, id, 0);
+          tc::mma_f16(d + 3 * BNP, aih, brl, id, 1);
+          tc::mma_f16(d + 3 * BNP, aih, brh, id, 1);
+          tc::mma_commit(&accf[set]);
+        }
+        tc::mma_commit(&empty[s]);
+      }
+      // wait for our own MMAs even when aborting: commit to a fresh arrival on accf of the
+      // last set used and wait on it with the abort flag ignored
+      if (step > 0) {
+        const int last = step - 1;
+        int zero = 0;
+        if (!tc::mbar_wait(&accf[last & 1], (last >> 1) & 1, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    float sre[BNP], sim[BNP];
+#pragma unroll
+    for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
+    bool ok = true;
+    for (int step = 0; step < NSTEP; ++step) {
+      const int set = step & 1, use = step >> 1;
+      if (!tc::mbar_wait(&accf[set], use & 1, abort)) {
+        if (lane == 0) atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t d = tmem + lane_off + set * 4 * BNP;
+#pragma unroll
+      for (int g = 0; g < BNP / 16; ++g) {
+        float rr[16], ii[16], ri[16], ir[16];
+        tc::tmem_ld16(d + 0 * BNP + g * 16, rr);
+        tc::tmem_ld16(d + 1 * BNP + g * 16, ii);
+        tc::tmem_ld16(d + 2 * BNP + g * 16, ri);
+        tc::tmem_ld16(d + 3 * BNP + g * 16, ir);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          sre[g * 16 + c] += rr[c] - ii[c];
+          sim[g * 16 + c] += ri[c] + ir[c];
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[set]);
+    }
+    if (ok) {
+      typename P::Row st;
+      p.row_begin(st, b, mt, nt, r);
+#pragma unroll
+      for (int g = 0; g < BNP / 16; ++g) p.chunk(st, b, mt, nt, r, g * 16, sre + g * 16, sim + g * 16);
+      p.row_end(st, b, mt, nt, r);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, Lay::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+// 5-D fp16 tensor map with 64-byte swizzle.  dims[0] is the contiguous k
+// extent (elements), strides are byte strides of dims 1..4, box[0] = 32.
+struct MapSpec {
+  uint64_t dims[5];
+  uint64_t strides[4];
+  uint32_t box[5];
+};
+
+cudaError_t make_map(CUtensorMap* map, void* base, const MapSpec& s);
+
+template <int BN, int STAGES, class P>
+cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
+  using Lay = Layout<BN, STAGES>;
+  auto fn = cgemm_kernel<BN, STAGES, P>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (p.tiles <= 0) return cudaSuccess;
+  fn<<<p.tiles, THREADS, Lay::SMEM, st>>>(a, b, p, err);
+  return cudaGetLastError();
+}
+
+template <int STAGES, class P>
+cudaError_t launch_precise(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
+  using Lay = LayoutP<STAGES>;
+  auto fn = cgemm_precise_kernel<STAGES, P>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (p.tiles <= 0) return cudaSuccess;
+  fn<<<p.tiles, THREADS, Lay::SMEM, st>>>(a, b, p, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tcg
