@@ -52,25 +52,43 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 # algorithmic work (complex multiply-add = 8 real flops)
 # ---------------------------------------------------------------------------
+def canonical_triples(spec) -> int:
+    """Number of (Q, k, k') terms kept after pairing (Q, k, k') with (-Q, k'-Q, k)."""
+    g = np.array(spec.grid)
+    kp = gen.kpoints(spec.grid)
+    lin = lambda v: int((v[0] * g[1] + v[1]) * g[2] + v[2])
+    minus = [lin((-kp[q]) % g) for q in range(spec.nk)]
+    t = 0
+    for Q in range(spec.nk):
+        for k in range(spec.nk):
+            for kx in range(spec.nk):
+                if Q < minus[Q] or (Q == minus[Q] and k <= kx):
+                    t += 1
+    return t
+
+
 def exchange_flops(spec) -> float:
-    """E_X for all walkers and both spins: every T^Q_g = LH^{Qg} Gh^T element once
-    (N x N per (Q, g), M complex MACs each), plus the pairing products."""
+    """Direct exchange (Sec. 3.2 steps 2a-2c) for all walkers and both spins: every
+    T^Q_g = LH^{Qg} Gh^T element once (N x N per (Q, g), M complex MACs each) plus the
+    pairing products.  This is what the FP64 kernel executes."""
     nk, G, N, M = spec.nk, spec.nchol, spec.N, spec.M
     return spec.nwalkers * 2 * 8.0 * nk * G * N * N * (M + 0.5)
 
 
-def step_flops(spec, order=6) -> dict:
-    nk, G, N, M, n, NM, W = spec.nk, spec.nchol, spec.N, spec.M, spec.nocc, spec.NM, spec.nwalkers
-    f = {
-        "overlap+inverse+green": W * 2 * 8.0 * (N * N * M + N ** 3 + N * N * NM) * 2,  # at step start and for E_L
-        "force_bias": W * 8.0 * nk * G * nk * n * M * 2,
-        "vhs": W * 8.0 * nk * nk * G * M * M,
-        "taylor": W * 8.0 * order * NM * NM * 2 * N,
-        "one_body": W * 2 * 8.0 * nk * M * M * 2 * N,
-        "exchange": exchange_flops(spec),
-    }
-    f["total"] = sum(f.values())
-    return f
+def exchange_precontracted_flops(spec) -> float:
+    """Exchange through the precontracted tensor: one (nM x nM) x WS complex GEMM per
+    canonical triple, 8 real flops per complex MAC."""
+    nM = spec.nocc * spec.M
+    return 8.0 * canonical_triples(spec) * nM * nM * 2 * spec.nwalkers
+
+
+def taylor_flops(spec, order=6) -> float:
+    return 8.0 * order * spec.nwalkers * spec.NM * spec.NM * 2 * spec.N
+
+
+def vhs_bytes(spec) -> float:
+    """Cholesky tensor read once (complex64 equivalent) + V written once."""
+    return 8.0 * spec.nk * spec.nk * spec.nchol * spec.M * spec.M + 8.0 * spec.nwalkers * spec.NM * spec.NM
 
 
 # ---------------------------------------------------------------------------
@@ -182,6 +200,7 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="diamond-3x3x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -215,7 +234,6 @@ def main():
     if sys_ is None:
         precision = "fp64"
         sys_ = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
-    del L
 
     # walkers and fields: independent replicas per rank (disjoint walker indices)
     first = rank * spec.nwalkers
@@ -302,22 +320,61 @@ def main():
         return
 
     peaks, peaks_kind = load_peaks()
-    ex_ms, ex_n = stages["exchange"]
-    ex_flops = exchange_flops(spec)
+    rooflines = {}
+    tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+
+    def put(stage, bound, work, peak, unit, note):
+        ms_s, n_s = stages[stage]
+        if not n_s:
+            return
+        per = ms_s / n_s
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = work / (per * 1e-3) / scale
+        rooflines[stage] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                            "traffic": None, "kernel": stage, "launch_ms": per,
+                            "algorithmic_per_launch": work, "peak_source": note}
+
     if precision == "fp64":
-        bound, peak, unit_r = "alu", 1.25, "TFLOP/s"
-        peak_note = "FP64 nominal 1.25 TFLOP/s (GB300 FP64 pipe); a DFMA probe measured 1.20"
         dtype = "f64"
+        put("exchange", "alu", exchange_flops(spec), 1.25, "TFLOP/s",
+            "FP64 nominal 1.25 TFLOP/s (GB300 FP64 pipe); a DFMA probe measured 1.20")
     else:
-        bound, peak, unit_r = "tensor", peaks.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
-        peak_note = f"dense f16/bf16 tensor, sustained, {peaks_kind}"
         dtype = "f16x2-split/f32-acc + f64"
-    achieved = ex_flops / (ex_ms / ex_n * 1e-3) / 1e12 if ex_n else None
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit_r,
-                "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "exchange", "peak_source": peak_note,
-                "algorithmic_flops_per_launch": ex_flops,
-                "launch_ms": ex_ms / ex_n if ex_n else None}
+        note = f"dense f16/bf16 tensor, sustained, {peaks_kind}"
+        put("exchange", "tensor", exchange_precontracted_flops(spec), tensor_peak, "TFLOP/s", note)
+        stages_taylor = stages["taylor"]
+        if stages_taylor[1]:
+            ms_t = stages_taylor[0] / stages_taylor[1]
+            rooflines["taylor"] = {"bound": "tensor", "achieved": taylor_flops(spec) / (ms_t * 1e-3) / 1e12,
+                                   "peak": tensor_peak, "unit": "TFLOP/s", "traffic": None, "kernel": "taylor",
+                                   "launch_ms": ms_t, "algorithmic_per_launch": taylor_flops(spec),
+                                   "peak_source": note + "; 6 GEMM launches + one-body kernels per stage"}
+            rooflines["taylor"]["frac"] = rooflines["taylor"]["achieved"] / tensor_peak
+        put("vhs", "hbm", vhs_bytes(spec), peaks.get("hbm_gbs", 6800.0), "GB/s", f"HBM copy, {peaks_kind}")
+    dom = max(rooflines, key=lambda k: rooflines[k]["launch_ms"] * stages[k][1]) if rooflines else None
+    roofline = rooflines.get(dom)
+
+    fp64_cmp = None
+    if precision == "mixed" and args.compare_fp64 and world == 1:
+        del sys_
+        torch.cuda.synchronize()
+        s64 = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
+        phi.copy_(torch.from_numpy(phi0).to(dev))
+        w.fill_(1.0)
+        step_fn = lambda i, x: (s64.propagate(phi, x, w, do_qr=((i + 1) % QR_PERIOD == 0)),
+                                s64.local_energy(phi, eloc))
+        step_fn(0, xs[0])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_fn(1, xs[min(1, nsteps - 1)])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64_cmp = {"value": spec.nwalkers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": 1,
+                    "speedup_mixed_over_fp64": value / (spec.nwalkers / (ms64 * 1e-3))}
+        s64.close()
+        sys_ = None
 
     cpu_baseline = None
     if not args.no_cpu_baseline and world == 1:
@@ -335,6 +392,8 @@ def main():
                    "qr_period": QR_PERIOD, "precision": precision, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (Cholesky tensor alone exceeds 129 MB)"},
         "roofline": roofline,
+        "rooflines": rooflines,
+        "fp64_path": fp64_cmp,
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
         "gpu_launches": gpu_launches,
@@ -343,7 +402,8 @@ def main():
         "finite": finite,
     }
     print(json.dumps(out))
-    sys_.close()
+    if sys_ is not None:
+        sys_.close()
     if world > 1:
         dist.destroy_process_group()
 
