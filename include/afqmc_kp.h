@@ -239,6 +239,34 @@ afqmc_status afqmc_kp_launch_count(afqmc_kp_t h, int* launches);
  */
 const char* afqmc_last_message(void);
 
+/*
+ * afqmc_orthonormalise_noalloc -- the walker re-orthonormalisation of
+ * afqmc_kp_orthonormalise (Householder QR, phi <- Q with diag(R) real
+ * positive) for callers that cannot allocate device memory: code running
+ * while a CUDA graph is captured in global mode, where cudaMalloc fails, or a
+ * plug-in inside a host program that owns every device byte.  It needs no
+ * handle and calls no allocator; its scratch is a fixed array of
+ * AFQMC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library keeps until the process exits.  The paper has no
+ * counterpart: this entry point exists only for such callers.
+ *
+ *   phi     DEVICE c128 [nmat][rows][cols], each matrix row-major, overwritten
+ *           by its Q factor (the layout of one spin block of a walker).
+ *   rows, cols, nmat   1 <= cols <= rows, cols <= 1024, nmat >= 1, and
+ *           rows * cols * nmat * 16 bytes <= AFQMC_NOALLOC_SCRATCH_BYTES;
+ *           larger requests return AFQMC_ERR_INVALID without doing anything.
+ *   stream  cudaStream_t.
+ * The first call on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array, so
+ * calls whose work overlaps on the GPU (different streams, threads or
+ * processes sharing the library image) race and must be serialised by the
+ * caller.  The array keeps the last call's contents; the kernel overwrites
+ * every entry it reads before reading it.
+ */
+#define AFQMC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+afqmc_status afqmc_orthonormalise_noalloc(void* phi, int rows, int cols, int nmat, void* stream);
+
 /* Static, NUL-terminated description of a status code. */
 const char* afqmc_status_string(afqmc_status s);
 

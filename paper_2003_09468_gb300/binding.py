@@ -39,6 +39,7 @@ SIGNATURES = {
     "afqmc_kp_stage_times": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "afqmc_status_string": [_I],
     "afqmc_last_message": [],
+    "afqmc_orthonormalise_noalloc": [_VP, _I, _I, _I, _VP],
 }
 
 

@@ -647,6 +647,13 @@ cudaError_t qr_with(afqmc_kp* h, zc* phi, zc* scratch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Same kernel, without a handle: nmat matrices of rows x cols, scratch of the same size.
+cudaError_t qr_launch(zc* phi, zc* scratch, int rows, int cols, int nmat, cudaStream_t st) {
+  size_t smem = (size_t)cols * (2 * sizeof(zc) + sizeof(double));
+  qr_kernel<<<nmat, 256, smem, st>>>(phi, scratch, rows, cols);
+  return cudaGetLastError();
+}
+
 static cudaError_t qr(afqmc_kp* h, zc* phi, cudaStream_t st) {
   size_t smem = (size_t)h->N * (2 * sizeof(zc) + sizeof(double));
   qr_kernel<<<2 * h->W, 256, smem, st>>>(phi, h->T1, h->NM, h->N);

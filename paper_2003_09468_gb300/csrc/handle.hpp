@@ -110,4 +110,5 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
 cudaError_t overlap_lu(afqmc_kp* h, const zc* phi, zc* ld, int* sing, int want_inv, cudaStream_t st);
 cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st);
 cudaError_t qr_with(afqmc_kp* h, zc* phi, zc* scratch, cudaStream_t st);
+cudaError_t qr_launch(zc* phi, zc* scratch, int rows, int cols, int nmat, cudaStream_t st);
 }  // namespace fp64
