@@ -248,9 +248,9 @@ def main():
     launches = [0]
 
     def step(i, x):
-        sys_.propagate(phi, x, w, do_qr=((i + 1) % QR_PERIOD == 0))
-        launches[0] += sys_.launch_count()
-        sys_.local_energy(phi, eloc)
+        # one fused call: propagate, then the local energy of the new walkers; the
+        # Green's function formed at the end of a step serves the next step's force bias
+        sys_.step(phi, x, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=True)
         launches[0] += sys_.launch_count()
 
     for i in range(args.warmup):
@@ -300,8 +300,7 @@ def main():
         t0 = time.perf_counter()
         for i in range(args.warmup, nsteps):
             xdev.copy_(xs_host[i], non_blocking=True)
-            sys_.propagate(phi, xdev, w, do_qr=((i + 1) % QR_PERIOD == 0))
-            sys_.local_energy(phi, eloc)
+            sys_.step(phi, xdev, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=True)
             e_host.copy_(eloc, non_blocking=True)
             w_host.copy_(w, non_blocking=True)
             stream.synchronize()
@@ -361,8 +360,7 @@ def main():
         s64 = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
         phi.copy_(torch.from_numpy(phi0).to(dev))
         w.fill_(1.0)
-        step_fn = lambda i, x: (s64.propagate(phi, x, w, do_qr=((i + 1) % QR_PERIOD == 0)),
-                                s64.local_energy(phi, eloc))
+        step_fn = lambda i, x: s64.step(phi, x, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=True)
         step_fn(0, xs[0])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

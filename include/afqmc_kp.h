@@ -149,6 +149,30 @@ afqmc_status afqmc_kp_force_bias(afqmc_kp_t h, const void* phi, void* xbar, void
 afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double* weight,
                                 void* logdet, int do_qr, void* stream);
 
+/* Flags of afqmc_kp_step. */
+#define AFQMC_STEP_REUSE_GREEN 1
+
+/*
+ * afqmc_kp_step -- one hybrid step of every walker followed by the local
+ * energy of the propagated walkers (a block of the paper's driver does many
+ * such steps, Sec. 3.1).  The result equals afqmc_kp_propagate followed by
+ * afqmc_kp_local_energy on the new walkers, but the Green's function of the
+ * new walkers is formed once: it gives their log det for the weight update,
+ * their energy, and (with AFQMC_STEP_REUSE_GREEN on the next call) the next
+ * step's force bias.
+ *   phi, x, weight, logdet, do_qr   as for afqmc_kp_propagate.
+ *   eloc   DEVICE c128 [W][3] output: (E1, EC, EX) of the propagated walkers
+ *          (a QR does not change them).
+ *   flags  0 or AFQMC_STEP_REUSE_GREEN.  With the flag, the caller promises
+ *          that phi is the output of the previous afqmc_kp_step call on this
+ *          handle and was not modified since; the stored Green's function,
+ *          Cholesky trace and log det are then reused instead of recomputed.
+ *          The library ignores the flag when another entry point ran on the
+ *          handle in between or phi is a different pointer.
+ */
+afqmc_status afqmc_kp_step(afqmc_kp_t h, void* phi, const double* x, double* weight, void* eloc, void* logdet,
+                           int do_qr, int flags, void* stream);
+
 /*
  * afqmc_kp_orthonormalise -- phi_s <- Q factor of phi_s with diag(R) > 0
  * (the walker orthogonalisation done once per block, Sec. 3.1).

@@ -30,6 +30,7 @@ SIGNATURES = {
     "afqmc_kp_force_bias": [_VP, _VP, _VP, _VP],
     "afqmc_kp_propagate": [_VP, _VP, _VP, _VP, _VP, _I, _VP],
     "afqmc_kp_orthonormalise": [_VP, _VP, _VP, _VP],
+    "afqmc_kp_step": [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP],
     "afqmc_kp_local_energy": [_VP, _VP, _VP, _VP],
     "afqmc_kp_local_energy_backward": [_VP, _VP, _VP, _VP, _VP, _VP],
     "afqmc_kp_last_error": [_VP, _VP, ctypes.POINTER(_I)],
@@ -175,6 +176,18 @@ class KPointAFQMC:
                                            _ptr(x, torch.float64, self.field_shape, "x"),
                                            _ptr(weight, torch.float64, (self.W,), "weight"), lp,
                                            1 if do_qr else 0, _stream(stream)), "afqmc_kp_propagate")
+
+    def step(self, phi, x, weight, eloc=None, logdet=None, do_qr=False, reuse=True, stream=None) -> torch.Tensor:
+        """Propagate every walker one step and return the local energy of the new walkers."""
+        if eloc is None:
+            eloc = torch.empty((self.W, 3), dtype=torch.complex128, device=phi.device)
+        lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
+        _check(self.lib.afqmc_kp_step(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                      _ptr(x, torch.float64, self.field_shape, "x"),
+                                      _ptr(weight, torch.float64, (self.W,), "weight"),
+                                      _ptr(eloc, torch.complex128, (self.W, 3), "eloc"), lp,
+                                      1 if do_qr else 0, 1 if reuse else 0, _stream(stream)), "afqmc_kp_step")
+        return eloc
 
     def orthonormalise(self, phi, logdet=None, stream=None):
         lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")

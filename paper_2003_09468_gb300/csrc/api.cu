@@ -218,6 +218,7 @@ afqmc_status afqmc_kp_destroy(afqmc_kp_t h) {
 afqmc_status afqmc_kp_set_one_body(afqmc_kp_t h, const void* h1, void* stream) {
   if (!h || !h1) return AFQMC_ERR_INVALID;
   h->launches = 0;
+  h->green_valid = false;
   cudaStream_t st = as_stream(stream);
   cudaError_t e = cudaMemcpyAsync(h->h1, h1, sizeof(zc) * (size_t)h->nk * h->M * h->M, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = fp64::set_one_body(h, st);
@@ -228,6 +229,7 @@ afqmc_status afqmc_kp_set_one_body(afqmc_kp_t h, const void* h1, void* stream) {
 afqmc_status afqmc_kp_force_bias(afqmc_kp_t h, const void* phi, void* xbar, void* stream) {
   if (!h || !phi || !xbar) return AFQMC_ERR_INVALID;
   h->launches = 0;
+  h->green_valid = false;
   cudaStream_t st = as_stream(stream);
   cudaError_t e;
   if (h->mixed) {
@@ -244,6 +246,7 @@ afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double
                                 int do_qr, void* stream) {
   if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1)) return AFQMC_ERR_INVALID;
   h->launches = 0;
+  h->green_valid = false;
   cudaStream_t st = as_stream(stream);
   cudaError_t e;
   if (h->mixed)
@@ -253,9 +256,32 @@ afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double
   return from_cuda(e);
 }
 
+afqmc_status afqmc_kp_step(afqmc_kp_t h, void* phi, const double* x, double* weight, void* eloc, void* logdet,
+                           int do_qr, int flags, void* stream) {
+  if (!h || !phi || !x || !weight || !eloc || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
+    return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  const int reuse = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi;
+  h->green_valid = false;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e;
+  if (h->mixed)
+    e = mixed::step(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(eloc), static_cast<zc*>(logdet), do_qr,
+                    reuse, st);
+  else
+    e = fp64::step(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(eloc), static_cast<zc*>(logdet), do_qr,
+                   reuse, st);
+  if (e == cudaSuccess) {
+    h->green_valid = true;
+    h->green_phi = phi;
+  }
+  return from_cuda(e);
+}
+
 afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void* stream) {
   if (!h || !phi) return AFQMC_ERR_INVALID;
   h->launches = 0;
+  h->green_valid = false;
   cudaStream_t st = as_stream(stream);
   cudaError_t e;
   if (h->mixed)
@@ -268,6 +294,7 @@ afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void
 afqmc_status afqmc_kp_local_energy(afqmc_kp_t h, const void* phi, void* eloc, void* stream) {
   if (!h || !phi || !eloc) return AFQMC_ERR_INVALID;
   h->launches = 0;
+  h->green_valid = false;
   cudaStream_t st = as_stream(stream);
   cudaError_t e;
   if (h->mixed)
@@ -281,6 +308,7 @@ afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const
                                             void* grad_h1, void* stream) {
   if (!h || !phi || !grad_e) return AFQMC_ERR_INVALID;
   h->launches = 0;
+  h->green_valid = false;
   cudaStream_t st = as_stream(stream);
   cudaError_t e;
   if (h->mixed)

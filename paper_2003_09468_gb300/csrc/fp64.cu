@@ -12,6 +12,8 @@
 //                                 Sec. 3.2 energy steps 1-3
 #include <math.h>
 
+#include <utility>
+
 #include "handle.hpp"
 
 namespace fp64 {
@@ -260,15 +262,37 @@ cudaError_t set_one_body(afqmc_kp* h, cudaStream_t st) {
 // Overlap, LU with partial pivoting, log det and inverse (one block per matrix)
 // ---------------------------------------------------------------------------
 
-// S[w][s][(k,a)][j] = sum_p conj(A[k][p][a]) phi[w][s][(k,p)][j]
+// S[ws][(k,a)][j] = sum_p conj(A[k][p][a]) phi[ws][(k,p)][j]
+// Block (ws, k); threads over j, eight rows a at a time held in registers.
+constexpr int OVA = 8;
+__global__ void __launch_bounds__(256) overlap_kernel(const zc* A, const zc* phi, zc* S, int nk, int M, int n,
+                                                      int N) {
+  const int ws = blockIdx.x, k = blockIdx.y;
+  const zc* Ak = A + (size_t)k * M * n;
+  const zc* ph = phi + ((size_t)ws * nk * M + (size_t)k * M) * N;
+  zc* Sk = S + ((size_t)ws * N + (size_t)k * n) * N;
+  for (int a0 = 0; a0 < n; a0 += OVA) {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      zc acc[OVA];
+#pragma unroll
+      for (int i = 0; i < OVA; ++i) acc[i] = zzero();
+      for (int p = 0; p < M; ++p) {
+        const zc v = ph[(size_t)p * N + j];
+#pragma unroll
+        for (int i = 0; i < OVA; ++i)
+          if (a0 + i < n) acc[i] = zfma(zconj(Ak[p * n + a0 + i]), v, acc[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < OVA; ++i)
+        if (a0 + i < n) Sk[(size_t)(a0 + i) * N + j] = acc[i];
+    }
+  }
+}
+
 static cudaError_t overlap(afqmc_kp* h, const zc* phi, cudaStream_t st) {
-  const int nk = h->nk, M = h->M, n = h->n, N = h->N, NM = h->NM;
-  ZGemm g = gemm_init(n, N, M, 2, 0);
-  g.A = h->A; g.lda = n; g.sA[0] = 0; g.sA[1] = (long)M * n;
-  g.B = phi; g.ldb = N; g.sB[0] = (long)NM * N; g.sB[1] = (long)M * N;
-  g.C = h->S; g.ldc = N; g.sC[0] = (long)N * N; g.sC[1] = (long)n * N;
-  g.nb[0] = 2 * h->W; g.nb[1] = nk;
-  return gemm_launch(h, g, st);
+  overlap_kernel<<<dim3(2 * h->W, h->nk), 256, 0, st>>>(h->A, phi, h->S, h->nk, h->M, h->n, h->N);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
 }
 
 // In-place LU of S (row pivoting), log det, optional inverse.  sing[b] = 1 if a
@@ -377,12 +401,11 @@ __global__ void __launch_bounds__(256) lu_kernel(zc* S, zc* Sinv, zc* logdet, in
 }
 
 // Gh[w][s] = (phi S^-1)^T = S^-T phi^T  (N x NM)
-static cudaError_t green_impl(afqmc_kp* h, const zc* phi, cudaStream_t st) {
+static cudaError_t green_impl(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
   cudaError_t e = overlap(h, phi, st);
   if (e != cudaSuccess) return e;
-  // perm workspace lives in the Gam buffer (unused until the backward pass)
-  lu_kernel<<<2 * h->W, 256, 0, st>>>(h->S, h->Sinv, h->ld_old, h->sing_old, h->flags, h->N, 1,
-                                      reinterpret_cast<int*>(h->P));
+  // pivot scratch lives in the P buffer (used otherwise only by the backward pass)
+  lu_kernel<<<2 * h->W, 256, 0, st>>>(h->S, h->Sinv, ld, sing, h->flags, h->N, 1, reinterpret_cast<int*>(h->P));
   AFQMC_LAUNCHED(h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int N = h->N, NM = h->NM;
@@ -396,7 +419,7 @@ static cudaError_t green_impl(afqmc_kp* h, const zc* phi, cudaStream_t st) {
 
 cudaError_t green(afqmc_kp* h, const zc* phi, cudaStream_t st) {
   prof_begin(h, AFQMC_STAGE_GREEN, st);
-  cudaError_t e = green_impl(h, phi, st);
+  cudaError_t e = green_impl(h, phi, h->ld_old, h->sing_old, st);
   prof_end(h, st);
   return e;
 }
@@ -672,6 +695,15 @@ static cudaError_t one_body(afqmc_kp* h, const zc* in, zc* out, cudaStream_t st)
   return gemm_launch(h, g, st);
 }
 
+// The two halves of overlap_lu, for callers that use S before it is factorised.
+cudaError_t overlap_only(afqmc_kp* h, const zc* phi, cudaStream_t st) { return overlap(h, phi, st); }
+cudaError_t lu_only(afqmc_kp* h, zc* ld, int* sing, int want_inv, cudaStream_t st) {
+  lu_kernel<<<2 * h->W, 256, 0, st>>>(h->S, h->Sinv, ld, sing, h->flags, h->N, want_inv,
+                                      reinterpret_cast<int*>(h->P));
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
 cudaError_t overlap_lu(afqmc_kp* h, const zc* phi, zc* ld, int* sing, int want_inv, cudaStream_t st) {
   cudaError_t e = overlap(h, phi, st);
   if (e != cudaSuccess) return e;
@@ -727,6 +759,14 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
 cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st) {
   cudaError_t e;
   if ((e = logdet_only(h, phi, h->ld_new, h->sing_new, st)) != cudaSuccess) return e;
+  weight_kernel<<<h->W, 256, 0, st>>>(x, h->xbar, h->ld_old, h->ld_new, h->sing_old, h->sing_new, w, logdet,
+                                      2 * h->nk * h->G);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+// Hybrid weight from the log dets already in ld_old / ld_new.
+cudaError_t weight_only(afqmc_kp* h, const double* x, double* w, zc* logdet, cudaStream_t st) {
   weight_kernel<<<h->W, 256, 0, st>>>(x, h->xbar, h->ld_old, h->ld_new, h->sing_old, h->sing_new, w, logdet,
                                       2 * h->nk * h->G);
   AFQMC_LAUNCHED(h);
@@ -878,6 +918,38 @@ cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) 
   STAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
   STAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
   STAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  return cudaSuccess;
+}
+
+// One fused walker step: propagate every walker and evaluate the local energy of
+// the propagated walkers.  The Green's function of the new walkers serves the
+// new log det (weights), the energy, and the next step's force bias.
+cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc* logdet, int do_qr, int reuse,
+                 cudaStream_t st) {
+  cudaError_t e;
+  if (!reuse) {
+    STAGE(AFQMC_STAGE_GREEN, green_impl(h, phi, h->ld_old, h->sing_old, st));
+    STAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+  }
+  STAGE(AFQMC_STAGE_FORCE_BIAS, force_bias(h, x, h->xbar, st));
+  STAGE(AFQMC_STAGE_VHS, vhs_build(h, st));
+  STAGE(AFQMC_STAGE_TAYLOR, taylor(h, phi, st));
+  STAGE(AFQMC_STAGE_GREEN, green_impl(h, phi, h->ld_new, h->sing_new, st));
+  STAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+  STAGE(AFQMC_STAGE_WEIGHT, weight_only(h, x, w, do_qr ? nullptr : logdet, st));
+  STAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
+  STAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
+  STAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  if (do_qr) {
+    // the Green's function is invariant under phi -> phi R^-1; only the log det moves
+    STAGE(AFQMC_STAGE_QR, qr(h, phi, st));
+    STAGE(AFQMC_STAGE_QR, overlap_lu(h, phi, h->ld_new, h->sing_new, 0, st));
+    if (logdet &&
+        (e = cudaMemcpyAsync(logdet, h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return e;
+  }
+  std::swap(h->ld_old, h->ld_new);
+  std::swap(h->sing_old, h->sing_new);
   return cudaSuccess;
 }
 

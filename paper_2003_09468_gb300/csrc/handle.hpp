@@ -48,6 +48,11 @@ struct afqmc_kp {
 
   MixedState* mixed = nullptr;
 
+  // Green's function state left by afqmc_kp_step (valid for green_phi until any
+  // other entry point reuses the buffers)
+  bool green_valid = false;
+  const void* green_phi = nullptr;
+
   // stage timing (afqmc_kp_profile)
   bool prof_on = false;
   struct Rec { int stage; cudaEvent_t a, b; };
@@ -108,7 +113,12 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
                                   zc* grad_h1, cudaStream_t st);
 // pieces shared with the mixed path
 cudaError_t overlap_lu(afqmc_kp* h, const zc* phi, zc* ld, int* sing, int want_inv, cudaStream_t st);
+cudaError_t overlap_only(afqmc_kp* h, const zc* phi, cudaStream_t st);
+cudaError_t lu_only(afqmc_kp* h, zc* ld, int* sing, int want_inv, cudaStream_t st);
 cudaError_t weights(afqmc_kp* h, const zc* phi, const double* x, double* w, zc* logdet, cudaStream_t st);
 cudaError_t qr_with(afqmc_kp* h, zc* phi, zc* scratch, cudaStream_t st);
 cudaError_t qr_launch(zc* phi, zc* scratch, int rows, int cols, int nmat, cudaStream_t st);
+cudaError_t weight_only(afqmc_kp* h, const double* x, double* w, zc* logdet, cudaStream_t st);
+cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc* logdet, int do_qr, int reuse,
+                 cudaStream_t st);
 }  // namespace fp64

@@ -44,12 +44,14 @@ struct MixedState {
   double2* acc = nullptr;                                // [W][2N][NM]
   double2* xpart = nullptr;                              // [T][ntile][WS]
   double2* xk = nullptr;                                 // [Nk][W][Nk][G] per-k-block Cholesky traces
+  unsigned long long* mx = nullptr;                      // max |.| bit patterns: phi[WS], sinv[WS], g[3W], acc[W]
   // static operands
   __half* lh_sp = nullptr;    float* s_lh = nullptr;    // [4][Nk][Nk][G][n][Mp], s_lh[Q][G]
   __half* lt_sp = nullptr;    float* s_l = nullptr;     // [4][Nk][Nk][M*M][Gp], s_l[Q][G]
   __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][T][nM][n*Mp]
   int4* tri = nullptr;                                   // [T] (Q, k, kx, weight)
   float2* dhalf = nullptr;                               // [Nk][M][M] exp(-dt/2 H1') - I
+  zc* bproj = nullptr;                                   // [Nk][M][n] A (A^dag A)^-1 per k
   zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
   std::vector<void*> allocs;
@@ -173,12 +175,14 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
 // ---------------------------------------------------------------------------
 struct NoRow {};
 
-// Gh[ws] = S^-T phi^T : rows i = (k1, a), cols (k2, p); written to g32 in tile layout.
+// Gh[ws] = B^T + S^-T phi_perp^T : rows i = (k1, a), cols (k2, p); written to g32 in tile
+// layout.  B = A (A^dag A)^-1 and phi_perp = phi - B S (see green()).
 struct GreenP {
   int tiles, kchunks;
   int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
   const float* s_sinv;
   const float* s_phi;
+  const zc* bproj;
   float2* g32;
   typedef float Row;  // inverse scale of the row's walker-spin
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
@@ -200,7 +204,13 @@ struct GreenP {
       const int col = nt * BN + c0 + c;
       if (col < NM) {
         const int k2 = col / M, p = col % M;
-        g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2(re[c] * st, im[c] * st);
+        double gr = (double)re[c] * st, gi = (double)im[c] * st;
+        if (k1 == k2) {
+          const zc bp = bproj[((size_t)k1 * M + p) * n + a];
+          gr += bp.x;
+          gi += bp.y;
+        }
+        g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2((float)gr, (float)gi);
       }
     }
   }
@@ -410,76 +420,108 @@ struct ExchangeP {
 // conversion kernels
 // ---------------------------------------------------------------------------
 
-// phi [WS][NM][N] (FP64) -> phi_sp [WS][4][NM][Np]
-__global__ void split_phi_kernel(const zc* phi, __half* out, float* scale, int NM, int N, int Np) {
-  const int ws = blockIdx.x;
+// ---- two-pass splits: block-parallel max |.| (atomic max on the bit pattern of a
+// non-negative double), then a block-parallel split with the resulting scale.
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
+  atomicMax(a, static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+__device__ __forceinline__ float scale_from_bits(const unsigned long long* a) {
+  return pow2_scale(__longlong_as_double(static_cast<long long>(*a)));
+}
+
+// max |.| over each of nmat contiguous arrays of `per` complex doubles; grid (nmat, chunks)
+__global__ void maxabs_kernel(const zc* src, size_t per, unsigned long long* out) {
   __shared__ double red[32];
-  const zc* p = phi + (size_t)ws * NM * N;
+  const size_t chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+  const zc* p = src + (size_t)blockIdx.x * per;
   double m = 0.0;
-  for (size_t e = threadIdx.x; e < (size_t)NM * N; e += blockDim.x) m = fmax(m, cabs_d(p[e]));
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) m = fmax(m, cabs_d(p[e]));
   m = block_max(m, red);
-  const float s = pow2_scale(m);
-  if (threadIdx.x == 0) scale[ws] = s;
-  const size_t ps = (size_t)NM * Np;
-  __half* o = out + (size_t)ws * 4 * ps;
-  for (size_t e = threadIdx.x; e < (size_t)NM * N; e += blockDim.x) {
-    const size_t i = e / N, j = e % N;
-    put4(o, ps, i * Np + j, p[e].x, p[e].y, s);
+  if (threadIdx.x == 0) atomic_max_pos(out + blockIdx.x, m);
+}
+
+// src[m][rows][cols] (FP64) -> dst[m][4][rows][ldd] with the per-matrix scale; grid (nmat, chunks)
+__global__ void split_rows_kernel(const zc* src, int rows, int cols, int ldd, const unsigned long long* mx,
+                                  float* scale, __half* dst) {
+  const int mI = blockIdx.x;
+  const float s = scale_from_bits(mx + mI);
+  if (blockIdx.y == 0 && threadIdx.x == 0) scale[mI] = s;
+  const size_t per = (size_t)rows * cols, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+  const zc* p = src + (size_t)mI * per;
+  const size_t ps = (size_t)rows * ldd;
+  __half* o = dst + (size_t)mI * 4 * ps;
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+    const size_t i = e / cols, j = e % cols;
+    put4(o, ps, i * ldd + j, p[e].x, p[e].y, s);
   }
 }
 
-// Sinv [WS][N][N] (FP64) -> split planes of Sinv^T [WS][4][N][Np]
-__global__ void split_sinvT_kernel(const zc* Sinv, __half* out, float* scale, int N, int Np) {
+// Sinv [WS][N][N] (FP64) -> split planes of Sinv^T [WS][4][N][Np]; grid (WS, chunks)
+__global__ void split_sinvT_kernel(const zc* Sinv, const unsigned long long* mx, float* scale, __half* out, int N,
+                                   int Np) {
   const int ws = blockIdx.x;
-  __shared__ double red[32];
+  const float s = scale_from_bits(mx + ws);
+  if (blockIdx.y == 0 && threadIdx.x == 0) scale[ws] = s;
+  const int per = N * N, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const int b = blockIdx.y * chunk, e_end = min(per, b + chunk);
   const zc* p = Sinv + (size_t)ws * N * N;
-  double m = 0.0;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) m = fmax(m, cabs_d(p[e]));
-  m = block_max(m, red);
-  const float s = pow2_scale(m);
-  if (threadIdx.x == 0) scale[ws] = s;
   const size_t ps = (size_t)N * Np;
   __half* o = out + (size_t)ws * 4 * ps;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+  for (int e = b + threadIdx.x; e < e_end; e += blockDim.x) {
     const int i = e / N, j = e % N;   // out row i, col j = Sinv[j][i]
     const zc v = p[(size_t)j * N + i];
     put4(o, ps, (size_t)i * Np + j, v.x, v.y, s);
   }
 }
 
-// g32 [Nk][Nk][WS][n][Mp] -> g_sp (per walker-spin scale) and gsum_sp (spin sum, per walker scale)
-__global__ void split_green_kernel(const float2* g32, __half* gsp, float* s_g, __half* gsum, float* s_gsum, int nk,
-                                   int W, int nMp) {
-  const int w = blockIdx.x;
-  const int WS = 2 * W;
+// max |.| of g32 per walker-spin and of the spin sum per walker; grid (W, chunks)
+__global__ void green_max_kernel(const float2* g32, unsigned long long* mx, int nk, int W, int nMp) {
+  const int w = blockIdx.x, WS = 2 * W;
   __shared__ double red[32];
-  const size_t per = (size_t)nk * nk * nMp;
+  const size_t per = (size_t)nk * nk * nMp, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
   double m0 = 0.0, m1 = 0.0, ms = 0.0;
-  for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
     const size_t blk = e / nMp, off = e % nMp;
     const float2 a = g32[(blk * WS + 2 * w) * nMp + off];
-    const float2 b = g32[(blk * WS + 2 * w + 1) * nMp + off];
+    const float2 c = g32[(blk * WS + 2 * w + 1) * nMp + off];
     m0 = fmax(m0, cabs_f(a));
-    m1 = fmax(m1, cabs_f(b));
-    ms = fmax(ms, fmax(fabs((double)a.x + b.x), fabs((double)a.y + b.y)));
+    m1 = fmax(m1, cabs_f(c));
+    ms = fmax(ms, fmax(fabs((double)a.x + c.x), fabs((double)a.y + c.y)));
   }
   m0 = block_max(m0, red);
   m1 = block_max(m1, red);
   ms = block_max(ms, red);
-  const float s0 = pow2_scale(m0), s1 = pow2_scale(m1), ss = pow2_scale(ms);
   if (threadIdx.x == 0) {
+    atomic_max_pos(mx + 3 * w, m0);
+    atomic_max_pos(mx + 3 * w + 1, m1);
+    atomic_max_pos(mx + 3 * w + 2, ms);
+  }
+}
+
+// g32 [Nk][Nk][WS][n][Mp] -> g_sp (per walker-spin scale) and gsum_sp (spin sum, per walker scale)
+__global__ void split_green_kernel(const float2* g32, const unsigned long long* mx, __half* gsp, float* s_g,
+                                   __half* gsum, float* s_gsum, int nk, int W, int nMp) {
+  const int w = blockIdx.x, WS = 2 * W;
+  const float s0 = scale_from_bits(mx + 3 * w), s1 = scale_from_bits(mx + 3 * w + 1),
+              ss = scale_from_bits(mx + 3 * w + 2);
+  if (blockIdx.y == 0 && threadIdx.x == 0) {
     s_g[2 * w] = s0;
     s_g[2 * w + 1] = s1;
     s_gsum[w] = ss;
   }
+  const size_t per = (size_t)nk * nk * nMp, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
   const size_t psg = (size_t)nk * nk * WS * nMp, pss = (size_t)nk * nk * W * nMp;
-  for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
     const size_t blk = e / nMp, off = e % nMp;
     const float2 a = g32[(blk * WS + 2 * w) * nMp + off];
-    const float2 b = g32[(blk * WS + 2 * w + 1) * nMp + off];
+    const float2 c = g32[(blk * WS + 2 * w + 1) * nMp + off];
     put4(gsp, psg, (blk * WS + 2 * w) * nMp + off, a.x, a.y, s0);
-    put4(gsp, psg, (blk * WS + 2 * w + 1) * nMp + off, b.x, b.y, s1);
-    put4(gsum, pss, (blk * W + w) * nMp + off, (double)a.x + b.x, (double)a.y + b.y, ss);
+    put4(gsp, psg, (blk * WS + 2 * w + 1) * nMp + off, c.x, c.y, s1);
+    put4(gsum, pss, (blk * W + w) * nMp + off, (double)a.x + c.x, (double)a.y + c.y, ss);
   }
 }
 
@@ -534,24 +576,6 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* a
   }
 }
 
-// acc [W][R][NM] -> t_sp [W][4][R][NMp] with a per-walker scale
-__global__ void split_acc_kernel(const double2* acc, __half* out, float* s_t, int R, int NM, int NMp) {
-  const int w = blockIdx.x;
-  __shared__ double red[32];
-  const double2* a = acc + (size_t)w * R * NM;
-  double m = 0.0;
-  for (size_t e = threadIdx.x; e < (size_t)R * NM; e += blockDim.x) m = fmax(m, fmax(fabs(a[e].x), fabs(a[e].y)));
-  m = block_max(m, red);
-  const float s = pow2_scale(m);
-  if (threadIdx.x == 0) s_t[w] = s;
-  const size_t ps = (size_t)R * NMp;
-  __half* o = out + (size_t)w * 4 * ps;
-  for (size_t e = threadIdx.x; e < (size_t)R * NM; e += blockDim.x) {
-    const size_t j = e / NM, i = e % NM;
-    put4(o, ps, j * NMp + i, a[e].x, a[e].y, s);
-  }
-}
-
 // phi[w][s][(k,p)][j] = acc + sum_q D[k][p][q] acc[(k,q)] with acc[w][s*N + j][(k, .)]
 __global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* phi, int nk, int M, int N, int NM) {
   const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
@@ -579,6 +603,60 @@ __global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* 
     }
     const double2 id = blk[j * M + p];
     dst[(size_t)(k * M + p) * N + j0 + j] = make_double2(id.x + cr, id.y + ci);
+  }
+}
+
+// B[k] = A[k] (A[k]^dag A[k])^-1 by Gauss-Jordan on the Hermitian positive definite
+// Gram matrix (no pivoting needed); one block per k; scratch [nk][n][2n].
+__global__ void trial_projector_kernel(const zc* A, zc* B, zc* scratch, int M, int n) {
+  const int k = blockIdx.x;
+  const zc* Ak = A + (size_t)k * M * n;
+  zc* aug = scratch + (size_t)k * n * 2 * n;  // [n][2n] = [Gram | I]
+  for (int e = threadIdx.x; e < n * 2 * n; e += blockDim.x) {
+    const int i = e / (2 * n), j = e % (2 * n);
+    zc v = zzero();
+    if (j < n) {
+      for (int p = 0; p < M; ++p) v = zfma(zconj(Ak[p * n + i]), Ak[p * n + j], v);
+    } else {
+      v = zmake(i == j - n ? 1.0 : 0.0, 0.0);
+    }
+    aug[e] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const zc inv = zinv(aug[j * 2 * n + j]);
+    __syncthreads();
+    for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) aug[j * 2 * n + c] = zmul(aug[j * 2 * n + c], inv);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * 2 * n; e += blockDim.x) {
+      const int i = e / (2 * n), c = e % (2 * n);
+      if (i != j) {
+        const zc f = aug[i * 2 * n + j];
+        aug[e] = zsub(aug[e], zmul(f, aug[j * 2 * n + c]));
+      }
+    }
+    __syncthreads();
+  }
+  // B = A Ginv
+  for (int e = threadIdx.x; e < M * n; e += blockDim.x) {
+    const int p = e / n, a = e % n;
+    zc v = zzero();
+    for (int b = 0; b < n; ++b) v = zfma(Ak[p * n + b], aug[b * 2 * n + n + a], v);
+    B[(size_t)k * M * n + e] = v;
+  }
+}
+
+// phi_perp[ws][(k,p)][j] = phi[ws][(k,p)][j] - sum_a B[k][p][a] S[ws][(k,a)][j]  (FP64); grid (ws, k)
+__global__ void project_kernel(const zc* phi, const zc* S, const zc* B, zc* out, int nk, int M, int n, int N) {
+  const int ws = blockIdx.x, k = blockIdx.y;
+  const zc* Bk = B + (size_t)k * M * n;
+  const zc* Sk = S + ((size_t)ws * N + (size_t)k * n) * N;
+  const size_t base = ((size_t)ws * nk * M + (size_t)k * M) * N;
+  for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
+    const int p = e / N, j = e % N;
+    zc v = phi[base + e];
+    for (int a = 0; a < n; ++a) v = zsub(v, zmul(Bk[p * n + a], Sk[(size_t)a * N + j]));
+    out[base + e] = v;
   }
 }
 
@@ -774,6 +852,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->acc, (size_t)W * 2 * N * NM, true, st));
   MTRY(dalloc(h, &m->xpart, (size_t)T * ntx * WS, true, st));
   MTRY(dalloc(h, &m->xk, (size_t)nk * W * nk * G, true, st));
+  MTRY(dalloc(h, &m->mx, (size_t)2 * WS + 3 * W + W, true, st));
   MTRY(dalloc(h, &m->lh_sp, (size_t)4 * nk * nk * G * nMp, true, st));
   MTRY(dalloc(h, &m->s_lh, (size_t)nk * G, true, st));
   MTRY(dalloc(h, &m->lt_sp, (size_t)4 * nk * nk * M * M * Gp, true, st));
@@ -782,10 +861,14 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->s_z, T, true, st));
   MTRY(dalloc(h, &m->tri, T, false, st));
   MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
+  MTRY(dalloc(h, &m->bproj, (size_t)nk * M * n, true, st));
   const int zctas = std::min(T, ZCTAS);
-  MTRY(dalloc(h, &m->zscratch, (size_t)zctas * nM * nM, false, st));
+  MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
   MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
 
+  // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
+  trial_projector_kernel<<<nk, 256, 0, st>>>(h->A, m->bproj, m->zscratch, M, n);
+  AFQMC_LAUNCHED(h);
   // static split operands and the precontracted exchange tensor
   static_scales_kernel<<<dim3(nk, G), 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, nk, G, M, n);
   AFQMC_LAUNCHED(h);
@@ -848,26 +931,48 @@ cudaError_t set_one_body(afqmc_kp* h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+constexpr int SPLIT_CHUNKS = 16;  // blocks per matrix in the split kernels
+
 // overlap + LU + inverse (FP64), split operands, Gh GEMM, split Gh
 static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
   MixedState* m = h->mixed;
   int* err = h->flags + 1;
-  MTRY(fp64::overlap_lu(h, phi, ld, sing, 1, st));
-  split_phi_kernel<<<m->WS, 256, 0, st>>>(phi, m->phi_sp, m->s_phi, h->NM, h->N, m->Np);
+  const int WS = m->WS;
+  unsigned long long* mx_phi = m->mx;
+  unsigned long long* mx_sinv = m->mx + WS;
+  unsigned long long* mx_g = m->mx + 2 * WS;
+  // phi (A^dag phi)^-1 = B + phi_perp S^-1 with B = A (A^dag A)^-1 and phi_perp = phi - B S:
+  // the trial-subspace part is exact, so the split GEMM never forms the large
+  // cancelling partial sums of S^-1 (A^dag phi) = I.
+  zc* phi_perp = reinterpret_cast<zc*>(m->acc);  // free until the Taylor series
+  MTRY(fp64::overlap_only(h, phi, st));
+  project_kernel<<<dim3(WS, h->nk), 256, 0, st>>>(phi, h->S, m->bproj, phi_perp, h->nk, h->M, h->n, h->N);
   AFQMC_LAUNCHED(h);
-  split_sinvT_kernel<<<m->WS, 256, 0, st>>>(h->Sinv, m->sinvt_sp, m->s_sinv, h->N, m->Np);
+  MTRY(fp64::lu_only(h, ld, sing, 1, st));
+  MTRY(cudaMemsetAsync(m->mx, 0, sizeof(unsigned long long) * (2 * WS + 3 * h->W), st));
+  maxabs_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi_perp, (size_t)h->NM * h->N, mx_phi);
+  AFQMC_LAUNCHED(h);
+  maxabs_kernel<<<dim3(WS, 4), 256, 0, st>>>(h->Sinv, (size_t)h->N * h->N, mx_sinv);
+  AFQMC_LAUNCHED(h);
+  split_rows_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi_perp, h->NM, h->N, m->Np, mx_phi, m->s_phi,
+                                                             m->phi_sp);
+  AFQMC_LAUNCHED(h);
+  split_sinvT_kernel<<<dim3(WS, 4), 256, 0, st>>>(h->Sinv, mx_sinv, m->s_sinv, m->sinvt_sp, h->N, m->Np);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
   GreenP p;
   p.mt_n = cdiv(h->N, 128);
   p.nt_n = cdiv(h->NM, BN);
-  p.tiles = m->WS * p.mt_n * p.nt_n;
+  p.tiles = WS * p.mt_n * p.nt_n;
   p.kchunks = m->Np / 32;
-  p.N = h->N; p.NM = h->NM; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nk = h->nk; p.WS = m->WS;
-  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.g32 = m->g32;
+  p.N = h->N; p.NM = h->NM; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nk = h->nk; p.WS = WS;
+  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.bproj = m->bproj; p.g32 = m->g32;
   MTRY(run_gemm(m->m_sinvt, m->m_phi, p, err, st));
   AFQMC_LAUNCHED(h);
-  split_green_kernel<<<h->W, 256, 0, st>>>(m->g32, m->g_sp, m->s_g, m->gsum_sp, m->s_gsum, h->nk, h->W, m->nMp);
+  green_max_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->g32, mx_g, h->nk, h->W, m->nMp);
+  AFQMC_LAUNCHED(h);
+  split_green_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->g32, mx_g, m->g_sp, m->s_g, m->gsum_sp, m->s_gsum,
+                                                                h->nk, h->W, m->nMp);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }
@@ -924,7 +1029,11 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   dim3 g1(h->nk, m->WS, cdiv(h->N, 64));
   onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, m->acc, h->nk, h->M, h->N, h->NM);
   AFQMC_LAUNCHED(h);
-  split_acc_kernel<<<h->W, 256, 0, st>>>(m->acc, m->t_sp[0], m->s_t, R, h->NM, m->NMp);
+  unsigned long long* mx_acc = m->mx + 2 * m->WS + 3 * h->W;
+  MTRY(cudaMemsetAsync(mx_acc, 0, sizeof(unsigned long long) * h->W, st));
+  maxabs_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->acc, (size_t)R * h->NM, mx_acc);
+  AFQMC_LAUNCHED(h);
+  split_rows_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->acc, R, h->NM, m->NMp, mx_acc, m->s_t, m->t_sp[0]);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
   for (int j = 1; j <= h->order; ++j) {
@@ -980,24 +1089,16 @@ cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
   return e;
 }
 
-cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) {
+static cudaError_t e1_ec(afqmc_kp* h, zc* eloc, cudaStream_t st) {
   MixedState* m = h->mixed;
-  cudaError_t e;
-  prof_begin(h, AFQMC_STAGE_GREEN, st);
-  e = green(h, phi, h->ld_old, h->sing_old, st);
-  prof_end(h, st);
-  if (e != cudaSuccess) return e;
-  prof_begin(h, AFQMC_STAGE_FORCE_BIAS, st);
-  e = cholesky_trace(h, st);
-  prof_end(h, st);
-  if (e != cudaSuccess) return e;
-  prof_begin(h, AFQMC_STAGE_ENERGY, st);
   e1_ec_mixed_kernel<<<h->W, 256, 0, st>>>(h->AhH, m->g32, h->X, h->minus, eloc, h->nk, h->M, h->n, m->Mp, h->G,
                                             m->WS);
   AFQMC_LAUNCHED(h);
-  e = cudaGetLastError();
-  prof_end(h, st);
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+static cudaError_t exchange(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
   ExchangeP p;
   p.mt_n = cdiv(m->WS, 128);
   p.nt_n = cdiv(m->nM, BN);
@@ -1006,17 +1107,61 @@ cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) 
   p.WS = m->WS; p.nk = h->nk; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nM = m->nM;
   p.kminus = h->kminus; p.minus = h->minus; p.tri = m->tri; p.s_g = m->s_g; p.s_z = m->s_z; p.g32 = m->g32;
   p.xpart = m->xpart;
-  prof_begin(h, AFQMC_STAGE_EXCHANGE, st);
-  e = run_gemm(m->m_g, m->m_z, p, h->flags + 1, st);
+  MTRY(run_gemm(m->m_g, m->m_z, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
-  prof_end(h, st);
-  if (e != cudaSuccess) return e;
-  prof_begin(h, AFQMC_STAGE_ENERGY, st);
-  ex_reduce_mixed_kernel<<<h->W, 256, 0, st>>>(m->xpart, m->tri, eloc, m->T, p.nt_n, m->WS);
+  return cudaSuccess;
+}
+
+static cudaError_t ex_reduce(afqmc_kp* h, zc* eloc, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  ex_reduce_mixed_kernel<<<h->W, 256, 0, st>>>(m->xpart, m->tri, eloc, m->T, cdiv(m->nM, BN), m->WS);
   AFQMC_LAUNCHED(h);
-  e = cudaGetLastError();
-  prof_end(h, st);
-  return e;
+  return cudaGetLastError();
+}
+
+#define MSTAGE(stage, body)           \
+  do {                                \
+    prof_begin(h, stage, st);         \
+    cudaError_t e_ = (body);          \
+    prof_end(h, st);                  \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st) {
+  MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_old, h->sing_old, st));
+  MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+  MSTAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
+  MSTAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
+  MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  return cudaSuccess;
+}
+
+// One fused walker step (see fp64::step): the Green's function of the
+// propagated walkers serves their log det, their energy and the next force bias.
+cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc* logdet, int do_qr, int reuse,
+                 cudaStream_t st) {
+  if (!reuse) {
+    MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_old, h->sing_old, st));
+    MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+  }
+  MSTAGE(AFQMC_STAGE_FORCE_BIAS, fp64::force_bias(h, x, h->xbar, st));
+  MSTAGE(AFQMC_STAGE_VHS, vhs(h, st));
+  MSTAGE(AFQMC_STAGE_TAYLOR, taylor(h, phi, st));
+  MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_new, h->sing_new, st));
+  MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+  MSTAGE(AFQMC_STAGE_WEIGHT, fp64::weight_only(h, x, w, do_qr ? nullptr : logdet, st));
+  MSTAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
+  MSTAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
+  MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  if (do_qr) {
+    MSTAGE(AFQMC_STAGE_QR, fp64::qr_with(h, phi, reinterpret_cast<zc*>(h->mixed->acc), st));
+    MSTAGE(AFQMC_STAGE_QR, fp64::overlap_lu(h, phi, h->ld_new, h->sing_new, 0, st));
+    if (logdet)
+      MTRY(cudaMemcpyAsync(logdet, h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, st));
+  }
+  std::swap(h->ld_old, h->ld_new);
+  std::swap(h->sing_old, h->sing_new);
+  return cudaSuccess;
 }
 
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,

@@ -11,6 +11,8 @@ cudaError_t force_bias(afqmc_kp* h, const zc* phi, zc* xbar, cudaStream_t st);
 cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr, cudaStream_t st);
 cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st);
 cudaError_t local_energy(afqmc_kp* h, const zc* phi, zc* eloc, cudaStream_t st);
+cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc* logdet, int do_qr, int reuse,
+                 cudaStream_t st);
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
                                   cudaStream_t st);
 }  // namespace mixed
