@@ -54,6 +54,7 @@ struct MixedState {
   zc* bproj = nullptr;                                   // [Nk][M][n] A (A^dag A)^-1 per k
   zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
+  CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
 };
 
@@ -178,6 +179,7 @@ struct NoRow {};
 // Gh[ws] = B^T + S^-T phi_perp^T : rows i = (k1, a), cols (k2, p); written to g32 in tile
 // layout.  B = A (A^dag A)^-1 and phi_perp = phi - B S (see green()).
 struct GreenP {
+  static constexpr bool kConjA = false;
   int tiles, kchunks;
   int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
   const float* s_sinv;
@@ -221,6 +223,7 @@ struct GreenP {
 // Splitting the k sum across tiles keeps every fp32 running sum short; the k
 // blocks are summed in FP64 by xsum_kernel.
 struct ForceBiasP {
+  static constexpr bool kConjA = false;
   int tiles, kchunks;
   int mt_n, nt_n, W, G, nk;
   const int* kminus;
@@ -273,6 +276,7 @@ __global__ void xsum_kernel(const double2* Xk, zc* X, int nk, size_t per) {
 
 // V[w][(k,p)][(k-Q,r)] = sum_g y[w,Q,g] L[Q,k,g,p,r]  -> split planes with a fixed scale
 struct VhsP {
+  static constexpr bool kConjA = false;
   int tiles, kchunks;
   int mt_n, nt_n, W, M, nk, NM, NMp;
   const int* kminus;
@@ -319,6 +323,7 @@ struct VhsP {
 
 // One Taylor term: T_j[w] = V[w] T_{j-1}[w] / j in transposed form (rows j' = (spin, column)).
 struct TaylorP {
+  static constexpr bool kConjA = false;
   int tiles, kchunks;
   int mt_n, nt_n, R, NM, NMp;
   float inv_j;
@@ -367,6 +372,7 @@ struct ExchangeRow {
   const float2* g2;
 };
 struct ExchangeP {
+  static constexpr bool kConjA = false;
   int tiles, kchunks;
   int mt_n, nt_n, WS, nk, n, M, Mp, nM;
   const int* kminus;
@@ -414,6 +420,71 @@ struct ExchangeP {
     const int ws = mt * 128 + r;
     if (ws < WS) xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2(st.re, st.im);
   }
+};
+
+// Gram[ws] = phi_ws^dag phi_ws from the transposed split planes (rows = columns of phi).
+struct GramP {
+  static constexpr bool kConjA = true;
+  int tiles, kchunks;
+  int mt_n, nt_n, N;
+  const float* s_t;   // per walker
+  double2* gram;      // [WS][N][N]
+  typedef float Row;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ tcg::Coords coords(int ws, int mt, int nt, int kc) const {
+    const int w = ws >> 1, sp = ws & 1;
+    tcg::Coords c = {{kc * 32, sp * N + mt * 128, 0, w, 0}, {kc * 32, sp * N + nt * BN, 0, w, 0}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int ws, int, int, int) const {
+    const float sc = s_t[ws >> 1];
+    st = 1.f / (sc * sc);
+  }
+  __device__ void chunk(Row& st, int ws, int mt, int nt, int r, int c0, const float* re, const float* im) const {
+    const int i = mt * 128 + r;
+    if (i >= N) return;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int j = nt * BN + c0 + c;
+      if (j < N) gram[((size_t)ws * N + i) * N + j] = make_double2((double)re[c] * st, (double)im[c] * st);
+    }
+  }
+  __device__ void row_end(Row&, int, int, int, int) const {}
+};
+
+// phi[ws] <- phi[ws] R^-1 : rows r = (k,p), columns j; B = (R^-1)^T split planes.
+struct ApplyRP {
+  static constexpr bool kConjA = false;
+  int tiles, kchunks;
+  int mt_n, nt_n, NM, N;
+  const float* s_phi;
+  const float* s_r;
+  zc* phi;
+  typedef float Row;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ tcg::Coords coords(int ws, int mt, int nt, int kc) const {
+    tcg::Coords c = {{kc * 32, mt * 128, 0, ws, 0}, {kc * 32, nt * BN, 0, ws, 0}};
+    return c;
+  }
+  __device__ void row_begin(Row& st, int ws, int, int, int) const { st = 1.f / (s_phi[ws] * s_r[ws]); }
+  __device__ void chunk(Row& st, int ws, int mt, int nt, int r, int c0, const float* re, const float* im) const {
+    const int row = mt * 128 + r;
+    if (row >= NM) return;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int j = nt * BN + c0 + c;
+      if (j < N) phi[((size_t)ws * NM + row) * N + j] = make_double2((double)re[c] * st, (double)im[c] * st);
+    }
+  }
+  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
 // ---------------------------------------------------------------------------
@@ -660,6 +731,88 @@ __global__ void project_kernel(const zc* phi, const zc* S, const zc* B, zc* out,
   }
 }
 
+// phi [W][2][NM][N] (FP64) -> transposed split planes [W][4][2N][NMp] (rows = (spin, column)),
+// per-walker scale; grid (W, chunks)
+__global__ void split_T_kernel(const zc* phi, const unsigned long long* mx, float* scale, __half* out, int NM, int N,
+                               int NMp) {
+  const int w = blockIdx.x;
+  const float s = scale_from_bits(mx + w);
+  if (blockIdx.y == 0 && threadIdx.x == 0) scale[w] = s;
+  const size_t per = (size_t)2 * NM * N, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+  const zc* p = phi + (size_t)w * per;
+  const size_t ps = (size_t)2 * N * NMp;
+  __half* o = out + (size_t)w * 4 * ps;
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+    const size_t sp = e / ((size_t)NM * N), r = (e / N) % NM, j = e % N;
+    put4(o, ps, (sp * N + j) * NMp + r, p[e].x, p[e].y, s);
+  }
+}
+
+// Gram = R^dag R (Cholesky, FP64, upper R in place), X = R^-1 (FP64, into X), and the
+// split planes of X^T [WS][4][N][Np] with a per-ws scale.  One block per walker-spin.
+// A Gram matrix that is not positive definite leaves X = I (the walker is kept) and
+// is counted with the singular walkers.
+__global__ void __launch_bounds__(256) chol_inv_kernel(zc* gram, zc* X, __half* out, float* scale, int* flags, int N,
+                                                       int Np) {
+  const int ws = blockIdx.x;
+  zc* G = gram + (size_t)ws * N * N;
+  zc* Xw = X + (size_t)ws * N * N;
+  __shared__ int s_fail;
+  __shared__ double red[32];
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < N; ++j) {
+    const double d = G[(size_t)j * N + j].x;
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) s_fail = 1;
+      __syncthreads();
+      break;
+    }
+    const double rjj = sqrt(d);
+    for (int c = j + 1 + threadIdx.x; c < N; c += blockDim.x) G[(size_t)j * N + c] = zscale(G[(size_t)j * N + c], 1.0 / rjj);
+    __syncthreads();
+    if (threadIdx.x == 0) G[(size_t)j * N + j] = zmake(rjj, 0.0);
+    const int rem = N - j - 1;
+    for (long e = threadIdx.x; e < (long)rem * rem; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / rem), c = j + 1 + (int)(e % rem);
+      if (c >= i) G[(size_t)i * N + c] = zsub(G[(size_t)i * N + c], zmul(zconj(G[(size_t)j * N + i]), G[(size_t)j * N + c]));
+    }
+    __syncthreads();
+  }
+  const int fail = s_fail;
+  if (fail && threadIdx.x == 0) atomicAdd(&flags[0], 1);
+  // X = R^-1 (upper triangular), one column per thread
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    for (int i = N - 1; i >= 0; --i) {
+      zc v = zzero();
+      if (fail) {
+        v = zmake(i == c ? 1.0 : 0.0, 0.0);
+      } else if (i == c) {
+        v = zinv(G[(size_t)c * N + c]);
+      } else if (i < c) {
+        zc sum = zzero();
+        for (int l = i + 1; l <= c; ++l) sum = zfma(G[(size_t)i * N + l], Xw[(size_t)l * N + c], sum);
+        v = zmul(zmake(-sum.x, -sum.y), zinv(G[(size_t)i * N + i]));
+      }
+      Xw[(size_t)i * N + c] = v;
+    }
+  }
+  __syncthreads();
+  double m = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) m = fmax(m, cabs_d(Xw[e]));
+  m = block_max(m, red);
+  const float sc = pow2_scale(m);
+  if (threadIdx.x == 0) scale[ws] = sc;
+  const size_t ps = (size_t)N * Np;
+  __half* o = out + (size_t)ws * 4 * ps;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int jrow = e / N, i = e % N;  // (X^T)[j][i] = X[i][j]
+    const zc v = Xw[(size_t)i * N + jrow];
+    put4(o, ps, (size_t)jrow * Np + i, v.x, v.y, sc);
+  }
+}
+
 // dhalf = Ehalf - I in fp32
 __global__ void dhalf_kernel(const zc* Ehalf, float2* d, int nk, int M) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nk * M * M;
@@ -902,6 +1055,12 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
             {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
   MTRY(map5(&m->m_z, m->z_sp, {(uint64_t)nMp, (uint64_t)nM, 4, (uint64_t)T, 1},
             {(uint64_t)nMp, (uint64_t)T * nM * nMp, (uint64_t)nM * nMp, (uint64_t)T * nM * nMp * 4}, BN));
+  MTRY(map5(&m->m_phi_a, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
+            {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, 128));
+  MTRY(map5(&m->m_sinvt_b, m->sinvt_sp, {(uint64_t)Np, (uint64_t)N, 4, (uint64_t)WS, 1},
+            {(uint64_t)Np, (uint64_t)N * Np, (uint64_t)4 * N * Np, (uint64_t)WS * 4 * N * Np}, BN));
+  MTRY(map5(&m->m_t0_b, m->t_sp[0], {(uint64_t)NMp, (uint64_t)2 * N, 4, (uint64_t)W, 1},
+            {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, BN));
   MTRY(set_smem_attr((const void*)onebody_in_kernel, onebody_smem(h)));
   MTRY(set_smem_attr((const void*)onebody_out_kernel, onebody_smem(h)));
   return cudaSuccess;
@@ -1081,9 +1240,51 @@ cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logd
   return cudaSuccess;
 }
 
+// Cholesky-QR2: twice { Gram = phi^dag phi on the tensor cores; R = chol(Gram) and R^-1 in
+// FP64; phi <- phi R^-1 on the tensor cores }.  R has a real positive diagonal, so
+// phi ends as the unique Q factor of the Householder QR with diag(R) > 0.
+static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  const int WS = m->WS, N = h->N, NM = h->NM, W = h->W;
+  unsigned long long* mx_phi = m->mx;
+  unsigned long long* mx_w = m->mx + 2 * WS + 3 * W;
+  for (int pass = 0; pass < 2; ++pass) {
+    MTRY(cudaMemsetAsync(m->mx, 0, sizeof(unsigned long long) * (2 * WS + 3 * W + W), st));
+    maxabs_kernel<<<dim3(W, SPLIT_CHUNKS), 256, 0, st>>>(phi, (size_t)2 * NM * N, mx_w);
+    AFQMC_LAUNCHED(h);
+    split_T_kernel<<<dim3(W, SPLIT_CHUNKS), 256, 0, st>>>(phi, mx_w, m->s_t, m->t_sp[0], NM, N, m->NMp);
+    AFQMC_LAUNCHED(h);
+    MTRY(cudaGetLastError());
+    GramP g;
+    g.mt_n = cdiv(N, 128);
+    g.nt_n = cdiv(N, BN);
+    g.tiles = WS * g.mt_n * g.nt_n;
+    g.kchunks = m->NMp / 32;
+    g.N = N; g.s_t = m->s_t; g.gram = h->P;
+    MTRY(run_gemm(m->m_t[0], m->m_t0_b, g, h->flags + 1, st));
+    AFQMC_LAUNCHED(h);
+    chol_inv_kernel<<<WS, 256, 0, st>>>(h->P, h->Sinv, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np);
+    AFQMC_LAUNCHED(h);
+    maxabs_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, (size_t)NM * N, mx_phi);
+    AFQMC_LAUNCHED(h);
+    split_rows_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, NM, N, m->Np, mx_phi, m->s_phi, m->phi_sp);
+    AFQMC_LAUNCHED(h);
+    MTRY(cudaGetLastError());
+    ApplyRP a;
+    a.mt_n = cdiv(NM, 128);
+    a.nt_n = cdiv(N, BN);
+    a.tiles = WS * a.mt_n * a.nt_n;
+    a.kchunks = m->Np / 32;
+    a.NM = NM; a.N = N; a.s_phi = m->s_phi; a.s_r = m->s_sinv; a.phi = phi;
+    MTRY(run_gemm(m->m_phi_a, m->m_sinvt_b, a, h->flags + 1, st));
+    AFQMC_LAUNCHED(h);
+  }
+  return cudaSuccess;
+}
+
 cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
   prof_begin(h, AFQMC_STAGE_QR, st);
-  cudaError_t e = fp64::qr_with(h, phi, reinterpret_cast<zc*>(h->mixed->acc), st);
+  cudaError_t e = cholqr2(h, phi, st);
   if (e == cudaSuccess && logdet) e = fp64::overlap_lu(h, phi, logdet, h->sing_new, 0, st);
   prof_end(h, st);
   return e;
@@ -1154,7 +1355,7 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   MSTAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
   MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
   if (do_qr) {
-    MSTAGE(AFQMC_STAGE_QR, fp64::qr_with(h, phi, reinterpret_cast<zc*>(h->mixed->acc), st));
+    MSTAGE(AFQMC_STAGE_QR, cholqr2(h, phi, st));
     MSTAGE(AFQMC_STAGE_QR, fp64::overlap_lu(h, phi, h->ld_new, h->sing_new, 0, st));
     if (logdet)
       MTRY(cudaMemcpyAsync(logdet, h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, st));

@@ -57,6 +57,7 @@ struct Layout {
 //   __device__ void row_begin(Row&, int b, int mt, int nt, int r) const;
 //   __device__ void chunk(Row&, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const;
 //   __device__ void row_end(Row&, int b, int mt, int nt, int r) const;
+//   static constexpr bool kConjA;                 precise variant: D = sum conj(A) B instead
 // r is the row inside the tile (0..127), c0 the first of 16 columns inside the tile.
 template <int BN, int STAGES, class P>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -377,8 +378,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc::tmem_ld_wait();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          sre[g * 16 + c] += rr[c] - ii[c];
-          sim[g * 16 + c] += ri[c] + ir[c];
+          if (P::kConjA) {  // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+            sre[g * 16 + c] += rr[c] + ii[c];
+            sim[g * 16 + c] += ri[c] - ir[c];
+          } else {
+            sre[g * 16 + c] += rr[c] - ii[c];
+            sim[g * 16 + c] += ri[c] + ir[c];
+          }
         }
       }
       tc::fence_before_sync();
