@@ -52,6 +52,8 @@ struct MixedState {
   int4* tri = nullptr;                                   // [T] (Q, k, kx, weight)
   float2* dhalf = nullptr;                               // [Nk][M][M] exp(-dt/2 H1') - I
   zc* bproj = nullptr;                                   // [Nk][M][n] A (A^dag A)^-1 per k
+  float2* bproj32 = nullptr;                             // the same in fp32 (Green epilogue)
+  float* inv_s_lh = nullptr;                             // 1 / s_lh
   zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
@@ -79,20 +81,30 @@ __device__ __forceinline__ float pow2_scale(double maxabs) {
   return (float)ldexp(1.0, e);
 }
 
-// x*s split into hi = fp16(x*s) and lo = fp16(x*s - hi)
-__device__ __forceinline__ void split_val(double v, float s, __half& hi, __half& lo) {
-  const double xs = v * (double)s;
-  hi = __double2half(xs);
-  lo = __double2half(xs - (double)__half2float(hi));
+// x*s split into hi = fp16(x*s) and lo = fp16(x*s - hi), in fp32 (s is a power of two, so
+// x*s is exact; x*s - hi is exact in fp32).  FP64 arithmetic is avoided on purpose: the
+// FP64 pipe of this GPU is about 60x slower than FP32.
+__device__ __forceinline__ void split_val(float xs, __half& hi, __half& lo) {
+  hi = __float2half_rn(xs);
+  lo = __float2half_rn(xs - __half2float(hi));
 }
-__device__ __forceinline__ void put4(__half* base, size_t plane_stride, size_t idx, double re, double im, float s) {
+__device__ __forceinline__ void put4f(__half* base, size_t plane_stride, size_t idx, float re, float im) {
   __half h, l;
-  split_val(re, s, h, l);
+  split_val(re, h, l);
   base[idx] = h;
   base[plane_stride + idx] = l;
-  split_val(im, s, h, l);
+  split_val(im, h, l);
   base[2 * plane_stride + idx] = h;
   base[3 * plane_stride + idx] = l;
+}
+// FP64 input of moderate range: rounded once to fp32 (24 bits, of which the split keeps
+// 22), then scaled (per-step operands: walkers, inverses, Green's functions)
+__device__ __forceinline__ void put4(__half* base, size_t plane_stride, size_t idx, double re, double im, float s) {
+  put4f(base, plane_stride, idx, (float)re * s, (float)im * s);
+}
+// FP64 input of any range: scaled in FP64 first (set-up data only)
+__device__ __forceinline__ void put4d(__half* base, size_t plane_stride, size_t idx, double re, double im, float s) {
+  put4f(base, plane_stride, idx, (float)(re * (double)s), (float)(im * (double)s));
 }
 
 __device__ __forceinline__ double block_max(double v, double* red) {
@@ -184,7 +196,7 @@ struct GreenP {
   int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
   const float* s_sinv;
   const float* s_phi;
-  const zc* bproj;
+  const float2* bproj32;
   float2* g32;
   typedef float Row;  // inverse scale of the row's walker-spin
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
@@ -206,13 +218,13 @@ struct GreenP {
       const int col = nt * BN + c0 + c;
       if (col < NM) {
         const int k2 = col / M, p = col % M;
-        double gr = (double)re[c] * st, gi = (double)im[c] * st;
+        float gr = re[c] * st, gi = im[c] * st;
         if (k1 == k2) {
-          const zc bp = bproj[((size_t)k1 * M + p) * n + a];
+          const float2 bp = bproj32[((size_t)k1 * M + p) * n + a];
           gr += bp.x;
           gi += bp.y;
         }
-        g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2((float)gr, (float)gi);
+        g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2(gr, gi);
       }
     }
   }
@@ -228,7 +240,7 @@ struct ForceBiasP {
   int mt_n, nt_n, W, G, nk;
   const int* kminus;
   const float* s_gsum;
-  const float* s_lh;
+  const float* inv_s_lh;
   double2* Xk;  // [Nk(k)][W][Nk(Q)][G]
   typedef float Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
@@ -253,8 +265,8 @@ struct ForceBiasP {
     for (int c = 0; c < 16; ++c) {
       const int g = nt * BN + c0 + c;
       if (g < G) {
-        const double f = (double)st / (double)s_lh[Q * G + g];
-        Xk[(((size_t)k * W + w) * nk + Q) * G + g] = make_double2(re[c] * f, im[c] * f);
+        const float f = st * inv_s_lh[Q * G + g];
+        Xk[(((size_t)k * W + w) * nk + Q) * G + g] = make_double2((double)(re[c] * f), (double)(im[c] * f));
       }
     }
   }
@@ -313,7 +325,7 @@ struct VhsP {
         const size_t idx = (size_t)(k * M + p) * NMp + kq * M + rr;
         const float vr = re[c] * st, vi = im[c] * st;
         bad |= !(fabsf(vr) < 60000.f && fabsf(vi) < 60000.f);
-        put4(base, ps, idx, vr, vi, 1.f);
+        put4f(base, ps, idx, vr, vi);
       }
     }
     if (bad) atomicExch(overflow, 1);
@@ -344,7 +356,7 @@ struct TaylorP {
   __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
     const int j = mt * 128 + r;
     if (j >= R) return;
-    const float s = s_t[b];
+    const float inv_s = 1.f / s_t[b];   // power of two: exact
     const size_t ps = (size_t)R * NMp;
     __half* tb = t_next + (size_t)b * 4 * ps;
     double2* ab = acc + ((size_t)b * R + j) * NM;
@@ -353,12 +365,12 @@ struct TaylorP {
       const int i = nt * BN + c0 + c;
       if (i < NM) {
         // D carries the operand scales s_t (A) and V_SCALE (B); st removes V_SCALE and applies 1/j
-        const double tr = (double)re[c] * st, ti = (double)im[c] * st;   // = T_j * s_t
+        const float tr = re[c] * st, ti = im[c] * st;   // = T_j * s_t
         double2 a = ab[i];
-        a.x += tr / s;
-        a.y += ti / s;
+        a.x += (double)(tr * inv_s);
+        a.y += (double)(ti * inv_s);
         ab[i] = a;
-        put4(tb, ps, (size_t)j * NMp + i, tr, ti, 1.f);
+        put4f(tb, ps, (size_t)j * NMp + i, tr, ti);
       }
     }
   }
@@ -367,7 +379,7 @@ struct TaylorP {
 
 // Exchange: rows = walker-spins, cols = (a, s) of Z_t; epilogue dots with Gh[(k,a),(kx+Q,s)].
 struct ExchangeRow {
-  double re, im;
+  float re[4], im[4];   // four interleaved fp32 partial sums of the 64-column dot product
   float inv;
   const float2* g2;
 };
@@ -395,7 +407,8 @@ struct ExchangeP {
   }
   __device__ void row_begin(Row& st, int t, int mt, int, int r) const {
     const int ws = mt * 128 + r;
-    st.re = st.im = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) st.re[u] = st.im[u] = 0.f;
     if (ws >= WS) { st.inv = 0.f; st.g2 = nullptr; return; }
     const int4 q = tri[t];
     const int kxq = kminus[q.z * nk + minus[q.x]];  // kx + Q
@@ -410,15 +423,18 @@ struct ExchangeP {
       if (col < nM) {
         const int a = col / M, s = col % M;
         const float2 g = st.g2[a * Mp + s];
-        const double yr = (double)re[c] * st.inv, yi = (double)im[c] * st.inv;
-        st.re += yr * g.x - yi * g.y;
-        st.im += yr * g.y + yi * g.x;
+        const float yr = re[c] * st.inv, yi = im[c] * st.inv;
+        st.re[c & 3] = fmaf(yr, g.x, fmaf(-yi, g.y, st.re[c & 3]));
+        st.im[c & 3] = fmaf(yr, g.y, fmaf(yi, g.x, st.im[c & 3]));
       }
     }
   }
   __device__ void row_end(Row& st, int t, int mt, int nt, int r) const {
     const int ws = mt * 128 + r;
-    if (ws < WS) xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2(st.re, st.im);
+    if (ws < WS)
+      xpart[((size_t)t * nt_n + nt) * WS + ws] =
+          make_double2((double)((st.re[0] + st.re[1]) + (st.re[2] + st.re[3])),
+                       (double)((st.im[0] + st.im[1]) + (st.im[2] + st.im[3])));
   }
 };
 
@@ -450,7 +466,7 @@ struct GramP {
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int j = nt * BN + c0 + c;
-      if (j < N) gram[((size_t)ws * N + i) * N + j] = make_double2((double)re[c] * st, (double)im[c] * st);
+      if (j < N) gram[((size_t)ws * N + i) * N + j] = make_double2((double)(re[c] * st), (double)(im[c] * st));
     }
   }
   __device__ void row_end(Row&, int, int, int, int) const {}
@@ -481,7 +497,7 @@ struct ApplyRP {
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int j = nt * BN + c0 + c;
-      if (j < N) phi[((size_t)ws * NM + row) * N + j] = make_double2((double)re[c] * st, (double)im[c] * st);
+      if (j < N) phi[((size_t)ws * NM + row) * N + j] = make_double2((double)(re[c] * st), (double)(im[c] * st));
     }
   }
   __device__ void row_end(Row&, int, int, int, int) const {}
@@ -617,19 +633,21 @@ __global__ void split_y_kernel(const zc* y, const float* s_l, __half* out, float
 }
 
 // acc[w][s*N + j][(k,p)] = phi[w][s][(k,p)][j] + sum_q D[k][p][q] phi[w][s][(k,q)][j]
-// grid (k, ws, j-chunk of 64); the correction runs in fp32, the identity part in FP64.
+// grid (k, ws, j-chunk of 64); the correction runs in fp32 on an fp32 copy staged in
+// shared memory, the identity part is the FP64 input itself.
 __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* acc, int nk, int M, int N, int NM) {
   const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  zc* blk = reinterpret_cast<zc*>(smraw);               // [M][64]   (16-byte entries first)
-  float2* D = reinterpret_cast<float2*>(blk + M * 64);  // [M][M]
+  float2* blk = reinterpret_cast<float2*>(smraw);          // [M][64]
+  float2* D = blk + M * 64;                                  // [M][M]
   for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
   const zc* src = phi + (size_t)ws * NM * N;
   for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
     const int q = e / jn, j = e % jn;
-    blk[q * 64 + j] = src[(size_t)(k * M + q) * N + j0 + j];
+    const zc v = src[(size_t)(k * M + q) * N + j0 + j];
+    blk[q * 64 + j] = make_float2((float)v.x, (float)v.y);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
@@ -637,12 +655,11 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* a
     float cr = 0.f, ci = 0.f;
     for (int q = 0; q < M; ++q) {
       const float2 d = D[p * M + q];
-      const zc b = blk[q * 64 + j];
-      const float br = (float)b.x, bi = (float)b.y;
-      cr = fmaf(d.x, br, fmaf(-d.y, bi, cr));
-      ci = fmaf(d.x, bi, fmaf(d.y, br, ci));
+      const float2 b = blk[q * 64 + j];
+      cr = fmaf(d.x, b.x, fmaf(-d.y, b.y, cr));
+      ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
     }
-    const zc id = blk[p * 64 + j];
+    const zc id = src[(size_t)(k * M + p) * N + j0 + j];
     acc[((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p] = make_double2(id.x + cr, id.y + ci);
   }
 }
@@ -653,12 +670,14 @@ __global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* 
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  double2* blk = reinterpret_cast<double2*>(smraw);       // [64][M]   (16-byte entries first)
-  float2* D = reinterpret_cast<float2*>(blk + 64 * M);    // [M][M]
+  float2* blk = reinterpret_cast<float2*>(smraw);          // [64][M]
+  float2* D = blk + 64 * M;                                  // [M][M]
   for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
+  const double2* src = acc + ((size_t)w * 2 * N + sp * N + j0) * NM + k * M;
   for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
     const int j = e / M, q = e % M;
-    blk[j * M + q] = acc[((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + q];
+    const double2 v = src[(size_t)j * NM + q];
+    blk[j * M + q] = make_float2((float)v.x, (float)v.y);
   }
   __syncthreads();
   zc* dst = phi + (size_t)ws * NM * N;
@@ -667,12 +686,11 @@ __global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* 
     float cr = 0.f, ci = 0.f;
     for (int q = 0; q < M; ++q) {
       const float2 d = D[p * M + q];
-      const double2 b = blk[j * M + q];
-      const float br = (float)b.x, bi = (float)b.y;
-      cr = fmaf(d.x, br, fmaf(-d.y, bi, cr));
-      ci = fmaf(d.x, bi, fmaf(d.y, br, ci));
+      const float2 b = blk[j * M + q];
+      cr = fmaf(d.x, b.x, fmaf(-d.y, b.y, cr));
+      ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
     }
-    const double2 id = blk[j * M + p];
+    const double2 id = src[(size_t)j * NM + p];
     dst[(size_t)(k * M + p) * N + j0 + j] = make_double2(id.x + cr, id.y + ci);
   }
 }
@@ -813,6 +831,15 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(zc* gram, zc* X, __half* 
   }
 }
 
+__global__ void to_f32_kernel(const zc* in, float2* out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = make_float2((float)in[e].x, (float)in[e].y);
+}
+__global__ void recip_kernel(const float* in, float* out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = 1.f / in[e];
+}
+
 // dhalf = Ehalf - I in fp32
 __global__ void dhalf_kernel(const zc* Ehalf, float2* d, int nk, int M) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nk * M * M;
@@ -893,13 +920,13 @@ __global__ void static_split_kernel(const zc* L, const zc* LH, const float* s_l,
   const zc* hp = LH + (size_t)b * G * n * M;
   for (int e = threadIdx.x; e < G * n * M; e += blockDim.x) {
     const int g = e / (n * M), a = (e / M) % n, r = e % M;
-    put4(lh_sp, lh_ps, (((size_t)b * G + g) * n + a) * Mp + r, hp[e].x, hp[e].y, s_lh[Q * G + g]);
+    put4d(lh_sp, lh_ps, (((size_t)b * G + g) * n + a) * Mp + r, hp[e].x, hp[e].y, s_lh[Q * G + g]);
   }
   const zc* lp = L + (size_t)b * G * M * M;
   for (int e = threadIdx.x; e < G * M * M; e += blockDim.x) {
     const int pr = e / G, g = e % G;  // g fastest in the output
     const zc v = lp[(size_t)g * M * M + pr];
-    put4(lt_sp, lt_ps, ((size_t)b * M * M + pr) * Gp + g, v.x, v.y, s_l[Q * G + g]);
+    put4d(lt_sp, lt_ps, ((size_t)b * M * M + pr) * Gp + g, v.x, v.y, s_l[Q * G + g]);
   }
 }
 
@@ -933,7 +960,7 @@ __global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, 
       const int r = (int)(e % M), b = (int)((e / M) % n), s = (int)((e / ((size_t)M * n)) % M),
                 a = (int)(e / ((size_t)M * n * M));
       const size_t idx = ((size_t)t * nM + a * M + s) * (n * Mp) + b * Mp + r;
-      put4(z_sp, ps, idx, buf[e].x, buf[e].y, sc);
+      put4d(z_sp, ps, idx, buf[e].x, buf[e].y, sc);
     }
     __syncthreads();
   }
@@ -959,7 +986,7 @@ static cudaError_t set_smem_attr(const void* fn, size_t bytes) {
 }
 
 static size_t onebody_smem(const afqmc_kp* h) {
-  return sizeof(float2) * h->M * h->M + sizeof(zc) * h->M * 64;
+  return sizeof(float2) * h->M * h->M + sizeof(float2) * h->M * 64;
 }
 
 static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
@@ -1015,6 +1042,8 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->tri, T, false, st));
   MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
   MTRY(dalloc(h, &m->bproj, (size_t)nk * M * n, true, st));
+  MTRY(dalloc(h, &m->bproj32, (size_t)nk * M * n, true, st));
+  MTRY(dalloc(h, &m->inv_s_lh, (size_t)nk * G, true, st));
   const int zctas = std::min(T, ZCTAS);
   MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
   MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
@@ -1022,8 +1051,12 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
   trial_projector_kernel<<<nk, 256, 0, st>>>(h->A, m->bproj, m->zscratch, M, n);
   AFQMC_LAUNCHED(h);
+  to_f32_kernel<<<64, 256, 0, st>>>(m->bproj, m->bproj32, (size_t)nk * M * n);
+  AFQMC_LAUNCHED(h);
   // static split operands and the precontracted exchange tensor
   static_scales_kernel<<<dim3(nk, G), 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, nk, G, M, n);
+  AFQMC_LAUNCHED(h);
+  recip_kernel<<<64, 256, 0, st>>>(m->s_lh, m->inv_s_lh, (size_t)nk * G);
   AFQMC_LAUNCHED(h);
   static_split_kernel<<<nk * nk, 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, m->lh_sp, m->lt_sp, nk, G, Gp, M, Mp,
                                                n);
@@ -1125,7 +1158,7 @@ static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStre
   p.tiles = WS * p.mt_n * p.nt_n;
   p.kchunks = m->Np / 32;
   p.N = h->N; p.NM = h->NM; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nk = h->nk; p.WS = WS;
-  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.bproj = m->bproj; p.g32 = m->g32;
+  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.bproj32 = m->bproj32; p.g32 = m->g32;
   MTRY(run_gemm(m->m_sinvt, m->m_phi, p, err, st));
   AFQMC_LAUNCHED(h);
   green_max_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->g32, mx_g, h->nk, h->W, m->nMp);
@@ -1144,7 +1177,7 @@ static cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st) {
   p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
   p.kchunks = m->nMp / 32;
   p.W = h->W; p.G = h->G; p.nk = h->nk;
-  p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.s_lh = m->s_lh; p.Xk = m->xk;
+  p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.inv_s_lh = m->inv_s_lh; p.Xk = m->xk;
   MTRY(run_gemm(m->m_gsum, m->m_lh, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   const size_t per = (size_t)h->W * h->nk * h->G;

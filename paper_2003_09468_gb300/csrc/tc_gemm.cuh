@@ -226,12 +226,17 @@ template <int STAGES, class P>
 __global__ void __launch_bounds__(THREADS, 1)
     cgemm_precise_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const P p, int* err) {
+  // Persistent: CTA i handles the contiguous tile range [i*per, min((i+1)*per, tiles)), so
+  // consecutive tiles of one CTA share operands in L2.  The TMA ring and the two TMEM
+  // accumulator sets run continuously across tile boundaries.  One drain per 32-wide k
+  // chunk: per accumulator the four small cross products of the chunk go first, then
+  // the two hi*hi products, so a drained partial carries two full-magnitude truncations.
   using Lay = LayoutP<STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Lay::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;   // [2] MMA -> epilogue: set holds a finished k step
+  uint64_t* accf = empty + STAGES;   // [2] MMA -> epilogue: set holds a finished chunk
   uint64_t* acce = accf + 2;         // [2] epilogue -> MMA: set drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -258,34 +263,40 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  int b, mt, nt;
-  p.tile(blockIdx.x, b, mt, nt);
+  const int per = (p.tiles + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * per;
+  const int t1 = min(p.tiles, t0 + per);
   const int KC = p.kchunks;
-  const int NSTEP = 2 * KC;
 
   if (warp == 0) {
     if (lane == 0) {
       tc::tma_prefetch(&tmA);
       tc::tma_prefetch(&tmB);
-      int issued = 0;
-      for (int kc = 0; kc < KC; ++kc) {
-        const int s = kc % STAGES;
-        const uint32_t ph = (kc / STAGES) & 1;
-        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort)) {
-          atomicCAS(err, 0, tc::ERR_TIMEOUT_EMPTY);
-          *abort = 1;
-          break;
+      long g = 0;
+      bool failed = false;
+      for (int t = t0; t < t1 && !failed; ++t) {
+        int b, mt, nt;
+        p.tile(t, b, mt, nt);
+        for (int kc = 0; kc < KC; ++kc, ++g) {
+          const int s = (int)(g % STAGES);
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, abort)) {
+            atomicCAS(err, 0, tc::ERR_TIMEOUT_EMPTY);
+            *abort = 1;
+            failed = true;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
+          const Coords c = p.coords(b, mt, nt, kc);
+          uint8_t* sa = smem + s * Lay::STAGE_BYTES;
+          tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
+          tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
         }
-        tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
-        const Coords c = p.coords(b, mt, nt, kc);
-        uint8_t* sa = smem + s * Lay::STAGE_BYTES;
-        tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
-        tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
-        ++issued;
       }
-      for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc) {
-        const int s = kc % STAGES;
-        const uint32_t ph = (kc / STAGES) & 1;
+      // every issued copy must land before the CTA may exit
+      for (long q = (g > STAGES ? g - STAGES : 0); q < g; ++q) {
+        const int s = (int)(q % STAGES);
+        const uint32_t ph = (uint32_t)((q / STAGES) & 1);
         int zero = 0;
         if (!tc::mbar_wait(&full[s], ph, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
       }
@@ -293,20 +304,20 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t id = tc::idesc_f16(BM, BNP, false);
-      int step = 0;
+      long g = 0;
       bool failed = false;
-      for (int kc = 0; kc < KC && !failed; ++kc) {
-        const int s = kc % STAGES;
-        const uint32_t ph = (kc / STAGES) & 1;
-        if (!tc::mbar_wait(&full[s], ph, abort)) {
-          atomicCAS(err, 0, tc::ERR_TIMEOUT_FULL);
-          *abort = 1;
-          break;
-        }
-        const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
-        const uint32_t sb = sa + Lay::A_BYTES;
-        for (int kk = 0; kk < 2; ++kk, ++step) {
-          const int set = step & 1, use = step >> 1;
+      for (int t = t0; t < t1 && !failed; ++t) {
+        for (int kc = 0; kc < KC; ++kc, ++g) {
+          const int s = (int)(g % STAGES);
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if (!tc::mbar_wait(&full[s], ph, abort)) {
+            atomicCAS(err, 0, tc::ERR_TIMEOUT_FULL);
+            *abort = 1;
+            failed = true;
+            break;
+          }
+          const int set = (int)(g & 1);
+          const uint32_t use = (uint32_t)(g >> 1);
           if (!tc::mbar_wait(&acce[set], (use & 1) ^ 1, abort)) {
             atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
             *abort = 1;
@@ -314,88 +325,92 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
+          const uint32_t sb = sa + Lay::A_BYTES;
           const uint32_t d = tmem + set * 4 * BNP;
-          const uint32_t ko = kk * 32;
-          const uint64_t arh = tc::desc_kmajor_sw64(sa + 0 * BM * 64 + ko);
-          const uint64_t arl = tc::desc_kmajor_sw64(sa + 1 * BM * 64 + ko);
-          const uint64_t aih = tc::desc_kmajor_sw64(sa + 2 * BM * 64 + ko);
-          const uint64_t ail = tc::desc_kmajor_sw64(sa + 3 * BM * 64 + ko);
-          const uint64_t brh = tc::desc_kmajor_sw64(sb + 0 * BNP * 64 + ko);
-          const uint64_t brl = tc::desc_kmajor_sw64(sb + 1 * BNP * 64 + ko);
-          const uint64_t bih = tc::desc_kmajor_sw64(sb + 2 * BNP * 64 + ko);
-          const uint64_t bil = tc::desc_kmajor_sw64(sb + 3 * BNP * 64 + ko);
-          // P_rr, P_ii, P_ri, P_ir at column offsets 0, 64, 128, 192 of the set.  The two
-          // small cross products go first, so the only truncation at the full magnitude
-          // is the final hi*hi accumulate.
-          tc::mma_f16(d + 0 * BNP, arl, brh, id, 0);
-          tc::mma_f16(d + 0 * BNP, arh, brl, id, 1);
-          tc::mma_f16(d + 0 * BNP, arh, brh, id, 1);
-          tc::mma_f16(d + 1 * BNP, ail, bih, id, 0);
-          tc::mma_f16(d + 1 * BNP, aih, bil, id, 1);
-          tc::mma_f16(d + 1 * BNP, aih, bih, id, 1);
-          tc::mma_f16(d + 2 * BNP, arl, bih, id, 0);
-          tc::mma_f16(d + 2 * BNP, arh, bil, id, 1);
-          tc::mma_f16(d + 2 * BNP, arh, bih, id, 1);
-          tc::mma_f16(d + 3 * BNP, ail, brh, id, 0);
-          tc::mma_f16(d + 3 * BNP, aih, brl, id, 1);
-          tc::mma_f16(d + 3 * BNP, aih, brh, id, 1);
+          uint64_t A[4][2], B[4][2];  // [plane][k16 half]
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              A[pl][kk] = tc::desc_kmajor_sw64(sa + pl * BM * 64 + kk * 32);
+              B[pl][kk] = tc::desc_kmajor_sw64(sb + pl * BNP * 64 + kk * 32);
+            }
+          // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo.  Accumulators (column offsets):
+          // P_rr = Ar Br (0), P_ii = Ai Bi (64), P_ri = Ar Bi (128), P_ir = Ai Br (192).
+          const int ap[4] = {0, 2, 0, 2}, bp[4] = {0, 2, 2, 0};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t dq = d + q * BNP;
+            const int ah = ap[q], bh = bp[q];
+            tc::mma_f16(dq, A[ah + 1][0], B[bh][0], id, 0);
+            tc::mma_f16(dq, A[ah][0], B[bh + 1][0], id, 1);
+            tc::mma_f16(dq, A[ah + 1][1], B[bh][1], id, 1);
+            tc::mma_f16(dq, A[ah][1], B[bh + 1][1], id, 1);
+            tc::mma_f16(dq, A[ah][0], B[bh][0], id, 1);
+            tc::mma_f16(dq, A[ah][1], B[bh][1], id, 1);
+          }
           tc::mma_commit(&accf[set]);
+          tc::mma_commit(&empty[s]);
         }
-        tc::mma_commit(&empty[s]);
       }
-      // wait for our own MMAs even when aborting: commit to a fresh arrival on accf of the
-      // last set used and wait on it with the abort flag ignored
-      if (step > 0) {
-        const int last = step - 1;
+      if (g > 0) {  // our own MMAs must complete before TMEM is freed
+        const long last = g - 1;
         int zero = 0;
-        if (!tc::mbar_wait(&accf[last & 1], (last >> 1) & 1, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
+        if (!tc::mbar_wait(&accf[last & 1], (uint32_t)((last >> 1) & 1), &zero))
+          atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
       }
     }
   } else {
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-    float sre[BNP], sim[BNP];
-#pragma unroll
-    for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
+    long g = 0;
     bool ok = true;
-    for (int step = 0; step < NSTEP; ++step) {
-      const int set = step & 1, use = step >> 1;
-      if (!tc::mbar_wait(&accf[set], use & 1, abort)) {
-        if (lane == 0) atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
-        ok = false;
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t d = tmem + lane_off + set * 4 * BNP;
+    for (int t = t0; t < t1 && ok; ++t) {
+      int b, mt, nt;
+      p.tile(t, b, mt, nt);
+      float sre[BNP], sim[BNP];
 #pragma unroll
-      for (int g = 0; g < BNP / 16; ++g) {
-        float rr[16], ii[16], ri[16], ir[16];
-        tc::tmem_ld16(d + 0 * BNP + g * 16, rr);
-        tc::tmem_ld16(d + 1 * BNP + g * 16, ii);
-        tc::tmem_ld16(d + 2 * BNP + g * 16, ri);
-        tc::tmem_ld16(d + 3 * BNP + g * 16, ir);
-        tc::tmem_ld_wait();
+      for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
+      for (int kc = 0; kc < KC; ++kc, ++g) {
+        const int set = (int)(g & 1);
+        const uint32_t use = (uint32_t)(g >> 1);
+        if (!tc::mbar_wait(&accf[set], use & 1, abort)) {
+          if (lane == 0) atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t d = tmem + lane_off + set * 4 * BNP;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          if (P::kConjA) {  // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-            sre[g * 16 + c] += rr[c] + ii[c];
-            sim[g * 16 + c] += ri[c] - ir[c];
-          } else {
-            sre[g * 16 + c] += rr[c] - ii[c];
-            sim[g * 16 + c] += ri[c] + ir[c];
+        for (int gq = 0; gq < BNP / 16; ++gq) {
+          float rr[16], ii[16], ri[16], ir[16];
+          tc::tmem_ld16(d + 0 * BNP + gq * 16, rr);
+          tc::tmem_ld16(d + 1 * BNP + gq * 16, ii);
+          tc::tmem_ld16(d + 2 * BNP + gq * 16, ri);
+          tc::tmem_ld16(d + 3 * BNP + gq * 16, ir);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            if (P::kConjA) {  // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+              sre[gq * 16 + c] += rr[c] + ii[c];
+              sim[gq * 16 + c] += ri[c] - ir[c];
+            } else {
+              sre[gq * 16 + c] += rr[c] - ii[c];
+              sim[gq * 16 + c] += ri[c] + ir[c];
+            }
           }
         }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce[set]);
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acce[set]);
-    }
-    if (ok) {
+      if (!ok) break;
       typename P::Row st;
       p.row_begin(st, b, mt, nt, r);
 #pragma unroll
-      for (int g = 0; g < BNP / 16; ++g) p.chunk(st, b, mt, nt, r, g * 16, sre + g * 16, sim + g * 16);
+      for (int gq = 0; gq < BNP / 16; ++gq) p.chunk(st, b, mt, nt, r, gq * 16, sre + gq * 16, sim + gq * 16);
       p.row_end(st, b, mt, nt, r);
     }
   }
@@ -444,7 +459,14 @@ cudaError_t launch_precise(const CUtensorMap& a, const CUtensorMap& b, const P& 
     configured = true;
   }
   if (p.tiles <= 0) return cudaSuccess;
-  fn<<<p.tiles, THREADS, Lay::SMEM, st>>>(a, b, p, err);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  const int grid = p.tiles < sms ? p.tiles : sms;
+  fn<<<grid, THREADS, Lay::SMEM, st>>>(a, b, p, err);
   return cudaGetLastError();
 }
 
