@@ -64,7 +64,7 @@ namespace mixed {
 
 // Output tile width of the precise GEMM (tc_gemm.cuh): 64 columns.
 constexpr int BN = tcg::BNP;
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr float SCALE_TARGET = 4096.f;
 constexpr float V_SCALE = 1024.f;   // fixed scale of vHS entries (|V| < 64 fits fp16 hi)
 constexpr int ZCTAS = 304;
@@ -186,7 +186,6 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
 // ---------------------------------------------------------------------------
 // GEMM policies
 // ---------------------------------------------------------------------------
-struct NoRow {};
 
 // Gh[ws] = B^T + S^-T phi_perp^T : rows i = (k1, a), cols (k2, p); written to g32 in tile
 // layout.  B = A (A^dag A)^-1 and phi_perp = phi - B S (see green()).
@@ -198,7 +197,6 @@ struct GreenP {
   const float* s_phi;
   const float2* bproj32;
   float2* g32;
-  typedef float Row;  // inverse scale of the row's walker-spin
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -208,27 +206,23 @@ struct GreenP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, b, 0}};
     return c;
   }
-  __device__ void row_begin(Row& st, int b, int, int, int) const { st = 1.f / (s_sinv[b] * s_phi[b]); }
-  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
-    const int i = mt * 128 + r;
-    if (i >= N) return;
-    const int k1 = i / n, a = i % n;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int col = nt * BN + c0 + c;
-      if (col < NM) {
-        const int k2 = col / M, p = col % M;
-        float gr = re[c] * st, gi = im[c] * st;
-        if (k1 == k2) {
-          const float2 bp = bproj32[((size_t)k1 * M + p) * n + a];
-          gr += bp.x;
-          gi += bp.y;
-        }
-        g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2(gr, gi);
+  __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
+    const float st = 1.f / (s_sinv[b] * s_phi[b]);
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int i = mt * 128 + r, col = nt * BN + c;
+      if (i >= N || col >= NM) continue;
+      const int k1 = i / n, a = i % n, k2 = col / M, p = col % M;
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      float gr = v.x * st, gi = v.y * st;
+      if (k1 == k2) {
+        const float2 bp = bproj32[((size_t)k1 * M + p) * n + a];
+        gr += bp.x;
+        gi += bp.y;
       }
+      g32[((((size_t)k1 * nk + k2) * WS + b) * n + a) * Mp + p] = make_float2(gr, gi);
     }
   }
-  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
 // Partial Cholesky trace of one k block: Xk[k][w][Q][g] = sum_{a,r} LH[Q,k,g,a,r] Gsum_w[(k,a),(k-Q,r)].
@@ -242,7 +236,6 @@ struct ForceBiasP {
   const float* s_gsum;
   const float* inv_s_lh;
   double2* Xk;  // [Nk(k)][W][Nk(Q)][G]
-  typedef float Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -253,24 +246,17 @@ struct ForceBiasP {
     tcg::Coords c = {{c0, mt * 128, 0, kminus[k * nk + Q], k}, {c0, nt * BN, 0, k, Q}};
     return c;
   }
-  __device__ void row_begin(Row& st, int, int mt, int, int r) const {
-    const int w = mt * 128 + r;
-    st = w < W ? 1.f / s_gsum[w] : 0.f;
-  }
-  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
-    const int w = mt * 128 + r;
-    if (w >= W) return;
+  __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
     const int Q = b / nk, k = b % nk;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int g = nt * BN + c0 + c;
-      if (g < G) {
-        const float f = st * inv_s_lh[Q * G + g];
-        Xk[(((size_t)k * W + w) * nk + Q) * G + g] = make_double2((double)(re[c] * f), (double)(im[c] * f));
-      }
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int w = mt * 128 + r, g = nt * BN + c;
+      if (w >= W || g >= G) continue;
+      const float f = inv_s_lh[Q * G + g] / s_gsum[w];
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      Xk[(((size_t)k * W + w) * nk + Q) * G + g] = make_double2((double)(v.x * f), (double)(v.y * f));
     }
   }
-  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
 // X[w][Q][g] = sum_k Xk[k][w][Q][g]  (FP64, fixed order)
@@ -295,7 +281,6 @@ struct VhsP {
   const float* s_y;  // [Q][W]
   __half* v_sp;
   int* overflow;
-  typedef float Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -306,31 +291,23 @@ struct VhsP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, Q, 0}, {kc * 32, nt * BN, 0, k, Q}};
     return c;
   }
-  __device__ void row_begin(Row& st, int b, int mt, int, int r) const {
-    const int Q = b / nk, w = mt * 128 + r;
-    st = w < W ? V_SCALE / s_y[Q * W + w] : 0.f;
-  }
-  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
-    const int w = mt * 128 + r;
-    if (w >= W) return;
+  __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
     const int Q = b / nk, k = b % nk, kq = kminus[k * nk + Q];
     const size_t ps = (size_t)NM * NMp;
-    __half* base = v_sp + (size_t)w * 4 * ps;
     bool bad = false;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int pr = nt * BN + c0 + c;
-      if (pr < M * M) {
-        const int p = pr / M, rr = pr % M;
-        const size_t idx = (size_t)(k * M + p) * NMp + kq * M + rr;
-        const float vr = re[c] * st, vi = im[c] * st;
-        bad |= !(fabsf(vr) < 60000.f && fabsf(vi) < 60000.f);
-        put4f(base, ps, idx, vr, vi);
-      }
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int w = mt * 128 + r, pr = nt * BN + c;
+      if (w >= W || pr >= M * M) continue;
+      const float st = V_SCALE / s_y[Q * W + w];
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      const float vr = v.x * st, vi = v.y * st;
+      bad |= !(fabsf(vr) < 60000.f && fabsf(vi) < 60000.f);
+      const int pp = pr / M, rr = pr % M;
+      put4f(v_sp + (size_t)w * 4 * ps, ps, (size_t)(k * M + pp) * NMp + kq * M + rr, vr, vi);
     }
     if (bad) atomicExch(overflow, 1);
   }
-  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
 // One Taylor term: T_j[w] = V[w] T_{j-1}[w] / j in transposed form (rows j' = (spin, column)).
@@ -342,7 +319,6 @@ struct TaylorP {
   const float* s_t;
   double2* acc;       // [W][R][NM]
   __half* t_next;     // [W][4][R][NMp]
-  typedef float Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -352,37 +328,29 @@ struct TaylorP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, b, 0}};
     return c;
   }
-  __device__ void row_begin(Row& st, int b, int, int, int) const { st = inv_j / V_SCALE; }
-  __device__ void chunk(Row& st, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const {
-    const int j = mt * 128 + r;
-    if (j >= R) return;
-    const float inv_s = 1.f / s_t[b];   // power of two: exact
+  __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
+    // D carries the operand scales s_t (A) and V_SCALE (B): T_j * s_t = D * inv_j / V_SCALE
+    const float st = inv_j / V_SCALE, inv_s = 1.f / s_t[b];
     const size_t ps = (size_t)R * NMp;
     __half* tb = t_next + (size_t)b * 4 * ps;
-    double2* ab = acc + ((size_t)b * R + j) * NM;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int i = nt * BN + c0 + c;
-      if (i < NM) {
-        // D carries the operand scales s_t (A) and V_SCALE (B); st removes V_SCALE and applies 1/j
-        const float tr = re[c] * st, ti = im[c] * st;   // = T_j * s_t
-        double2 a = ab[i];
-        a.x += (double)(tr * inv_s);
-        a.y += (double)(ti * inv_s);
-        ab[i] = a;
-        put4f(tb, ps, (size_t)j * NMp + i, tr, ti);
-      }
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int j = mt * 128 + r, i = nt * BN + c;
+      if (j >= R || i >= NM) continue;
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      const float tr = v.x * st, ti = v.y * st;
+      double2* a = acc + ((size_t)b * R + j) * NM + i;
+      double2 av = *a;
+      av.x += (double)(tr * inv_s);
+      av.y += (double)(ti * inv_s);
+      *a = av;
+      put4f(tb, ps, (size_t)j * NMp + i, tr, ti);
     }
   }
-  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
-// Exchange: rows = walker-spins, cols = (a, s) of Z_t; epilogue dots with Gh[(k,a),(kx+Q,s)].
-struct ExchangeRow {
-  float re[4], im[4];   // four interleaved fp32 partial sums of the 64-column dot product
-  float inv;
-  const float2* g2;
-};
+// Exchange: rows = walker-spins, cols = (a, s) of Z_t; epilogue dots with Gh[(k,a),(kx+Q,s)]
+// (one warp per row, lanes along the columns, warp-shuffle reduction).
 struct ExchangeP {
   static constexpr bool kConjA = false;
   int tiles, kchunks;
@@ -394,7 +362,6 @@ struct ExchangeP {
   const float* s_z;
   const float2* g32;
   double2* xpart;  // [T][nt_n][WS]
-  typedef ExchangeRow Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -405,36 +372,60 @@ struct ExchangeP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, t, 0}};
     return c;
   }
-  __device__ void row_begin(Row& st, int t, int mt, int, int r) const {
-    const int ws = mt * 128 + r;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) st.re[u] = st.im[u] = 0.f;
-    if (ws >= WS) { st.inv = 0.f; st.g2 = nullptr; return; }
+  __device__ void store_tile(int t, int mt, int nt, const float2* tile, int, int ew, int lane) const {
     const int4 q = tri[t];
     const int kxq = kminus[q.z * nk + minus[q.x]];  // kx + Q
-    st.inv = 1.f / (s_g[ws] * s_z[t]);
-    st.g2 = g32 + (((size_t)q.y * nk + kxq) * WS + ws) * n * Mp;
-  }
-  __device__ void chunk(Row& st, int, int, int nt, int, int c0, const float* re, const float* im) const {
-    if (!st.g2) return;
+    const size_t rs = (size_t)n * Mp;                // row (walker-spin) stride of a Gh block
+    const float2* blk = g32 + ((size_t)q.y * nk + kxq) * WS * rs;
+    const float sz = s_z[t];
+    int off[BN / 32];
+    bool on[BN / 32];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int col = nt * BN + c0 + c;
-      if (col < nM) {
-        const int a = col / M, s = col % M;
-        const float2 g = st.g2[a * Mp + s];
-        const float yr = re[c] * st.inv, yi = im[c] * st.inv;
-        st.re[c & 3] = fmaf(yr, g.x, fmaf(-yi, g.y, st.re[c & 3]));
-        st.im[c & 3] = fmaf(yr, g.y, fmaf(yi, g.x, st.im[c & 3]));
+    for (int h = 0; h < BN / 32; ++h) {
+      const int col = nt * BN + lane + 32 * h;
+      on[h] = col < nM;
+      off[h] = on[h] ? (col / M) * Mp + col % M : 0;
+    }
+    // lane partial sums of the 32 rows of this warp; every load is independent of the
+    // others, so all of them are in flight together
+    const int r0 = ew * 32;
+    float pr[32], pi[32];
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) {
+      const int ws = mt * 128 + r0 + rr;
+      float sr = 0.f, si = 0.f;
+      if (ws < WS) {
+#pragma unroll
+        for (int h = 0; h < BN / 32; ++h) {
+          if (on[h]) {
+            const float2 y = tile[(r0 + rr) * tcg::STAGE_LD + lane + 32 * h];
+            const float2 g = blk[ws * rs + off[h]];
+            sr = fmaf(y.x, g.x, fmaf(-y.y, g.y, sr));
+            si = fmaf(y.x, g.y, fmaf(y.y, g.x, si));
+          }
+        }
+        const float inv = 1.f / (s_g[ws] * sz);   // powers of two: exact after the sum
+        sr *= inv;
+        si *= inv;
+      }
+      pr[rr] = sr;
+      pi[rr] = si;
+    }
+    // transpose-reduce: at each halving step a lane keeps the half of its rows selected by
+    // its lane bit and adds its partner's copy of that half; slot 0 ends as row r0 + lane
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < o; ++j) {
+        const float send_r = up ? pr[j] : pr[j + o], keep_r = up ? pr[j + o] : pr[j];
+        const float send_i = up ? pi[j] : pi[j + o], keep_i = up ? pi[j + o] : pi[j];
+        pr[j] = keep_r + __shfl_xor_sync(0xffffffffu, send_r, o);
+        pi[j] = keep_i + __shfl_xor_sync(0xffffffffu, send_i, o);
       }
     }
-  }
-  __device__ void row_end(Row& st, int t, int mt, int nt, int r) const {
-    const int ws = mt * 128 + r;
-    if (ws < WS)
-      xpart[((size_t)t * nt_n + nt) * WS + ws] =
-          make_double2((double)((st.re[0] + st.re[1]) + (st.re[2] + st.re[3])),
-                       (double)((st.im[0] + st.im[1]) + (st.im[2] + st.im[3])));
+    const int ws = mt * 128 + r0 + lane;
+    if (ws < WS) xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)pr[0], (double)pi[0]);
   }
 };
 
@@ -445,7 +436,6 @@ struct GramP {
   int mt_n, nt_n, N;
   const float* s_t;   // per walker
   double2* gram;      // [WS][N][N]
-  typedef float Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -456,20 +446,17 @@ struct GramP {
     tcg::Coords c = {{kc * 32, sp * N + mt * 128, 0, w, 0}, {kc * 32, sp * N + nt * BN, 0, w, 0}};
     return c;
   }
-  __device__ void row_begin(Row& st, int ws, int, int, int) const {
+  __device__ void store_tile(int ws, int mt, int nt, const float2* tile, int tid, int, int) const {
     const float sc = s_t[ws >> 1];
-    st = 1.f / (sc * sc);
-  }
-  __device__ void chunk(Row& st, int ws, int mt, int nt, int r, int c0, const float* re, const float* im) const {
-    const int i = mt * 128 + r;
-    if (i >= N) return;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int j = nt * BN + c0 + c;
-      if (j < N) gram[((size_t)ws * N + i) * N + j] = make_double2((double)(re[c] * st), (double)(im[c] * st));
+    const float st = 1.f / (sc * sc);
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int i = mt * 128 + r, j = nt * BN + c;
+      if (i >= N || j >= N) continue;
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      gram[((size_t)ws * N + i) * N + j] = make_double2((double)(v.x * st), (double)(v.y * st));
     }
   }
-  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
 // phi[ws] <- phi[ws] R^-1 : rows r = (k,p), columns j; B = (R^-1)^T split planes.
@@ -480,7 +467,6 @@ struct ApplyRP {
   const float* s_phi;
   const float* s_r;
   zc* phi;
-  typedef float Row;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -490,17 +476,16 @@ struct ApplyRP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, ws, 0}, {kc * 32, nt * BN, 0, ws, 0}};
     return c;
   }
-  __device__ void row_begin(Row& st, int ws, int, int, int) const { st = 1.f / (s_phi[ws] * s_r[ws]); }
-  __device__ void chunk(Row& st, int ws, int mt, int nt, int r, int c0, const float* re, const float* im) const {
-    const int row = mt * 128 + r;
-    if (row >= NM) return;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int j = nt * BN + c0 + c;
-      if (j < N) phi[((size_t)ws * NM + row) * N + j] = make_double2((double)(re[c] * st), (double)(im[c] * st));
+  __device__ void store_tile(int ws, int mt, int nt, const float2* tile, int tid, int, int) const {
+    const float st = 1.f / (s_phi[ws] * s_r[ws]);
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int row = mt * 128 + r, j = nt * BN + c;
+      if (row >= NM || j >= N) continue;
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      phi[((size_t)ws * NM + row) * N + j] = make_double2((double)(v.x * st), (double)(v.y * st));
     }
   }
-  __device__ void row_end(Row&, int, int, int, int) const {}
 };
 
 // ---------------------------------------------------------------------------

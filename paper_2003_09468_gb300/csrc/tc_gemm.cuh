@@ -58,6 +58,10 @@ struct Layout {
 //   __device__ void chunk(Row&, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const;
 //   __device__ void row_end(Row&, int b, int mt, int nt, int r) const;
 //   static constexpr bool kConjA;                 precise variant: D = sum conj(A) B instead
+//   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int ewarp, int lane) const;
+//                                                precise variant: the finished 128 x 64 tile in shared
+//                                                memory, tile[r * STAGE_LD + c]; called by the 128
+//                                                epilogue threads (tid 0..127, ewarp 0..3)
 // r is the row inside the tile (0..127), c0 the first of 16 columns inside the tile.
 template <int BN, int STAGES, class P>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -212,13 +216,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 // Tile 128 x BNP (BNP = 64): 4 x 64 columns per set, 2 sets = all 512 TMEM columns.
 constexpr int BNP = 64;
 
+// Epilogue staging: the finished 128 x 64 tile as (re, im) fp32 pairs, rows padded to 65
+// entries so that row-per-thread and column-per-thread accesses both avoid bank conflicts.
+constexpr int STAGE_LD = BNP + 1;
+
 template <int STAGES>
 struct LayoutP {
   static constexpr int A_BYTES = NPLANE * BM * 64;
   static constexpr int B_BYTES = NPLANE * BNP * 64;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int TILE_BYTES = BM * STAGE_LD * 8;
   static constexpr int BAR_BYTES = 256;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + TILE_BYTES + BAR_BYTES + 1024;
   static constexpr uint32_t TMEM_COLS = 512;
 };
 
@@ -234,7 +243,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   using Lay = LayoutP<STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Lay::STAGE_BYTES);
+  float2* tile_buf = reinterpret_cast<float2*>(smem + STAGES * Lay::STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Lay::STAGE_BYTES + Lay::TILE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* accf = empty + STAGES;   // [2] MMA -> epilogue: set holds a finished chunk
   uint64_t* acce = accf + 2;         // [2] epilogue -> MMA: set drained
@@ -362,12 +372,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else {
+    // All four epilogue warps run the same sequence of named barriers for every tile, so a
+    // failed (timed-out) wait never leaves a warp behind at bar.sync: failure is sticky,
+    // skips the work, and raises the abort flag that ends every later wait at once.
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
     long g = 0;
     bool ok = true;
-    for (int t = t0; t < t1 && ok; ++t) {
+    for (int t = t0; t < t1; ++t) {
       int b, mt, nt;
       p.tile(t, b, mt, nt);
       float sre[BNP], sim[BNP];
@@ -376,11 +389,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int kc = 0; kc < KC; ++kc, ++g) {
         const int set = (int)(g & 1);
         const uint32_t use = (uint32_t)(g >> 1);
-        if (!tc::mbar_wait(&accf[set], use & 1, abort)) {
+        if (ok && !tc::mbar_wait(&accf[set], use & 1, abort)) {
           if (lane == 0) atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
+          *abort = 1;
           ok = false;
-          break;
         }
+        if (!ok) continue;
         tc::fence_after_sync();
         const uint32_t d = tmem + lane_off + set * 4 * BNP;
 #pragma unroll
@@ -406,12 +420,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce[set]);
       }
-      if (!ok) break;
-      typename P::Row st;
-      p.row_begin(st, b, mt, nt, r);
+      // stage the tile, then let the policy store it with its own (coalesced) mapping
+      asm volatile("bar.sync 1, 128;" ::: "memory");   // previous tile fully stored
 #pragma unroll
-      for (int gq = 0; gq < BNP / 16; ++gq) p.chunk(st, b, mt, nt, r, gq * 16, sre + gq * 16, sim + gq * 16);
-      p.row_end(st, b, mt, nt, r);
+      for (int c = 0; c < BNP; ++c) tile_buf[r * STAGE_LD + c] = make_float2(sre[c], sim[c]);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!*abort) p.store_tile(b, mt, nt, tile_buf, threadIdx.x - 64, warp - 2, lane);
     }
   }
   tc::fence_before_sync();
