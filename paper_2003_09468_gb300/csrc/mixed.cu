@@ -48,7 +48,7 @@ struct MixedState {
   // static operands
   __half* lh_sp = nullptr;    float* s_lh = nullptr;    // [4][Nk][Nk][G][n][Mp], s_lh[Q][G]
   __half* lt_sp = nullptr;    float* s_l = nullptr;     // [4][Nk][Nk][M*M][Gp], s_l[Q][G]
-  __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][T][nM][n*Mp]
+  __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][T][n*Mp][n*Mp]
   int4* tri = nullptr;                                   // [T] (Q, k, kx, weight)
   float2* dhalf = nullptr;                               // [Nk][M][M] exp(-dt/2 H1') - I
   zc* bproj = nullptr;                                   // [Nk][M][n] A (A^dag A)^-1 per k
@@ -191,6 +191,7 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
 // layout.  B = A (A^dag A)^-1 and phi_perp = phi - B S (see green()).
 struct GreenP {
   static constexpr bool kConjA = false;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
   const float* s_sinv;
@@ -230,6 +231,7 @@ struct GreenP {
 // blocks are summed in FP64 by xsum_kernel.
 struct ForceBiasP {
   static constexpr bool kConjA = false;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, W, G, nk;
   const int* kminus;
@@ -275,6 +277,7 @@ __global__ void xsum_kernel(const double2* Xk, zc* X, int nk, size_t per) {
 // V[w][(k,p)][(k-Q,r)] = sum_g y[w,Q,g] L[Q,k,g,p,r]  -> split planes with a fixed scale
 struct VhsP {
   static constexpr bool kConjA = false;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, W, M, nk, NM, NMp;
   const int* kminus;
@@ -313,6 +316,7 @@ struct VhsP {
 // One Taylor term: T_j[w] = V[w] T_{j-1}[w] / j in transposed form (rows j' = (spin, column)).
 struct TaylorP {
   static constexpr bool kConjA = false;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, R, NM, NMp;
   float inv_j;
@@ -349,19 +353,21 @@ struct TaylorP {
   }
 };
 
-// Exchange: rows = walker-spins, cols = (a, s) of Z_t; epilogue dots with Gh[(k,a),(kx+Q,s)]
-// (one warp per row, lanes along the columns, warp-shuffle reduction).
+// Exchange: rows = walker-spins, cols = (a, s) of Z_t in the padded order a*Mp + s, so the
+// matching 64 columns of Gh[(k,a),(kx+Q,s)] are one contiguous run per walker-spin; the
+// epilogue prefetches that tile into shared memory and dots each row in its own thread.
 struct ExchangeP {
   static constexpr bool kConjA = false;
+  static constexpr bool kRowDot = true;
   int tiles, kchunks;
-  int mt_n, nt_n, WS, nk, n, M, Mp, nM;
+  int mt_n, nt_n, WS, nk, nMp;
   const int* kminus;
   const int* minus;
   const int4* tri;
   const float* s_g;
   const float* s_z;
-  const float2* g32;
-  double2* xpart;  // [T][nt_n][WS]
+  const float2* g32;  // [Nk][Nk][WS][n*Mp]
+  double2* xpart;     // [T][nt_n][WS]
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -372,66 +378,42 @@ struct ExchangeP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, t, 0}};
     return c;
   }
-  __device__ void store_tile(int t, int mt, int nt, const float2* tile, int, int ew, int lane) const {
+  __device__ void prefetch(int t, int mt, int nt, float2* buf, int tid) const {
     const int4 q = tri[t];
     const int kxq = kminus[q.z * nk + minus[q.x]];  // kx + Q
-    const size_t rs = (size_t)n * Mp;                // row (walker-spin) stride of a Gh block
-    const float2* blk = g32 + ((size_t)q.y * nk + kxq) * WS * rs;
-    const float sz = s_z[t];
-    int off[BN / 32];
-    bool on[BN / 32];
-#pragma unroll
-    for (int h = 0; h < BN / 32; ++h) {
-      const int col = nt * BN + lane + 32 * h;
-      on[h] = col < nM;
-      off[h] = on[h] ? (col / M) * Mp + col % M : 0;
+    const float2* src = g32 + (((size_t)q.y * nk + kxq) * WS + mt * 128) * nMp + nt * BN;
+    const int rows = min(128, WS - mt * 128);
+    const int pairs = min(BN, nMp - nt * BN) / 2;   // nMp is even: whole column pairs
+    for (int e = tid; e < rows * (BN / 2); e += 128) {
+      const int r = e / (BN / 2), j = e % (BN / 2);
+      if (j < pairs) tc::cp_async16(buf + r * tcg::ROWDOT_LD + 2 * j, src + (size_t)r * nMp + 2 * j);
     }
-    // lane partial sums of the 32 rows of this warp; every load is independent of the
-    // others, so all of them are in flight together
-    const int r0 = ew * 32;
-    float pr[32], pi[32];
+  }
+  __device__ void row_dot(int t, int mt, int nt, int r, const float* re, const float* im, const float2* buf) const {
+    const int ws = mt * 128 + r;
+    if (ws >= WS) return;
+    // padding columns (s >= M) of Z_t are zero, so every column below n*Mp takes part
+    const float4* g4 = reinterpret_cast<const float4*>(buf + r * tcg::ROWDOT_LD);
+    const int pairs = min(BN, nMp - nt * BN) / 2;
+    float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
 #pragma unroll
-    for (int rr = 0; rr < 32; ++rr) {
-      const int ws = mt * 128 + r0 + rr;
-      float sr = 0.f, si = 0.f;
-      if (ws < WS) {
-#pragma unroll
-        for (int h = 0; h < BN / 32; ++h) {
-          if (on[h]) {
-            const float2 y = tile[(r0 + rr) * tcg::STAGE_LD + lane + 32 * h];
-            const float2 g = blk[ws * rs + off[h]];
-            sr = fmaf(y.x, g.x, fmaf(-y.y, g.y, sr));
-            si = fmaf(y.x, g.y, fmaf(y.y, g.x, si));
-          }
-        }
-        const float inv = 1.f / (s_g[ws] * sz);   // powers of two: exact after the sum
-        sr *= inv;
-        si *= inv;
-      }
-      pr[rr] = sr;
-      pi[rr] = si;
+    for (int j = 0; j < BN / 2; ++j) {
+      if (j >= pairs) break;
+      const float4 g = g4[j];
+      pr0 = fmaf(re[2 * j], g.x, fmaf(-im[2 * j], g.y, pr0));
+      pi0 = fmaf(re[2 * j], g.y, fmaf(im[2 * j], g.x, pi0));
+      pr1 = fmaf(re[2 * j + 1], g.z, fmaf(-im[2 * j + 1], g.w, pr1));
+      pi1 = fmaf(re[2 * j + 1], g.w, fmaf(im[2 * j + 1], g.z, pi1));
     }
-    // transpose-reduce: at each halving step a lane keeps the half of its rows selected by
-    // its lane bit and adds its partner's copy of that half; slot 0 ends as row r0 + lane
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const bool up = (lane & o) != 0;
-#pragma unroll
-      for (int j = 0; j < o; ++j) {
-        const float send_r = up ? pr[j] : pr[j + o], keep_r = up ? pr[j + o] : pr[j];
-        const float send_i = up ? pi[j] : pi[j + o], keep_i = up ? pi[j + o] : pi[j];
-        pr[j] = keep_r + __shfl_xor_sync(0xffffffffu, send_r, o);
-        pi[j] = keep_i + __shfl_xor_sync(0xffffffffu, send_i, o);
-      }
-    }
-    const int ws = mt * 128 + r0 + lane;
-    if (ws < WS) xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)pr[0], (double)pi[0]);
+    const float inv = 1.f / (s_g[ws] * s_z[t]);   // powers of two: exact after the sum
+    xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)((pr0 + pr1) * inv), (double)((pi0 + pi1) * inv));
   }
 };
 
 // Gram[ws] = phi_ws^dag phi_ws from the transposed split planes (rows = columns of phi).
 struct GramP {
   static constexpr bool kConjA = true;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, N;
   const float* s_t;   // per walker
@@ -462,6 +444,7 @@ struct GramP {
 // phi[ws] <- phi[ws] R^-1 : rows r = (k,p), columns j; B = (R^-1)^T split planes.
 struct ApplyRP {
   static constexpr bool kConjA = false;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, NM, N;
   const float* s_phi;
@@ -922,7 +905,8 @@ __global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, 
   const size_t per = (size_t)nM * nM;
   zc* buf = scratch + (size_t)blockIdx.x * per;
   __shared__ double red[32];
-  const size_t ps = (size_t)T * nM * n * Mp;
+  const int nMp = n * Mp;
+  const size_t ps = (size_t)T * nMp * nMp;
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int4 q = tri[t];
     const zc* L1 = LH + ((size_t)q.x * nk + q.y) * G * nM;            // LH[Q][k]
@@ -944,7 +928,7 @@ __global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, 
     for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = (int)(e % M), b = (int)((e / M) % n), s = (int)((e / ((size_t)M * n)) % M),
                 a = (int)(e / ((size_t)M * n * M));
-      const size_t idx = ((size_t)t * nM + a * M + s) * (n * Mp) + b * Mp + r;
+      const size_t idx = ((size_t)t * nMp + a * Mp + s) * nMp + b * Mp + r;   // rows s >= M stay zero
       put4d(z_sp, ps, idx, buf[e].x, buf[e].y, sc);
     }
     __syncthreads();
@@ -997,7 +981,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
       }
   m->T = (int)tri.size();
   const int T = m->T;
-  const int ntx = cdiv(nM, BN);
+  const int ntx = cdiv(nMp, BN);
 
   MTRY(dalloc(h, &m->phi_sp, (size_t)WS * 4 * NM * Np, true, st));
   MTRY(dalloc(h, &m->s_phi, WS, true, st));
@@ -1022,7 +1006,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->s_lh, (size_t)nk * G, true, st));
   MTRY(dalloc(h, &m->lt_sp, (size_t)4 * nk * nk * M * M * Gp, true, st));
   MTRY(dalloc(h, &m->s_l, (size_t)nk * G, true, st));
-  MTRY(dalloc(h, &m->z_sp, (size_t)4 * T * nM * nMp, true, st));
+  MTRY(dalloc(h, &m->z_sp, (size_t)4 * T * nMp * nMp, true, st));
   MTRY(dalloc(h, &m->s_z, T, true, st));
   MTRY(dalloc(h, &m->tri, T, false, st));
   MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
@@ -1071,8 +1055,8 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
             {(uint64_t)NMp, (uint64_t)NM * NMp, (uint64_t)4 * NM * NMp, (uint64_t)W * 4 * NM * NMp}, BN));
   MTRY(map5(&m->m_g, m->g_sp, {(uint64_t)nMp, (uint64_t)WS, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
-  MTRY(map5(&m->m_z, m->z_sp, {(uint64_t)nMp, (uint64_t)nM, 4, (uint64_t)T, 1},
-            {(uint64_t)nMp, (uint64_t)T * nM * nMp, (uint64_t)nM * nMp, (uint64_t)T * nM * nMp * 4}, BN));
+  MTRY(map5(&m->m_z, m->z_sp, {(uint64_t)nMp, (uint64_t)nMp, 4, (uint64_t)T, 1},
+            {(uint64_t)nMp, (uint64_t)T * nMp * nMp, (uint64_t)nMp * nMp, (uint64_t)T * nMp * nMp * 4}, BN));
   MTRY(map5(&m->m_phi_a, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, 128));
   MTRY(map5(&m->m_sinvt_b, m->sinvt_sp, {(uint64_t)Np, (uint64_t)N, 4, (uint64_t)WS, 1},
@@ -1320,10 +1304,10 @@ static cudaError_t exchange(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
   ExchangeP p;
   p.mt_n = cdiv(m->WS, 128);
-  p.nt_n = cdiv(m->nM, BN);
+  p.nt_n = cdiv(m->nMp, BN);
   p.tiles = m->T * p.mt_n * p.nt_n;
   p.kchunks = m->nMp / 32;
-  p.WS = m->WS; p.nk = h->nk; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nM = m->nM;
+  p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
   p.kminus = h->kminus; p.minus = h->minus; p.tri = m->tri; p.s_g = m->s_g; p.s_z = m->s_z; p.g32 = m->g32;
   p.xpart = m->xpart;
   MTRY(run_gemm(m->m_g, m->m_z, p, h->flags + 1, st));
@@ -1333,7 +1317,7 @@ static cudaError_t exchange(afqmc_kp* h, cudaStream_t st) {
 
 static cudaError_t ex_reduce(afqmc_kp* h, zc* eloc, cudaStream_t st) {
   MixedState* m = h->mixed;
-  ex_reduce_mixed_kernel<<<h->W, 256, 0, st>>>(m->xpart, m->tri, eloc, m->T, cdiv(m->nM, BN), m->WS);
+  ex_reduce_mixed_kernel<<<h->W, 256, 0, st>>>(m->xpart, m->tri, eloc, m->T, cdiv(m->nMp, BN), m->WS);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }

@@ -12,13 +12,13 @@
 // and imaginary parts of D use two accumulators:
 //   D_re = Ar Br - Ai Bi,   D_im = Ar Bi + Ai Br   (negation via the MMA's B-negate bit)
 //
-// One CTA computes one BM x BN tile: warp 0 issues TMA loads (one 5-D box per
-// operand per 32-wide k chunk, all four planes at once, 64-byte swizzle) into a
-// STAGES-deep ring; warp 1 allocates tensor memory and one of its threads
-// issues the tcgen05.mma chain; warps 2-5 read the accumulators back with
-// tcgen05.ld and hand each row to the policy's epilogue.  Every mbarrier wait
-// is bounded; on time-out the kernel records an error, drains its own copies
-// and MMAs, frees tensor memory and returns.
+// Persistent kernel, one CTA per SM over a contiguous range of 128 x 64 output tiles:
+// warp 0 issues TMA loads (one 5-D box per operand per 32-wide k chunk, all four planes
+// at once, 64-byte swizzle) into a STAGES-deep ring; warp 1 allocates tensor memory and
+// one of its threads issues the tcgen05.mma chain; warps 2-5 read the accumulators back
+// with tcgen05.ld and hand the finished tile to the policy's epilogue.  Every mbarrier
+// wait is bounded; on time-out the kernel records an error, drains its own copies and
+// MMAs, frees tensor memory and returns.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -37,173 +37,24 @@ struct Coords {
   int b[5];
 };
 
-template <int BN, int STAGES>
-struct Layout {
-  static constexpr int A_BYTES = NPLANE * BM * 64;
-  static constexpr int B_BYTES = NPLANE * BN * 64;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int BAR_BYTES = 256;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;  // + alignment slack
-  static constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128
-                                        : (2 * BN <= 256) ? 256 : 512;
-};
-
 // Policy P provides:
-//   int tiles;                                   number of output tiles
-//   int kchunks;                                 k chunks of BK per tile
+//   static constexpr bool kConjA;     D = sum conj(A) B instead of sum A B
+//   static constexpr bool kRowDot;    epilogue form (below)
+//   int tiles;                        number of output tiles
+//   int kchunks;                      k chunks of BK per tile
 //   __device__ void tile(int t, int& b, int& mt, int& nt) const;
 //   __device__ Coords coords(int b, int mt, int nt, int kc) const;
-//   struct Row;                                  per-thread epilogue state
-//   __device__ void row_begin(Row&, int b, int mt, int nt, int r) const;
-//   __device__ void chunk(Row&, int b, int mt, int nt, int r, int c0, const float* re, const float* im) const;
-//   __device__ void row_end(Row&, int b, int mt, int nt, int r) const;
-//   static constexpr bool kConjA;                 precise variant: D = sum conj(A) B instead
+// and, for kRowDot == false,
 //   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int ewarp, int lane) const;
-//                                                precise variant: the finished 128 x 64 tile in shared
-//                                                memory, tile[r * STAGE_LD + c]; called by the 128
-//                                                epilogue threads (tid 0..127, ewarp 0..3)
-// r is the row inside the tile (0..127), c0 the first of 16 columns inside the tile.
-template <int BN, int STAGES, class P>
-__global__ void __launch_bounds__(THREADS, 1)
-    cgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const P p,
-                 int* err) {
-  using Lay = Layout<BN, STAGES>;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Lay::STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* accb = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
-  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
-    }
-    tc::mbar_init(accb, 1);
-    *abort = 0;
-    tc::fence_mbar_init();
-  }
-  if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, Lay::TMEM_COLS);
-    tc::tmem_relinquish();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t d_re = tmem, d_im = tmem + BN;
-
-  int b, mt, nt;
-  p.tile(blockIdx.x, b, mt, nt);
-  const int KC = p.kchunks;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      tc::tma_prefetch(&tmA);
-      tc::tma_prefetch(&tmB);
-      int issued = 0;
-      for (int kc = 0; kc < KC; ++kc) {
-        const int s = kc % STAGES;
-        const uint32_t ph = (kc / STAGES) & 1;
-        if (!tc::mbar_wait(&empty[s], ph ^ 1, abort)) {
-          atomicCAS(err, 0, tc::ERR_TIMEOUT_EMPTY);
-          *abort = 1;
-          break;
-        }
-        tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
-        const Coords c = p.coords(b, mt, nt, kc);
-        uint8_t* sa = smem + s * Lay::STAGE_BYTES;
-        tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
-        tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
-        ++issued;
-      }
-      // drain: every issued copy must land before the CTA may exit
-      for (int kc = (issued > STAGES ? issued - STAGES : 0); kc < issued; ++kc) {
-        const int s = kc % STAGES;
-        const uint32_t ph = (kc / STAGES) & 1;
-        int zero = 0;
-        if (!tc::mbar_wait(&full[s], ph, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idp = tc::idesc_f16(BM, BN, false);
-      constexpr uint32_t idn = tc::idesc_f16(BM, BN, true);
-      for (int kc = 0; kc < KC; ++kc) {
-        const int s = kc % STAGES;
-        const uint32_t ph = (kc / STAGES) & 1;
-        if (!tc::mbar_wait(&full[s], ph, abort)) {
-          atomicCAS(err, 0, tc::ERR_TIMEOUT_FULL);
-          *abort = 1;
-          break;
-        }
-        tc::fence_after_sync();
-        const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
-        const uint32_t sb = sa + Lay::A_BYTES;
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const uint32_t ko = kk * 32;  // 16 fp16 = 32 bytes
-          const uint64_t arh = tc::desc_kmajor_sw64(sa + 0 * BM * 64 + ko);
-          const uint64_t arl = tc::desc_kmajor_sw64(sa + 1 * BM * 64 + ko);
-          const uint64_t aih = tc::desc_kmajor_sw64(sa + 2 * BM * 64 + ko);
-          const uint64_t ail = tc::desc_kmajor_sw64(sa + 3 * BM * 64 + ko);
-          const uint64_t brh = tc::desc_kmajor_sw64(sb + 0 * BN * 64 + ko);
-          const uint64_t brl = tc::desc_kmajor_sw64(sb + 1 * BN * 64 + ko);
-          const uint64_t bih = tc::desc_kmajor_sw64(sb + 2 * BN * 64 + ko);
-          const uint64_t bil = tc::desc_kmajor_sw64(sb + 3 * BN * 64 + ko);
-          const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-          // D_re = Ar Br - Ai Bi
-          tc::mma_f16(d_re, arh, brh, idp, first);
-          tc::mma_f16(d_re, arh, brl, idp, 1);
-          tc::mma_f16(d_re, arl, brh, idp, 1);
-          tc::mma_f16(d_re, aih, bih, idn, 1);
-          tc::mma_f16(d_re, aih, bil, idn, 1);
-          tc::mma_f16(d_re, ail, bih, idn, 1);
-          // D_im = Ar Bi + Ai Br
-          tc::mma_f16(d_im, arh, bih, idp, first);
-          tc::mma_f16(d_im, arh, bil, idp, 1);
-          tc::mma_f16(d_im, arl, bih, idp, 1);
-          tc::mma_f16(d_im, aih, brh, idp, 1);
-          tc::mma_f16(d_im, aih, brl, idp, 1);
-          tc::mma_f16(d_im, ail, brh, idp, 1);
-        }
-        tc::mma_commit(&empty[s]);
-      }
-      tc::mma_commit(accb);
-      int zero = 0;  // wait for our own MMAs even when aborting
-      if (!tc::mbar_wait(accb, 0, &zero)) atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
-    }
-  } else {
-    const int q = warp & 3;  // TMEM lane quarter accessible to this warp
-    const int r = q * 32 + lane;
-    const bool ok = tc::mbar_wait(accb, 0, abort);
-    if (!ok) {
-      if (lane == 0) atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
-    } else {
-      tc::fence_after_sync();
-      typename P::Row st;
-      p.row_begin(st, b, mt, nt, r);
-      const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float re[16], im[16];
-        tc::tmem_ld16(d_re + lane_off + c0, re);
-        tc::tmem_ld16(d_im + lane_off + c0, im);
-        tc::tmem_ld_wait();
-        p.chunk(st, b, mt, nt, r, c0, re, im);
-      }
-      p.row_end(st, b, mt, nt, r);
-    }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 1) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, Lay::TMEM_COLS);
-  }
-}
+//       the finished 128 x 64 tile in shared memory, tile[r * STAGE_LD + c] = (re, im);
+//       called by the 128 epilogue threads (tid 0..127, ewarp 0..3)
+// or, for kRowDot == true (a per-row dot product of D with a second operand tile),
+//   __device__ void prefetch(int b, int mt, int nt, float2* buf, int tid) const;
+//       issues cp.async copies of the 128 x 64 operand tile into buf[r * ROWDOT_LD + c];
+//       runs while the tile's chunks are drained
+//   __device__ void row_dot(int b, int mt, int nt, int r, const float* re, const float* im,
+//                           const float2* buf) const;
+//       row r of D in registers (re[c], im[c], c < 64) and the operand tile in buf.
 
 // ---------------------------------------------------------------- precise variant
 // The tensor-core accumulator adds each MMA's partial sum with truncation, so a
@@ -219,13 +70,17 @@ constexpr int BNP = 64;
 // Epilogue staging: the finished 128 x 64 tile as (re, im) fp32 pairs, rows padded to 65
 // entries so that row-per-thread and column-per-thread accesses both avoid bank conflicts.
 constexpr int STAGE_LD = BNP + 1;
+// Row-dot policies receive a 128 x 64 operand tile in the same buffer, rows padded to 66
+// entries: 16-byte aligned rows for cp.async, and 16-byte reads of one column pair by a
+// quarter warp (consecutive rows) fall in eight different bank groups.
+constexpr int ROWDOT_LD = BNP + 2;
 
 template <int STAGES>
 struct LayoutP {
   static constexpr int A_BYTES = NPLANE * BM * 64;
   static constexpr int B_BYTES = NPLANE * BNP * 64;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int TILE_BYTES = BM * STAGE_LD * 8;
+  static constexpr int TILE_BYTES = BM * ROWDOT_LD * 8;
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = STAGES * STAGE_BYTES + TILE_BYTES + BAR_BYTES + 1024;
   static constexpr uint32_t TMEM_COLS = 512;
@@ -383,6 +238,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = t0; t < t1; ++t) {
       int b, mt, nt;
       p.tile(t, b, mt, nt);
+      if constexpr (P::kRowDot) {
+        // the previous tile's rows are all dotted: fetch this tile's operand while its
+        // chunks are drained
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!*abort) p.prefetch(b, mt, nt, tile_buf, threadIdx.x - 64);
+        tc::cp_async_commit();
+      }
       float sre[BNP], sim[BNP];
 #pragma unroll
       for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
@@ -420,12 +282,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce[set]);
       }
-      // stage the tile, then let the policy store it with its own (coalesced) mapping
-      asm volatile("bar.sync 1, 128;" ::: "memory");   // previous tile fully stored
+      if constexpr (P::kRowDot) {
+        tc::cp_async_wait_all();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!*abort) p.row_dot(b, mt, nt, r, sre, sim, tile_buf);
+      } else {
+        // stage the tile, then let the policy store it with its own (coalesced) mapping
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // previous tile fully stored
 #pragma unroll
-      for (int c = 0; c < BNP; ++c) tile_buf[r * STAGE_LD + c] = make_float2(sre[c], sim[c]);
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (!*abort) p.store_tile(b, mt, nt, tile_buf, threadIdx.x - 64, warp - 2, lane);
+        for (int c = 0; c < BNP; ++c) tile_buf[r * STAGE_LD + c] = make_float2(sre[c], sim[c]);
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!*abort) p.store_tile(b, mt, nt, tile_buf, threadIdx.x - 64, warp - 2, lane);
+      }
     }
   }
   tc::fence_before_sync();
@@ -446,21 +314,6 @@ struct MapSpec {
 };
 
 cudaError_t make_map(CUtensorMap* map, void* base, const MapSpec& s);
-
-template <int BN, int STAGES, class P>
-cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
-  using Lay = Layout<BN, STAGES>;
-  auto fn = cgemm_kernel<BN, STAGES, P>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (p.tiles <= 0) return cudaSuccess;
-  fn<<<p.tiles, THREADS, Lay::SMEM, st>>>(a, b, p, err);
-  return cudaGetLastError();
-}
 
 template <int STAGES, class P>
 cudaError_t launch_precise(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
