@@ -337,18 +337,28 @@ struct TaylorP {
     const float st = inv_j / V_SCALE, inv_s = 1.f / s_t[b];
     const size_t ps = (size_t)R * NMp;
     __half* tb = t_next + (size_t)b * 4 * ps;
-    for (int e = tid; e < 128 * BN; e += 128) {
-      const int r = e / BN, c = e % BN;
-      const int j = mt * 128 + r, i = nt * BN + c;
-      if (j >= R || i >= NM) continue;
-      const float2 v = tile[r * tcg::STAGE_LD + c];
-      const float tr = v.x * st, ti = v.y * st;
-      double2* a = acc + ((size_t)b * R + j) * NM + i;
-      double2 av = *a;
-      av.x += (double)(tr * inv_s);
-      av.y += (double)(ti * inv_s);
-      *a = av;
-      put4f(tb, ps, (size_t)j * NMp + i, tr, ti);
+    double2* ab = acc + (size_t)b * R * NM;
+    // the accumulator is read, updated and written back: all U reads of a batch are
+    // issued before its writes, so they overlap instead of waiting on one another
+    constexpr int U = 16;
+    for (int e0 = tid; e0 < 128 * BN; e0 += 128 * U) {
+      double2 av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + 128 * u, j = mt * 128 + e / BN, i = nt * BN + e % BN;
+        if (j < R && i < NM) av[u] = ab[(size_t)j * NM + i];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + 128 * u, r = e / BN, c = e % BN, j = mt * 128 + r, i = nt * BN + c;
+        if (j >= R || i >= NM) continue;
+        const float2 v = tile[r * tcg::STAGE_LD + c];
+        const float tr = v.x * st, ti = v.y * st;
+        av[u].x += (double)(tr * inv_s);
+        av[u].y += (double)(ti * inv_s);
+        ab[(size_t)j * NM + i] = av[u];
+        put4f(tb, ps, (size_t)j * NMp + i, tr, ti);
+      }
     }
   }
 };
