@@ -28,6 +28,8 @@
 #include <vector>
 
 #include "mixed.hpp"
+#include "ffla.hpp"
+#include "split.cuh"
 #include "tc_gemm.cuh"
 
 struct MixedState {
@@ -55,6 +57,7 @@ struct MixedState {
   float2* bproj32 = nullptr;                             // the same in fp32 (Green epilogue)
   float* inv_s_lh = nullptr;                             // 1 / s_lh
   zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
+  float4* s_ff = nullptr;                                // [WS][N][N] double-float overlap matrices
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
@@ -65,38 +68,12 @@ namespace mixed {
 // Output tile width of the precise GEMM (tc_gemm.cuh): 64 columns.
 constexpr int BN = tcg::BNP;
 constexpr int STAGES = 3;
-constexpr float SCALE_TARGET = 4096.f;
 constexpr float V_SCALE = 1024.f;   // fixed scale of vHS entries (|V| < 64 fits fp16 hi)
 constexpr int ZCTAS = 304;
 
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float pow2_scale(double maxabs) {
-  if (!(maxabs > 0.0) || !isfinite(maxabs)) return 1.f;
-  int e;
-  frexp((double)SCALE_TARGET / maxabs, &e);  // 2^(e-1) <= target/max < 2^e
-  e -= 1;
-  e = max(-100, min(100, e));
-  return (float)ldexp(1.0, e);
-}
-
-// x*s split into hi = fp16(x*s) and lo = fp16(x*s - hi), in fp32 (s is a power of two, so
-// x*s is exact; x*s - hi is exact in fp32).  FP64 arithmetic is avoided on purpose: the
-// FP64 pipe of this GPU is about 60x slower than FP32.
-__device__ __forceinline__ void split_val(float xs, __half& hi, __half& lo) {
-  hi = __float2half_rn(xs);
-  lo = __float2half_rn(xs - __half2float(hi));
-}
-__device__ __forceinline__ void put4f(__half* base, size_t plane_stride, size_t idx, float re, float im) {
-  __half h, l;
-  split_val(re, h, l);
-  base[idx] = h;
-  base[plane_stride + idx] = l;
-  split_val(im, h, l);
-  base[2 * plane_stride + idx] = h;
-  base[3 * plane_stride + idx] = l;
-}
 // FP64 input of moderate range: rounded once to fp32 (24 bits, of which the split keeps
 // 22), then scaled (per-step operands: walkers, inverses, Green's functions)
 __device__ __forceinline__ void put4(__half* base, size_t plane_stride, size_t idx, double re, double im, float s) {
@@ -523,21 +500,20 @@ __global__ void split_rows_kernel(const zc* src, int rows, int cols, int ldd, co
   }
 }
 
-// Sinv [WS][N][N] (FP64) -> split planes of Sinv^T [WS][4][N][Np]; grid (WS, chunks)
-__global__ void split_sinvT_kernel(const zc* Sinv, const unsigned long long* mx, float* scale, __half* out, int N,
-                                   int Np) {
-  const int ws = blockIdx.x;
-  const float s = scale_from_bits(mx + ws);
-  if (blockIdx.y == 0 && threadIdx.x == 0) scale[ws] = s;
-  const int per = N * N, chunk = (per + gridDim.y - 1) / gridDim.y;
-  const int b = blockIdx.y * chunk, e_end = min(per, b + chunk);
-  const zc* p = Sinv + (size_t)ws * N * N;
-  const size_t ps = (size_t)N * Np;
-  __half* o = out + (size_t)ws * 4 * ps;
-  for (int e = b + threadIdx.x; e < e_end; e += blockDim.x) {
-    const int i = e / N, j = e % N;   // out row i, col j = Sinv[j][i]
-    const zc v = p[(size_t)j * N + i];
-    put4(o, ps, (size_t)i * Np + j, v.x, v.y, s);
+// src[m][rows][cols] (fp32) -> dst[m][4][rows][ldd] with the per-matrix scale; grid (nmat, chunks)
+__global__ void split_rows32_kernel(const float2* src, int rows, int cols, int ldd, const unsigned long long* mx,
+                                    float* scale, __half* dst) {
+  const int mI = blockIdx.x;
+  const float s = scale_from_bits(mx + mI);
+  if (blockIdx.y == 0 && threadIdx.x == 0) scale[mI] = s;
+  const size_t per = (size_t)rows * cols, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+  const float2* p = src + (size_t)mI * per;
+  const size_t ps = (size_t)rows * ldd;
+  __half* o = dst + (size_t)mI * 4 * ps;
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+    const size_t i = e / cols, j = e % cols;
+    put4f(o, ps, i * ldd + j, p[e].x * s, p[e].y * s);
   }
 }
 
@@ -710,20 +686,6 @@ __global__ void trial_projector_kernel(const zc* A, zc* B, zc* scratch, int M, i
     zc v = zzero();
     for (int b = 0; b < n; ++b) v = zfma(Ak[p * n + b], aug[b * 2 * n + n + a], v);
     B[(size_t)k * M * n + e] = v;
-  }
-}
-
-// phi_perp[ws][(k,p)][j] = phi[ws][(k,p)][j] - sum_a B[k][p][a] S[ws][(k,a)][j]  (FP64); grid (ws, k)
-__global__ void project_kernel(const zc* phi, const zc* S, const zc* B, zc* out, int nk, int M, int n, int N) {
-  const int ws = blockIdx.x, k = blockIdx.y;
-  const zc* Bk = B + (size_t)k * M * n;
-  const zc* Sk = S + ((size_t)ws * N + (size_t)k * n) * N;
-  const size_t base = ((size_t)ws * nk * M + (size_t)k * M) * N;
-  for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
-    const int p = e / N, j = e % N;
-    zc v = phi[base + e];
-    for (int a = 0; a < n; ++a) v = zsub(v, zmul(Bk[p * n + a], Sk[(size_t)a * N + j]));
-    out[base + e] = v;
   }
 }
 
@@ -1025,6 +987,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->inv_s_lh, (size_t)nk * G, true, st));
   const int zctas = std::min(T, ZCTAS);
   MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
+  MTRY(dalloc(h, &m->s_ff, (size_t)WS * h->N * h->N, false, st));
   MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
 
   // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
@@ -1105,30 +1068,35 @@ cudaError_t set_one_body(afqmc_kp* h, cudaStream_t st) {
 constexpr int SPLIT_CHUNKS = 16;  // blocks per matrix in the split kernels
 
 // overlap + LU + inverse (FP64), split operands, Gh GEMM, split Gh
+// log det (A^dag phi) of every walker-spin, double-float (ffla.cu)
+static cudaError_t overlap_logdet(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  MTRY(ffla::overlap(h->A, phi, nullptr, m->s_ff, nullptr, nullptr, m->WS, h->nk, h->M, h->n, h->N, st));
+  AFQMC_LAUNCHED(h);
+  MTRY(ffla::invert(m->s_ff, m->WS, h->N, ld, sing, h->flags, nullptr, m->Np, nullptr, st));
+  AFQMC_LAUNCHED(h);
+  return cudaSuccess;
+}
+
 static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
   MixedState* m = h->mixed;
   int* err = h->flags + 1;
   const int WS = m->WS;
   unsigned long long* mx_phi = m->mx;
-  unsigned long long* mx_sinv = m->mx + WS;
   unsigned long long* mx_g = m->mx + 2 * WS;
   // phi (A^dag phi)^-1 = B + phi_perp S^-1 with B = A (A^dag A)^-1 and phi_perp = phi - B S:
   // the trial-subspace part is exact, so the split GEMM never forms the large
   // cancelling partial sums of S^-1 (A^dag phi) = I.
-  zc* phi_perp = reinterpret_cast<zc*>(m->acc);  // free until the Taylor series
-  MTRY(fp64::overlap_only(h, phi, st));
-  project_kernel<<<dim3(WS, h->nk), 256, 0, st>>>(phi, h->S, m->bproj, phi_perp, h->nk, h->M, h->n, h->N);
-  AFQMC_LAUNCHED(h);
-  MTRY(fp64::lu_only(h, ld, sing, 1, st));
+  float2* phi_perp = reinterpret_cast<float2*>(m->acc);  // free until the Taylor series
+  // S = A^dag phi, phi_perp and S^-1 / log det in double-float (ffla.cu); the inverse
+  // leaves the kernel as the split planes of S^-T
   MTRY(cudaMemsetAsync(m->mx, 0, sizeof(unsigned long long) * (2 * WS + 3 * h->W), st));
-  maxabs_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi_perp, (size_t)h->NM * h->N, mx_phi);
+  MTRY(ffla::overlap(h->A, phi, m->bproj, m->s_ff, phi_perp, mx_phi, WS, h->nk, h->M, h->n, h->N, st));
   AFQMC_LAUNCHED(h);
-  maxabs_kernel<<<dim3(WS, 4), 256, 0, st>>>(h->Sinv, (size_t)h->N * h->N, mx_sinv);
+  MTRY(ffla::invert(m->s_ff, WS, h->N, ld, sing, h->flags, m->sinvt_sp, m->Np, m->s_sinv, st));
   AFQMC_LAUNCHED(h);
-  split_rows_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi_perp, h->NM, h->N, m->Np, mx_phi, m->s_phi,
-                                                             m->phi_sp);
-  AFQMC_LAUNCHED(h);
-  split_sinvT_kernel<<<dim3(WS, 4), 256, 0, st>>>(h->Sinv, mx_sinv, m->s_sinv, m->sinvt_sp, h->N, m->Np);
+  split_rows32_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi_perp, h->NM, h->N, m->Np, mx_phi, m->s_phi,
+                                                               m->phi_sp);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
   GreenP p;
@@ -1245,7 +1213,8 @@ cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logd
   prof_end(h, st);
   if (e != cudaSuccess) return e;
   prof_begin(h, AFQMC_STAGE_WEIGHT, st);
-  e = fp64::weights(h, phi, x, w, do_qr ? nullptr : logdet, st);
+  e = overlap_logdet(h, phi, h->ld_new, h->sing_new, st);
+  if (e == cudaSuccess) e = fp64::weight_only(h, x, w, do_qr ? nullptr : logdet, st);
   prof_end(h, st);
   if (e != cudaSuccess) return e;
   if (do_qr) return orthonormalise(h, phi, logdet, st);
@@ -1297,7 +1266,7 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
 cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
   prof_begin(h, AFQMC_STAGE_QR, st);
   cudaError_t e = cholqr2(h, phi, st);
-  if (e == cudaSuccess && logdet) e = fp64::overlap_lu(h, phi, logdet, h->sing_new, 0, st);
+  if (e == cudaSuccess && logdet) e = overlap_logdet(h, phi, logdet, h->sing_new, st);
   prof_end(h, st);
   return e;
 }
@@ -1368,7 +1337,7 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
   if (do_qr) {
     MSTAGE(AFQMC_STAGE_QR, cholqr2(h, phi, st));
-    MSTAGE(AFQMC_STAGE_QR, fp64::overlap_lu(h, phi, h->ld_new, h->sing_new, 0, st));
+    MSTAGE(AFQMC_STAGE_QR, overlap_logdet(h, phi, h->ld_new, h->sing_new, st));
     if (logdet)
       MTRY(cudaMemcpyAsync(logdet, h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, st));
   }
