@@ -404,7 +404,7 @@ struct GramP {
   int tiles, kchunks;
   int mt_n, nt_n, N;
   const float* s_t;   // per walker
-  double2* gram;      // [WS][N][N]
+  float2* gram;       // [WS][N][N]
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -423,7 +423,7 @@ struct GramP {
       const int i = mt * 128 + r, j = nt * BN + c;
       if (i >= N || j >= N) continue;
       const float2 v = tile[r * tcg::STAGE_LD + c];
-      gram[((size_t)ws * N + i) * N + j] = make_double2((double)(v.x * st), (double)(v.y * st));
+      gram[((size_t)ws * N + i) * N + j] = make_float2(v.x * st, v.y * st);
     }
   }
 };
@@ -707,67 +707,114 @@ __global__ void split_T_kernel(const zc* phi, const unsigned long long* mx, floa
   }
 }
 
-// Gram = R^dag R (Cholesky, FP64, upper R in place), X = R^-1 (FP64, into X), and the
-// split planes of X^T [WS][4][N][Np] with a per-ws scale.  One block per walker-spin.
-// A Gram matrix that is not positive definite leaves X = I (the walker is kept) and
-// is counted with the singular walkers.
-__global__ void __launch_bounds__(256) chol_inv_kernel(zc* gram, zc* X, __half* out, float* scale, int* flags, int N,
-                                                       int Np) {
-  const int ws = blockIdx.x;
-  zc* G = gram + (size_t)ws * N * N;
-  zc* Xw = X + (size_t)ws * N * N;
+// Gram = R^dag R (Cholesky, upper R in place) and X = R^-1, both in fp32 (the Gram
+// comes from the split GEMM, about 22 bits, so FP64 would add nothing), then the split
+// planes of X^T [WS][4][N][Np] with a per-ws scale.  One block per walker-spin, the
+// matrix in shared memory when it fits (SMEM), else in place in global memory.
+// R^-1 is formed by Gauss-Jordan elimination on the upper triangle: step j scales row j
+// by 1/r_jj and clears column j from the rows above it, N^3/6 complex multiply-adds with
+// every step fully parallel.  A Gram matrix that is not positive definite leaves X = I
+// (the walker is kept) and is counted with the singular walkers.
+constexpr int CI_THREADS = 512;
+template <bool SMEM>
+__global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(float2* gram, __half* out, float* scale, int* flags,
+                                                              int N, int Np) {
+  extern __shared__ __align__(16) unsigned char ci_smem[];
+  constexpr int NW = CI_THREADS / 32;
   __shared__ int s_fail;
-  __shared__ double red[32];
-  if (threadIdx.x == 0) s_fail = 0;
+  __shared__ float s_red[NW];
+  const int ws = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2* g = gram + (size_t)ws * N * N;
+  float2* a = SMEM ? reinterpret_cast<float2*>(ci_smem) : g;
+  float2* fcol = reinterpret_cast<float2*>(ci_smem + (SMEM ? (size_t)N * N * sizeof(float2) : 0));
+  if (SMEM)
+    for (int e = tid; e < N * N; e += CI_THREADS) a[e] = g[e];
+  if (tid == 0) s_fail = 0;
   __syncthreads();
+  // Cholesky, right-looking, upper triangle only
   for (int j = 0; j < N; ++j) {
-    const double d = G[(size_t)j * N + j].x;
-    if (!(d > 0.0) || !isfinite(d)) {
-      if (threadIdx.x == 0) s_fail = 1;
-      __syncthreads();
+    const float d = a[(size_t)j * N + j].x;
+    if (!(d > 0.f) || !isfinite(d)) {   // the same value in every thread
+      if (tid == 0) s_fail = 1;
       break;
     }
-    const double rjj = sqrt(d);
-    for (int c = j + 1 + threadIdx.x; c < N; c += blockDim.x) G[(size_t)j * N + c] = zscale(G[(size_t)j * N + c], 1.0 / rjj);
-    __syncthreads();
-    if (threadIdx.x == 0) G[(size_t)j * N + j] = zmake(rjj, 0.0);
-    const int rem = N - j - 1;
-    for (long e = threadIdx.x; e < (long)rem * rem; e += blockDim.x) {
-      const int i = j + 1 + (int)(e / rem), c = j + 1 + (int)(e % rem);
-      if (c >= i) G[(size_t)i * N + c] = zsub(G[(size_t)i * N + c], zmul(zconj(G[(size_t)j * N + i]), G[(size_t)j * N + c]));
+    const float r = sqrtf(d), ir = 1.f / r;
+    __syncthreads();   // every thread has read a[j][j]
+    for (int c = j + tid; c < N; c += CI_THREADS) {
+      const float2 v = a[(size_t)j * N + c];
+      a[(size_t)j * N + c] = (c == j) ? make_float2(r, 0.f) : make_float2(v.x * ir, v.y * ir);
     }
     __syncthreads();
-  }
-  const int fail = s_fail;
-  if (fail && threadIdx.x == 0) atomicAdd(&flags[0], 1);
-  // X = R^-1 (upper triangular), one column per thread
-  for (int c = threadIdx.x; c < N; c += blockDim.x) {
-    for (int i = N - 1; i >= 0; --i) {
-      zc v = zzero();
-      if (fail) {
-        v = zmake(i == c ? 1.0 : 0.0, 0.0);
-      } else if (i == c) {
-        v = zinv(G[(size_t)c * N + c]);
-      } else if (i < c) {
-        zc sum = zzero();
-        for (int l = i + 1; l <= c; ++l) sum = zfma(G[(size_t)i * N + l], Xw[(size_t)l * N + c], sum);
-        v = zmul(zmake(-sum.x, -sum.y), zinv(G[(size_t)i * N + i]));
+    for (int i = j + 1 + warp; i < N; i += NW) {
+      const float2 u = a[(size_t)j * N + i];   // conj(R[j][i]) R[j][c]
+      for (int c = i + lane; c < N; c += 32) {
+        const float2 v = a[(size_t)j * N + c];
+        float2 t = a[(size_t)i * N + c];
+        t.x -= u.x * v.x + u.y * v.y;
+        t.y -= u.x * v.y - u.y * v.x;
+        a[(size_t)i * N + c] = t;
       }
-      Xw[(size_t)i * N + c] = v;
     }
+    __syncthreads();
   }
   __syncthreads();
-  double m = 0.0;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) m = fmax(m, cabs_d(Xw[e]));
-  m = block_max(m, red);
-  const float sc = pow2_scale(m);
-  if (threadIdx.x == 0) scale[ws] = sc;
+  const int fail = s_fail;
+  if (fail && tid == 0) atomicAdd(&flags[0], 1);
+  if (!fail) {
+    for (int j = 0; j < N; ++j) {
+      const float inv = 1.f / a[(size_t)j * N + j].x;   // r_jj is real and positive
+      for (int i = tid; i < j; i += CI_THREADS) fcol[i] = a[(size_t)i * N + j];
+      __syncthreads();   // every thread has read r_jj and the multipliers
+      for (int c = j + tid; c < N; c += CI_THREADS) {
+        const float2 v = a[(size_t)j * N + c];
+        a[(size_t)j * N + c] = (c == j) ? make_float2(inv, 0.f) : make_float2(v.x * inv, v.y * inv);
+      }
+      __syncthreads();
+      for (int i = warp; i < j; i += NW) {
+        const float2 f = fcol[i];
+        for (int c = j + lane; c < N; c += 32) {
+          if (c == j) {
+            a[(size_t)i * N + c] = make_float2(-f.x * inv, -f.y * inv);
+          } else {
+            const float2 v = a[(size_t)j * N + c];
+            float2 t = a[(size_t)i * N + c];
+            t.x -= f.x * v.x - f.y * v.y;
+            t.y -= f.x * v.y + f.y * v.x;
+            a[(size_t)i * N + c] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // X[i][c] (upper triangle; identity on failure); out row jr, column i = X[i][jr]
+  float m = 0.f;
+  for (int e = tid; e < N * N; e += CI_THREADS) {
+    const int i = e / N, c = e % N;
+    if (fail) {
+      if (i == c) m = 1.f;
+    } else if (i <= c) {
+      const float2 v = a[e];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) s_red[warp] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int w = 0; w < NW; ++w) m = fmaxf(m, s_red[w]);
+  const float sc = pow2_scale((double)m);
+  if (tid == 0) scale[ws] = sc;
   const size_t ps = (size_t)N * Np;
   __half* o = out + (size_t)ws * 4 * ps;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int jrow = e / N, i = e % N;  // (X^T)[j][i] = X[i][j]
-    const zc v = Xw[(size_t)i * N + jrow];
-    put4(o, ps, (size_t)jrow * Np + i, v.x, v.y, sc);
+  for (int e = tid; e < N * N; e += CI_THREADS) {
+    const int jr = e / N, i = e % N;
+    float2 v = make_float2(0.f, 0.f);
+    if (fail)
+      v.x = (i == jr) ? 1.f : 0.f;
+    else if (i <= jr)
+      v = a[(size_t)i * N + jr];
+    put4f(o, ps, (size_t)jr * Np + i, v.x * sc, v.y * sc);
   }
 }
 
@@ -1221,8 +1268,26 @@ cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logd
   return cudaSuccess;
 }
 
+static cudaError_t chol_inv(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  const int N = h->N;
+  const size_t full = (size_t)N * N * sizeof(float2) + (size_t)N * sizeof(float2);
+  const bool in_smem = full <= 220 * 1024;
+  const size_t bytes = in_smem ? full : (size_t)N * sizeof(float2);
+  float2* gram = reinterpret_cast<float2*>(h->P);
+  if (in_smem) {
+    MTRY(set_smem_attr((const void*)chol_inv_kernel<true>, bytes));
+    chol_inv_kernel<true><<<m->WS, CI_THREADS, bytes, st>>>(gram, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np);
+  } else {
+    MTRY(set_smem_attr((const void*)chol_inv_kernel<false>, bytes));
+    chol_inv_kernel<false><<<m->WS, CI_THREADS, bytes, st>>>(gram, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np);
+  }
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
 // Cholesky-QR2: twice { Gram = phi^dag phi on the tensor cores; R = chol(Gram) and R^-1 in
-// FP64; phi <- phi R^-1 on the tensor cores }.  R has a real positive diagonal, so
+// fp32; phi <- phi R^-1 on the tensor cores }.  R has a real positive diagonal, so
 // phi ends as the unique Q factor of the Householder QR with diag(R) > 0.
 static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
   MixedState* m = h->mixed;
@@ -1241,11 +1306,10 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
     g.nt_n = cdiv(N, BN);
     g.tiles = WS * g.mt_n * g.nt_n;
     g.kchunks = m->NMp / 32;
-    g.N = N; g.s_t = m->s_t; g.gram = h->P;
+    g.N = N; g.s_t = m->s_t; g.gram = reinterpret_cast<float2*>(h->P);
     MTRY(run_gemm(m->m_t[0], m->m_t0_b, g, h->flags + 1, st));
     AFQMC_LAUNCHED(h);
-    chol_inv_kernel<<<WS, 256, 0, st>>>(h->P, h->Sinv, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np);
-    AFQMC_LAUNCHED(h);
+    MTRY(chol_inv(h, st));
     maxabs_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, (size_t)NM * N, mx_phi);
     AFQMC_LAUNCHED(h);
     split_rows_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, NM, N, m->Np, mx_phi, m->s_phi, m->phi_sp);

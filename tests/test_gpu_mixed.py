@@ -40,6 +40,9 @@ SPECS = {
     "3x3x3-small": gen.SystemSpec(grid=(3, 3, 3), M=4, nocc=1, nchol=9, nwalkers=2, random_trial=True, seed=11),
     # more than 128 walker-spins: two row tiles in every walker-batched GEMM
     "2x1x1-many-walkers": gen.SystemSpec(grid=(2, 1, 1), M=6, nocc=2, nchol=10, nwalkers=70, seed=2),
+    # N = 128 occupied orbitals: the overlap inverse is too large for shared memory and
+    # runs on its global-memory variant
+    "2x2x2-N128": gen.SystemSpec(grid=(2, 2, 2), M=20, nocc=16, nchol=10, nwalkers=2, random_trial=True, seed=9),
 }
 
 
@@ -156,5 +159,20 @@ def test_diamond_size_sampled():
     pn, wn, _, _, _ = ok.propagate_walker(osys, phis[5], x[5], 1.0)
     assert rel(phi_g[5], pn) < TOL_PHI
     assert abs(w_g[5] - wn) < TOL_W * abs(wn)
+    assert sys_.last_error() == (0, 0)
+    sys_.close()
+
+
+def test_singular_walker_gets_zero_weight():
+    spec = SPECS["2x2x2-rtrial"]
+    sys_, _ = make(spec, "mixed")
+    phis = gen.walkers(spec)
+    phis[1, 0][:, 0] = 0.0          # walker 1, spin up: a zero column makes A^dag phi singular
+    w = dev(np.ones(spec.nwalkers))
+    sys_.propagate(dev(phis), dev(gen.fields(spec, 0)), w)
+    status, nsing = sys_.last_error()
+    wg = host(w)
+    assert status == 4 and nsing >= 1
+    assert wg[1] == 0.0 and np.all(np.isfinite(wg)) and np.all(wg[[0, 2, 3, 4]] > 0)
     assert sys_.last_error() == (0, 0)
     sys_.close()
