@@ -44,6 +44,7 @@ struct MixedState {
   __half* v_sp = nullptr;                                // [W][4][NM][NMp]
   __half* t_sp[2] = {nullptr, nullptr}; float* s_t = nullptr;  // [W][4][2N][NMp]
   double2* acc = nullptr;                                // [W][2N][NM]
+  float2* p32 = nullptr;                                 // [W][2N][NM] phi' in fp32 (Taylor series)
   double2* xpart = nullptr;                              // [T][ntile][WS]
   double2* xk = nullptr;                                 // [Nk][W][Nk][G] per-k-block Cholesky traces
   unsigned long long* mx = nullptr;                      // max |.| bit patterns: phi[WS], sinv[WS], g[3W], acc[W]
@@ -291,14 +292,23 @@ struct VhsP {
 };
 
 // One Taylor term: T_j[w] = V[w] T_{j-1}[w] / j in transposed form (rows j' = (spin, column)).
+// One Horner step of the Taylor series (order K): u <- phi' + V u / j, j = K .. 1, so that
+// after the last step u = sum_j V^j phi' / j! (Sec. 3.2 step 3).  Rows j of R = 2N
+// (spin, column), columns i of NM, D = sum_k U[j][k] V[i][k]; D carries the operand
+// scales s_t (A) and V_SCALE (B), so (V u / j) * s_t = D * inv_j / V_SCALE.
+//   inner steps: the new u * s_t = p32 * s_t + D * inv_j / V_SCALE goes to the split
+//                planes t_next (fp32: u only ever enters a further product with V);
+//   last step:   acc = phi' (FP64) + V u, the identity part exact.
 struct TaylorP {
   static constexpr bool kConjA = false;
   static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, R, NM, NMp;
   float inv_j;
+  int last;
   const float* s_t;
-  double2* acc;       // [W][R][NM]
+  const float2* p32;  // [W][R][NM] phi' in fp32
+  double2* acc;       // [W][R][NM] phi' in FP64 on entry, the result after the last step
   __half* t_next;     // [W][4][R][NMp]
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
@@ -310,31 +320,47 @@ struct TaylorP {
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
-    // D carries the operand scales s_t (A) and V_SCALE (B): T_j * s_t = D * inv_j / V_SCALE
-    const float st = inv_j / V_SCALE, inv_s = 1.f / s_t[b];
-    const size_t ps = (size_t)R * NMp;
-    __half* tb = t_next + (size_t)b * 4 * ps;
-    double2* ab = acc + (size_t)b * R * NM;
-    // the accumulator is read, updated and written back: all U reads of a batch are
-    // issued before its writes, so they overlap instead of waiting on one another
+    const float st = inv_j / V_SCALE, sc = s_t[b];
+    // all U reads of a batch are issued before its writes, so they overlap
     constexpr int U = 16;
-    for (int e0 = tid; e0 < 128 * BN; e0 += 128 * U) {
-      double2 av[U];
+    if (last) {
+      const float inv_s = 1.f / sc;   // power of two: exact
+      double2* ab = acc + (size_t)b * R * NM;
+      for (int e0 = tid; e0 < 128 * BN; e0 += 128 * U) {
+        double2 av[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + 128 * u, j = mt * 128 + e / BN, i = nt * BN + e % BN;
-        if (j < R && i < NM) av[u] = ab[(size_t)j * NM + i];
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + 128 * u, j = mt * 128 + e / BN, i = nt * BN + e % BN;
+          if (j < R && i < NM) av[u] = ab[(size_t)j * NM + i];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + 128 * u, r = e / BN, c = e % BN, j = mt * 128 + r, i = nt * BN + c;
+          if (j >= R || i >= NM) continue;
+          const float2 v = tile[r * tcg::STAGE_LD + c];
+          av[u].x += (double)(v.x * st * inv_s);
+          av[u].y += (double)(v.y * st * inv_s);
+          ab[(size_t)j * NM + i] = av[u];
+        }
       }
+    } else {
+      const size_t ps = (size_t)R * NMp;
+      __half* tb = t_next + (size_t)b * 4 * ps;
+      const float2* pb = p32 + (size_t)b * R * NM;
+      for (int e0 = tid; e0 < 128 * BN; e0 += 128 * U) {
+        float2 pv[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = e0 + 128 * u, r = e / BN, c = e % BN, j = mt * 128 + r, i = nt * BN + c;
-        if (j >= R || i >= NM) continue;
-        const float2 v = tile[r * tcg::STAGE_LD + c];
-        const float tr = v.x * st, ti = v.y * st;
-        av[u].x += (double)(tr * inv_s);
-        av[u].y += (double)(ti * inv_s);
-        ab[(size_t)j * NM + i] = av[u];
-        put4f(tb, ps, (size_t)j * NMp + i, tr, ti);
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + 128 * u, j = mt * 128 + e / BN, i = nt * BN + e % BN;
+          if (j < R && i < NM) pv[u] = pb[(size_t)j * NM + i];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + 128 * u, r = e / BN, c = e % BN, j = mt * 128 + r, i = nt * BN + c;
+          if (j >= R || i >= NM) continue;
+          const float2 v = tile[r * tcg::STAGE_LD + c];
+          put4f(tb, ps, (size_t)j * NMp + i, fmaf(pv[u].x, sc, v.x * st), fmaf(pv[u].y, sc, v.y * st));
+        }
       }
     }
   }
@@ -589,7 +615,9 @@ __global__ void split_y_kernel(const zc* y, const float* s_l, __half* out, float
 // acc[w][s*N + j][(k,p)] = phi[w][s][(k,p)][j] + sum_q D[k][p][q] phi[w][s][(k,q)][j]
 // grid (k, ws, j-chunk of 64); the correction runs in fp32 on an fp32 copy staged in
 // shared memory, the identity part is the FP64 input itself.
-__global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* acc, int nk, int M, int N, int NM) {
+__global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* acc, float2* p32,
+                                  unsigned long long* mx, int nk, int M, int N, int NM) {
+  __shared__ double red[32];
   const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
@@ -604,6 +632,7 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* a
     blk[q * 64 + j] = make_float2((float)v.x, (float)v.y);
   }
   __syncthreads();
+  double m = 0.0;
   for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
     const int j = e / M, p = e % M;
     float cr = 0.f, ci = 0.f;
@@ -614,8 +643,15 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* a
       ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
     }
     const zc id = src[(size_t)(k * M + p) * N + j0 + j];
-    acc[((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p] = make_double2(id.x + cr, id.y + ci);
+    const size_t o = ((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p;
+    acc[o] = make_double2(id.x + cr, id.y + ci);
+    const float2 b = blk[p * 64 + j];
+    const float2 v = make_float2(b.x + cr, b.y + ci);
+    p32[o] = v;
+    m = fmax(m, (double)fmaxf(fabsf(v.x), fabsf(v.y)));
   }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomic_max_pos(mx + w, m);
 }
 
 // phi[w][s][(k,p)][j] = acc + sum_q D[k][p][q] acc[(k,q)] with acc[w][s*N + j][(k, .)]
@@ -1018,6 +1054,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->t_sp[1], (size_t)W * 4 * 2 * N * NMp, true, st));
   MTRY(dalloc(h, &m->s_t, W, true, st));
   MTRY(dalloc(h, &m->acc, (size_t)W * 2 * N * NM, true, st));
+  MTRY(dalloc(h, &m->p32, (size_t)W * 2 * N * NM, true, st));
   MTRY(dalloc(h, &m->xpart, (size_t)T * ntx * WS, true, st));
   MTRY(dalloc(h, &m->xk, (size_t)nk * W * nk * G, true, st));
   MTRY(dalloc(h, &m->mx, (size_t)2 * WS + 3 * W + W, true, st));
@@ -1213,17 +1250,17 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   MixedState* m = h->mixed;
   const int R = 2 * h->N;
   dim3 g1(h->nk, m->WS, cdiv(h->N, 64));
-  onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, m->acc, h->nk, h->M, h->N, h->NM);
-  AFQMC_LAUNCHED(h);
   unsigned long long* mx_acc = m->mx + 2 * m->WS + 3 * h->W;
   MTRY(cudaMemsetAsync(mx_acc, 0, sizeof(unsigned long long) * h->W, st));
-  maxabs_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->acc, (size_t)R * h->NM, mx_acc);
+  onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, m->acc, m->p32, mx_acc, h->nk, h->M, h->N,
+                                                       h->NM);
   AFQMC_LAUNCHED(h);
-  split_rows_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->acc, R, h->NM, m->NMp, mx_acc, m->s_t, m->t_sp[0]);
+  split_rows32_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->p32, R, h->NM, m->NMp, mx_acc, m->s_t, m->t_sp[0]);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
-  for (int j = 1; j <= h->order; ++j) {
-    const int cur = (j - 1) & 1, nxt = j & 1;
+  // Horner: u = phi'; u <- phi' + V u / j for j = order .. 1
+  for (int j = h->order, step = 0; j >= 1; --j, ++step) {
+    const int cur = step & 1, nxt = (step + 1) & 1;
     TaylorP p;
     p.mt_n = cdiv(R, 128);
     p.nt_n = cdiv(h->NM, BN);
@@ -1231,7 +1268,8 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
     p.kchunks = m->NMp / 32;
     p.R = R; p.NM = h->NM; p.NMp = m->NMp;
     p.inv_j = 1.f / (float)j;
-    p.s_t = m->s_t; p.acc = m->acc; p.t_next = m->t_sp[nxt];
+    p.last = (j == 1);
+    p.s_t = m->s_t; p.p32 = m->p32; p.acc = m->acc; p.t_next = m->t_sp[nxt];
     MTRY(run_gemm(m->m_t[cur], m->m_v, p, h->flags + 1, st));
     AFQMC_LAUNCHED(h);
   }
