@@ -90,9 +90,8 @@ template <int STAGES, class P>
 __global__ void __launch_bounds__(THREADS, 1)
     cgemm_precise_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const P p, int* err) {
-  // Persistent: CTA i handles the contiguous tile range [i*per, min((i+1)*per, tiles)), so
-  // consecutive tiles of one CTA share operands in L2.  The TMA ring and the two TMEM
-  // accumulator sets run continuously across tile boundaries.  One drain per 32-wide k
+  // Persistent: CTA i handles tiles i, i + grid, i + 2 grid, ...  The TMA ring and the
+  // two TMEM accumulator sets run continuously across tile boundaries.  One drain per 32-wide k
   // chunk: per accumulator the four small cross products of the chunk go first, then
   // the two hi*hi products, so a drained partial carries two full-magnitude truncations.
   using Lay = LayoutP<STAGES>;
@@ -128,9 +127,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  const int per = (p.tiles + gridDim.x - 1) / gridDim.x;
-  const int t0 = blockIdx.x * per;
-  const int t1 = min(p.tiles, t0 + per);
+  // tile t runs on CTA t mod gridDim.x: the tiles in flight at any moment are
+  // consecutive, so the operands they share (one walker's rows, one Cholesky block)
+  // are read from HBM once and served from L2 to the others
+  const int t0 = blockIdx.x, tstep = gridDim.x;
   const int KC = p.kchunks;
 
   if (warp == 0) {
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc::tma_prefetch(&tmB);
       long g = 0;
       bool failed = false;
-      for (int t = t0; t < t1 && !failed; ++t) {
+      for (int t = t0; t < p.tiles && !failed; t += tstep) {
         int b, mt, nt;
         p.tile(t, b, mt, nt);
         for (int kc = 0; kc < KC; ++kc, ++g) {
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr uint32_t id = tc::idesc_f16(BM, BNP, false);
       long g = 0;
       bool failed = false;
-      for (int t = t0; t < t1 && !failed; ++t) {
+      for (int t = t0; t < p.tiles && !failed; t += tstep) {
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % STAGES);
           const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
     long g = 0;
     bool ok = true;
-    for (int t = t0; t < t1; ++t) {
+    for (int t = t0; t < p.tiles; t += tstep) {
       int b, mt, nt;
       p.tile(t, b, mt, nt);
       if constexpr (P::kRowDot) {
