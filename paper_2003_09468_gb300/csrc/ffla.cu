@@ -26,6 +26,9 @@ constexpr int GJ_THREADS = 512;
 constexpr int GJ_WARPS = GJ_THREADS / 32;
 constexpr size_t OV_SMEM_TARGET = 96 * 1024;
 constexpr size_t SMEM_LIMIT = 220 * 1024;
+// largest N held in shared memory (N^2 float4 + per-row arrays within SMEM_LIMIT; < 128,
+// which the register-held pivot row of the shared-memory variant relies on)
+constexpr int GJ_SMEM_MAXN = 118;
 
 __device__ __forceinline__ float block_max_f(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
@@ -194,8 +197,32 @@ __global__ void __launch_bounds__(GJ_THREADS)
       f[i] = fi;
     }
     __syncthreads();
-    if (INV) {
-      const float4* aj = a + (size_t)j * N;
+    const float4* aj = a + (size_t)j * N;
+    if (SMEM) {
+      // N <= GJ_SMEM_MAXN < 128: each lane owns the columns lane + 32 h, h < 4, and keeps
+      // its part of row j in registers for all the rows it updates
+      float4 ajr[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int c = lane + 32 * h;
+        ajr[h] = (c < N) ? aj[c] : ffa::czero();
+      }
+      const int i0 = INV ? warp : j + 1 + warp;
+      for (int i = i0; i < N; i += GJ_WARPS) {
+        if (INV && i == j) continue;
+        const float4 fi = f[i];
+        float4* ai = a + (size_t)i * N;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int c = lane + 32 * h;
+          if (c >= N || (!INV && c <= j)) continue;
+          if (INV && c == j)
+            ai[c] = ffa::cneg(ffa::cmul(fi, inv));
+          else
+            ai[c] = ffa::cfms(ai[c], fi, ajr[h]);
+        }
+      }
+    } else if (INV) {
       for (int i = warp; i < N; i += GJ_WARPS) {
         if (i == j) continue;
         const float4 fi = f[i];
@@ -208,7 +235,6 @@ __global__ void __launch_bounds__(GJ_THREADS)
         }
       }
     } else {
-      const float4* aj = a + (size_t)j * N;
       for (int i = j + 1 + warp; i < N; i += GJ_WARPS) {
         const float4 fi = f[i];
         float4* ai = a + (size_t)i * N;
@@ -298,7 +324,7 @@ cudaError_t overlap(const zc* A, const zc* phi, const zc* B, float4* Sff, float2
 
 cudaError_t invert(float4* Sff, int WS, int N, zc* logdet, int* sing, int* flags, __half* out, int Np, float* s_out,
                    cudaStream_t st) {
-  const bool in_smem = gj_smem_bytes(N, true) <= SMEM_LIMIT;
+  const bool in_smem = N <= GJ_SMEM_MAXN && gj_smem_bytes(N, true) <= SMEM_LIMIT;
   const size_t bytes = gj_smem_bytes(N, in_smem);
   cudaError_t e;
 #define GJ_LAUNCH(S, I)                                                                              \

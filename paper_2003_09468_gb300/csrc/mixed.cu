@@ -95,7 +95,6 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return m;
 }
 __device__ __forceinline__ double cabs_d(zc v) { return fmax(fabs(v.x), fabs(v.y)); }
-__device__ __forceinline__ double cabs_f(float2 v) { return fmax(fabs((double)v.x), fabs((double)v.y)); }
 
 template <typename T>
 static cudaError_t dalloc(afqmc_kp* h, T** p, size_t count, bool zero, cudaStream_t st) {
@@ -544,27 +543,39 @@ __global__ void split_rows32_kernel(const float2* src, int rows, int cols, int l
 }
 
 // max |.| of g32 per walker-spin and of the spin sum per walker; grid (W, chunks)
+__device__ __forceinline__ float block_max_f(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = 0.f;
+  for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+__device__ __forceinline__ float cabs_inf(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+
+// max |.| of g32 per walker-spin and of the spin sum per walker, in fp32; grid (W, chunks)
 __global__ void green_max_kernel(const float2* g32, unsigned long long* mx, int nk, int W, int nMp) {
   const int w = blockIdx.x, WS = 2 * W;
-  __shared__ double red[32];
-  const size_t per = (size_t)nk * nk * nMp, chunk = (per + gridDim.y - 1) / gridDim.y;
-  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
-  double m0 = 0.0, m1 = 0.0, ms = 0.0;
-  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
-    const size_t blk = e / nMp, off = e % nMp;
-    const float2 a = g32[(blk * WS + 2 * w) * nMp + off];
-    const float2 c = g32[(blk * WS + 2 * w + 1) * nMp + off];
-    m0 = fmax(m0, cabs_f(a));
-    m1 = fmax(m1, cabs_f(c));
-    ms = fmax(ms, fmax(fabs((double)a.x + c.x), fabs((double)a.y + c.y)));
+  __shared__ float red[32];
+  const unsigned per = (unsigned)(nk * nk * nMp), chunk = (per + gridDim.y - 1) / gridDim.y;
+  const unsigned b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+  float m0 = 0.f, m1 = 0.f, ms = 0.f;
+  for (unsigned e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+    const unsigned blk = e / nMp, off = e % nMp;
+    const float2 a = g32[((size_t)blk * WS + 2 * w) * nMp + off];
+    const float2 c = g32[((size_t)blk * WS + 2 * w + 1) * nMp + off];
+    m0 = fmaxf(m0, cabs_inf(a));
+    m1 = fmaxf(m1, cabs_inf(c));
+    ms = fmaxf(ms, cabs_inf(make_float2(a.x + c.x, a.y + c.y)));
   }
-  m0 = block_max(m0, red);
-  m1 = block_max(m1, red);
-  ms = block_max(ms, red);
+  m0 = block_max_f(m0, red);
+  m1 = block_max_f(m1, red);
+  ms = block_max_f(ms, red);
   if (threadIdx.x == 0) {
-    atomic_max_pos(mx + 3 * w, m0);
-    atomic_max_pos(mx + 3 * w + 1, m1);
-    atomic_max_pos(mx + 3 * w + 2, ms);
+    atomic_max_pos(mx + 3 * w, (double)m0);
+    atomic_max_pos(mx + 3 * w + 1, (double)m1);
+    atomic_max_pos(mx + 3 * w + 2, (double)ms);
   }
 }
 
@@ -579,16 +590,17 @@ __global__ void split_green_kernel(const float2* g32, const unsigned long long* 
     s_g[2 * w + 1] = s1;
     s_gsum[w] = ss;
   }
-  const size_t per = (size_t)nk * nk * nMp, chunk = (per + gridDim.y - 1) / gridDim.y;
-  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+  const unsigned per = (unsigned)(nk * nk * nMp), chunk = (per + gridDim.y - 1) / gridDim.y;
+  const unsigned b = blockIdx.y * chunk, e_end = min(per, b + chunk);
   const size_t psg = (size_t)nk * nk * WS * nMp, pss = (size_t)nk * nk * W * nMp;
-  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
-    const size_t blk = e / nMp, off = e % nMp;
-    const float2 a = g32[(blk * WS + 2 * w) * nMp + off];
-    const float2 c = g32[(blk * WS + 2 * w + 1) * nMp + off];
-    put4(gsp, psg, (blk * WS + 2 * w) * nMp + off, a.x, a.y, s0);
-    put4(gsp, psg, (blk * WS + 2 * w + 1) * nMp + off, c.x, c.y, s1);
-    put4(gsum, pss, (blk * W + w) * nMp + off, (double)a.x + c.x, (double)a.y + c.y, ss);
+  for (unsigned e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+    const unsigned blk = e / nMp, off = e % nMp;
+    const size_t i0 = ((size_t)blk * WS + 2 * w) * nMp + off;
+    const float2 a = g32[i0];
+    const float2 c = g32[i0 + nMp];
+    put4f(gsp, psg, i0, a.x * s0, a.y * s0);
+    put4f(gsp, psg, i0 + nMp, c.x * s1, c.y * s1);
+    put4f(gsum, pss, ((size_t)blk * W + w) * nMp + off, (a.x + c.x) * ss, (a.y + c.y) * ss);
   }
 }
 
