@@ -30,7 +30,9 @@ namespace tcg {
 constexpr int BM = 128;      // tile rows = TMEM lanes
 constexpr int BK = 32;       // complex k per stage: 64-byte fp16 rows
 constexpr int NPLANE = 4;
-constexpr int THREADS = 192; // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+// warp 0 TMA, warp 1 MMA, warps 2-5 drain the accumulators, warps 6-9 store the drained
+// tiles (so that the stores of one tile overlap the MMAs of the next)
+constexpr int THREADS = 320;
 
 struct Coords {
   int a[5];
@@ -47,7 +49,8 @@ struct Coords {
 // and, for kRowDot == false,
 //   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int ewarp, int lane) const;
 //       the finished 128 x 64 tile in shared memory, tile[r * STAGE_LD + c] = (re, im);
-//       called by the 128 epilogue threads (tid 0..127, ewarp 0..3)
+//       called by the 128 store threads (tid 0..127, ewarp 0..3) while the drain warps
+//       already accumulate the next tile
 // or, for kRowDot == true (a per-row dot product of D with a second operand tile),
 //   __device__ void prefetch(int b, int mt, int nt, float2* buf, int tid) const;
 //       issues cp.async copies of the 128 x 64 operand tile into buf[r * ROWDOT_LD + c];
@@ -226,16 +229,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
       }
     }
-  } else {
-    // All four epilogue warps run the same sequence of named barriers for every tile, so a
-    // failed (timed-out) wait never leaves a warp behind at bar.sync: failure is sticky,
+  } else if (warp < 6) {
+    // Drain warps.  All four run the same sequence of named barriers for every tile, so a
+    // failed (timed-out) wait never leaves a warp behind at a barrier: failure is sticky,
     // skips the work, and raises the abort flag that ends every later wait at once.
+    // Hand-off to the store warps: barrier 2 ("tile staged", drain arrives, store waits)
+    // and barrier 3 ("buffer free", store arrives, drain waits before the next staging
+    // and once after the last tile), one phase of each per tile on both sides.
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
     long g = 0;
     bool ok = true;
-    for (int t = t0; t < p.tiles; t += tstep) {
+    int ntile = 0;
+    for (int t = t0; t < p.tiles; t += tstep, ++ntile) {
       int b, mt, nt;
       p.tile(t, b, mt, nt);
       if constexpr (P::kRowDot) {
@@ -261,22 +268,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t d = tmem + lane_off + set * 4 * BNP;
 #pragma unroll
         for (int gq = 0; gq < BNP / 16; ++gq) {
-          float rr[16], ii[16], ri[16], ir[16];
-          tc::tmem_ld16(d + 0 * BNP + gq * 16, rr);
-          tc::tmem_ld16(d + 1 * BNP + gq * 16, ii);
-          tc::tmem_ld16(d + 2 * BNP + gq * 16, ri);
-          tc::tmem_ld16(d + 3 * BNP + gq * 16, ir);
+          float x[16], y[16];
+          tc::tmem_ld16(d + 0 * BNP + gq * 16, x);   // P_rr
+          tc::tmem_ld16(d + 1 * BNP + gq * 16, y);   // P_ii
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            if (P::kConjA) {  // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-              sre[gq * 16 + c] += rr[c] + ii[c];
-              sim[gq * 16 + c] += ri[c] - ir[c];
-            } else {
-              sre[gq * 16 + c] += rr[c] - ii[c];
-              sim[gq * 16 + c] += ri[c] + ir[c];
-            }
-          }
+          for (int c = 0; c < 16; ++c) sre[gq * 16 + c] += P::kConjA ? x[c] + y[c] : x[c] - y[c];
+          tc::tmem_ld16(d + 2 * BNP + gq * 16, x);   // P_ri
+          tc::tmem_ld16(d + 3 * BNP + gq * 16, y);   // P_ir
+          tc::tmem_ld_wait();
+          // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+#pragma unroll
+          for (int c = 0; c < 16; ++c) sim[gq * 16 + c] += P::kConjA ? x[c] - y[c] : x[c] + y[c];
         }
         tc::fence_before_sync();
         __syncwarp();
@@ -287,12 +290,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (!*abort) p.row_dot(b, mt, nt, r, sre, sim, tile_buf);
       } else {
-        // stage the tile, then let the policy store it with its own (coalesced) mapping
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // previous tile fully stored
+        if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");   // previous tile stored
 #pragma unroll
         for (int c = 0; c < BNP; ++c) tile_buf[r * STAGE_LD + c] = make_float2(sre[c], sim[c]);
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (!*abort) p.store_tile(b, mt, nt, tile_buf, threadIdx.x - 64, warp - 2, lane);
+        __threadfence_block();
+        asm volatile("bar.arrive 2, 256;" ::: "memory");
+      }
+    }
+    if constexpr (!P::kRowDot) {
+      if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");
+    }
+  } else {
+    // Store warps: write each staged tile with the policy's own (coalesced) mapping.
+    if constexpr (!P::kRowDot) {
+      const int tid = threadIdx.x - 192, ew = warp - 6;
+      for (int t = t0; t < p.tiles; t += tstep) {
+        int b, mt, nt;
+        p.tile(t, b, mt, nt);
+        asm volatile("bar.sync 2, 256;" ::: "memory");
+        if (!*abort) p.store_tile(b, mt, nt, tile_buf, tid, ew, lane);
+        __threadfence_block();
+        asm volatile("bar.arrive 3, 256;" ::: "memory");
       }
     }
   }
