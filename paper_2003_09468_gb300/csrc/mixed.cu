@@ -264,20 +264,22 @@ struct VhsP {
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
-    b = t / (nt_n * mt_n);
+    b = t / (nt_n * mt_n);   // b = Q * nk + k
   }
+  // rows (p, r) of L[Q][k] (A), columns = walkers (B = y[Q])
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
     const int Q = b / nk, k = b % nk;
-    tcg::Coords c = {{kc * 32, mt * 128, 0, Q, 0}, {kc * 32, nt * BN, 0, k, Q}};
+    tcg::Coords c = {{kc * 32, mt * 128, 0, k, Q}, {kc * 32, nt * BN, 0, Q, 0}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
     const int Q = b / nk, k = b % nk, kq = kminus[k * nk + Q];
     const size_t ps = (size_t)NM * NMp;
     bool bad = false;
+    // down the rows: consecutive threads write consecutive r of one (walker, p)
     for (int e = tid; e < 128 * BN; e += 128) {
-      const int r = e / BN, c = e % BN;
-      const int w = mt * 128 + r, pr = nt * BN + c;
+      const int r = e % 128, c = e / 128;
+      const int pr = mt * 128 + r, w = nt * BN + c;
       if (w >= W || pr >= M * M) continue;
       const float st = V_SCALE / s_y[Q * W + w];
       const float2 v = tile[r * tcg::STAGE_LD + c];
@@ -1114,9 +1116,9 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(map5(&m->m_lh, m->lh_sp, {(uint64_t)nMp, (uint64_t)G, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)nMp, (uint64_t)nk * nk * G * nMp, (uint64_t)G * nMp, (uint64_t)nk * G * nMp}, BN));
   MTRY(map5(&m->m_y, m->y_sp, {(uint64_t)Gp, (uint64_t)W, 4, (uint64_t)nk, 1},
-            {(uint64_t)Gp, (uint64_t)nk * W * Gp, (uint64_t)W * Gp, (uint64_t)nk * W * Gp * 4}, 128));
+            {(uint64_t)Gp, (uint64_t)nk * W * Gp, (uint64_t)W * Gp, (uint64_t)nk * W * Gp * 4}, BN));
   MTRY(map5(&m->m_lt, m->lt_sp, {(uint64_t)Gp, (uint64_t)M * M, 4, (uint64_t)nk, (uint64_t)nk},
-            {(uint64_t)Gp, (uint64_t)nk * nk * M * M * Gp, (uint64_t)M * M * Gp, (uint64_t)nk * M * M * Gp}, BN));
+            {(uint64_t)Gp, (uint64_t)nk * nk * M * M * Gp, (uint64_t)M * M * Gp, (uint64_t)nk * M * M * Gp}, 128));
   for (int i = 0; i < 2; ++i)
     MTRY(map5(&m->m_t[i], m->t_sp[i], {(uint64_t)NMp, (uint64_t)2 * N, 4, (uint64_t)W, 1},
               {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, 128));
@@ -1247,13 +1249,13 @@ static cudaError_t vhs(afqmc_kp* h, cudaStream_t st) {
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
   VhsP p;
-  p.mt_n = cdiv(h->W, 128);
-  p.nt_n = cdiv(h->M * h->M, BN);
+  p.mt_n = cdiv(h->M * h->M, 128);
+  p.nt_n = cdiv(h->W, BN);
   p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
   p.kchunks = m->Gp / 32;
   p.W = h->W; p.M = h->M; p.nk = h->nk; p.NM = h->NM; p.NMp = m->NMp;
   p.kminus = h->kminus; p.s_y = m->s_y; p.v_sp = m->v_sp; p.overflow = h->flags + 2;
-  MTRY(run_gemm(m->m_y, m->m_lt, p, h->flags + 1, st));
+  MTRY(run_gemm(m->m_lt, m->m_y, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   return cudaSuccess;
 }
