@@ -43,7 +43,7 @@ struct MixedState {
   __half* y_sp = nullptr;     float* s_y = nullptr;     // [4][Nk][W][Gp], s_y[Q][W]
   __half* v_sp = nullptr;                                // [W][4][NM][NMp]
   __half* t_sp[2] = {nullptr, nullptr}; float* s_t = nullptr;  // [W][4][2N][NMp]
-  double2* acc = nullptr;                                // [W][2N][NM]
+  double2* acc = nullptr;                                // [W][2N][NM] (scratch: float4 Taylor corrections, phi_perp)
   float2* p32 = nullptr;                                 // [W][2N][NM] phi' in fp32 (Taylor series)
   double2* xpart = nullptr;                              // [T][ntile][WS]
   double2* xk = nullptr;                                 // [Nk][W][Nk][G] per-k-block Cholesky traces
@@ -309,7 +309,7 @@ struct TaylorP {
   int last;
   const float* s_t;
   const float2* p32;  // [W][R][NM] phi' in fp32
-  double2* acc;       // [W][R][NM] phi' in FP64 on entry, the result after the last step
+  float4* corr;       // [W][R][NM] (d, .) with d = phi' - phi on entry; (phi'' - phi, phi'') after the last step
   __half* t_next;     // [W][4][R][NMp]
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
@@ -326,22 +326,26 @@ struct TaylorP {
     constexpr int U = 16;
     if (last) {
       const float inv_s = 1.f / sc;   // power of two: exact
-      double2* ab = acc + (size_t)b * R * NM;
+      float4* cb = corr + (size_t)b * R * NM;
+      const float2* pb = p32 + (size_t)b * R * NM;
       for (int e0 = tid; e0 < 128 * BN; e0 += 128 * U) {
-        double2 av[U];
+        float2 dv[U], pv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = e0 + 128 * u, j = mt * 128 + e / BN, i = nt * BN + e % BN;
-          if (j < R && i < NM) av[u] = ab[(size_t)j * NM + i];
+          if (j < R && i < NM) {
+            const size_t o = (size_t)j * NM + i;
+            dv[u] = reinterpret_cast<const float2*>(cb)[2 * o];
+            pv[u] = pb[o];
+          }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = e0 + 128 * u, r = e / BN, c = e % BN, j = mt * 128 + r, i = nt * BN + c;
           if (j >= R || i >= NM) continue;
           const float2 v = tile[r * tcg::STAGE_LD + c];
-          av[u].x += (double)(v.x * st * inv_s);
-          av[u].y += (double)(v.y * st * inv_s);
-          ab[(size_t)j * NM + i] = av[u];
+          const float vr = v.x * st * inv_s, vi = v.y * st * inv_s;   // V u
+          cb[(size_t)j * NM + i] = make_float4(dv[u].x + vr, dv[u].y + vi, pv[u].x + vr, pv[u].y + vi);
         }
       }
     } else {
@@ -626,10 +630,12 @@ __global__ void split_y_kernel(const zc* y, const float* s_l, __half* out, float
   }
 }
 
-// acc[w][s*N + j][(k,p)] = phi[w][s][(k,p)][j] + sum_q D[k][p][q] phi[w][s][(k,q)][j]
-// grid (k, ws, j-chunk of 64); the correction runs in fp32 on an fp32 copy staged in
-// shared memory, the identity part is the FP64 input itself.
-__global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* acc, float2* p32,
+// First one-body half step, phi' = phi + D phi with D = exp(-dt/2 H1') - I (Sec. 3.2 step
+// 3), in the transposed (row = (spin, column), column = orbital) layout of the Taylor
+// series, as fp32 parts only: p32 = phi' (rounded) and corr.xy = D phi.  The FP64 walker
+// itself is added back once, after the series (onebody_out_kernel).  mx[w] = max |p32|.
+// grid (k, ws, j-chunk of 64)
+__global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, float4* corr, float2* p32,
                                   unsigned long long* mx, int nk, int M, int N, int NM) {
   __shared__ double red[32];
   const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
@@ -656,9 +662,8 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* a
       cr = fmaf(d.x, b.x, fmaf(-d.y, b.y, cr));
       ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
     }
-    const zc id = src[(size_t)(k * M + p) * N + j0 + j];
     const size_t o = ((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p;
-    acc[o] = make_double2(id.x + cr, id.y + ci);
+    reinterpret_cast<float2*>(corr)[2 * o] = make_float2(cr, ci);
     const float2 b = blk[p * 64 + j];
     const float2 v = make_float2(b.x + cr, b.y + ci);
     p32[o] = v;
@@ -668,8 +673,10 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, double2* a
   if (threadIdx.x == 0) atomic_max_pos(mx + w, m);
 }
 
-// phi[w][s][(k,p)][j] = acc + sum_q D[k][p][q] acc[(k,q)] with acc[w][s*N + j][(k, .)]
-__global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* phi, int nk, int M, int N, int NM) {
+// Second half step: with corr.xy = d = phi'' - phi and corr.zw = phi'' (fp32) after the
+// Taylor series, phi <- phi + d + D phi'' (the sum of fp32 corrections is added to the
+// FP64 walker once).  grid (k, ws, j-chunk of 64)
+__global__ void onebody_out_kernel(const float4* corr, const float2* dhalf, zc* phi, int nk, int M, int N, int NM) {
   const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
@@ -677,11 +684,11 @@ __global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* 
   float2* blk = reinterpret_cast<float2*>(smraw);          // [64][M]
   float2* D = blk + 64 * M;                                  // [M][M]
   for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
-  const double2* src = acc + ((size_t)w * 2 * N + sp * N + j0) * NM + k * M;
+  const float4* src = corr + ((size_t)w * 2 * N + sp * N + j0) * NM + k * M;
   for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
     const int j = e / M, q = e % M;
-    const double2 v = src[(size_t)j * NM + q];
-    blk[j * M + q] = make_float2((float)v.x, (float)v.y);
+    const float4 v = src[(size_t)j * NM + q];
+    blk[j * M + q] = make_float2(v.z, v.w);
   }
   __syncthreads();
   zc* dst = phi + (size_t)ws * NM * N;
@@ -694,8 +701,11 @@ __global__ void onebody_out_kernel(const double2* acc, const float2* dhalf, zc* 
       cr = fmaf(d.x, b.x, fmaf(-d.y, b.y, cr));
       ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
     }
-    const double2 id = src[(size_t)j * NM + p];
-    dst[(size_t)(k * M + p) * N + j0 + j] = make_double2(id.x + cr, id.y + ci);
+    const float2 dd = reinterpret_cast<const float2*>(src)[2 * ((size_t)j * NM + p)];
+    zc v = dst[(size_t)(k * M + p) * N + j0 + j];
+    v.x += (double)(dd.x + cr);
+    v.y += (double)(dd.y + ci);
+    dst[(size_t)(k * M + p) * N + j0 + j] = v;
   }
 }
 
@@ -1266,7 +1276,8 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   dim3 g1(h->nk, m->WS, cdiv(h->N, 64));
   unsigned long long* mx_acc = m->mx + 2 * m->WS + 3 * h->W;
   MTRY(cudaMemsetAsync(mx_acc, 0, sizeof(unsigned long long) * h->W, st));
-  onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, m->acc, m->p32, mx_acc, h->nk, h->M, h->N,
+  float4* corr = reinterpret_cast<float4*>(m->acc);
+  onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, corr, m->p32, mx_acc, h->nk, h->M, h->N,
                                                        h->NM);
   AFQMC_LAUNCHED(h);
   split_rows32_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->p32, R, h->NM, m->NMp, mx_acc, m->s_t, m->t_sp[0]);
@@ -1283,11 +1294,11 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
     p.R = R; p.NM = h->NM; p.NMp = m->NMp;
     p.inv_j = 1.f / (float)j;
     p.last = (j == 1);
-    p.s_t = m->s_t; p.p32 = m->p32; p.acc = m->acc; p.t_next = m->t_sp[nxt];
+    p.s_t = m->s_t; p.p32 = m->p32; p.corr = corr; p.t_next = m->t_sp[nxt];
     MTRY(run_gemm(m->m_t[cur], m->m_v, p, h->flags + 1, st));
     AFQMC_LAUNCHED(h);
   }
-  onebody_out_kernel<<<g1, 256, onebody_smem(h), st>>>(m->acc, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
+  onebody_out_kernel<<<g1, 256, onebody_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }
