@@ -86,9 +86,66 @@ def taylor_flops(spec, order=6) -> float:
     return 8.0 * order * spec.nwalkers * spec.NM * spec.NM * 2 * spec.N
 
 
+def taylor_term_flops(spec) -> float:
+    """One Taylor term, V u for every walker: (2N x NM) x (NM x NM) complex, 8 flops per MAC."""
+    return 8.0 * spec.nwalkers * spec.NM * spec.NM * 2 * spec.N
+
+
 def vhs_bytes(spec) -> float:
-    """Cholesky tensor read once (complex64 equivalent) + V written once."""
+    """Cholesky tensor read once and V written once, both as four fp16 planes (8 bytes per
+    complex element), which is the form the kernel reads and writes."""
     return 8.0 * spec.nk * spec.nk * spec.nchol * spec.M * spec.M + 8.0 * spec.nwalkers * spec.NM * spec.NM
+
+
+# ---------------------------------------------------------------------------
+# measured DRAM traffic of a kernel, from its committed ncu summary
+# ---------------------------------------------------------------------------
+KERNEL_POLICY = {"taylor": "TaylorP", "exchange": "ExchangeP", "vhs": "VhsP"}
+CSRC = os.path.join(ROOT, "paper_2003_09468_gb300", "csrc")
+
+
+def kernel_fingerprint(stage: str):
+    """sha256 (12 hex digits) of the sources that define the stage's GEMM kernel: the
+    generic kernel headers and the text of its policy struct."""
+    import hashlib
+    pol = KERNEL_POLICY.get(stage)
+    if pol is None:
+        return None
+    h = hashlib.sha256()
+    try:
+        for f in ("tc.cuh", "tc_gemm.cuh", "split.cuh"):
+            with open(os.path.join(CSRC, f), "rb") as fh:
+                h.update(fh.read())
+        with open(os.path.join(CSRC, "mixed.cu")) as fh:
+            src = fh.read()
+        a = src.index(f"struct {pol} {{")
+        h.update(src[a:src.index("\n};\n", a)].encode())
+    except (OSError, ValueError):
+        return None
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(stage: str, workload: str):
+    """(bytes per launch, file) from profiles/<stage>_gemm_<workload>.md when the
+    fingerprint recorded there matches the current sources, else (None, reason)."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_gemm_{workload}.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None, "no ncu summary"
+    vals = {}
+    for line in text.splitlines():
+        for key in ("traffic_bytes_per_launch:", "source_fingerprint:"):
+            if line.strip().startswith(key):
+                vals[key] = line.split(":", 1)[1].strip()
+    fp = kernel_fingerprint(stage)
+    if fp is None or vals.get("source_fingerprint:") != fp:
+        return None, "kernel changed since the ncu capture"
+    try:
+        return float(vals["traffic_bytes_per_launch:"]), os.path.relpath(path, ROOT)
+    except (KeyError, ValueError):
+        return None, "no traffic line"
 
 
 # ---------------------------------------------------------------------------
@@ -323,15 +380,18 @@ def main():
     tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
 
     def put(stage, bound, work, peak, unit, note):
+        """Per-launch roofline of the kernel a stage times: the library records one
+        interval per launch for the Taylor GEMM and the exchange GEMM."""
         ms_s, n_s = stages[stage]
         if not n_s:
             return
         per = ms_s / n_s
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         ach = work / (per * 1e-3) / scale
+        traffic, src = measured_traffic(stage, args.workload) if precision == "mixed" else (None, None)
         rooflines[stage] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                            "traffic": None, "kernel": stage, "launch_ms": per,
-                            "algorithmic_per_launch": work, "peak_source": note}
+                            "traffic": traffic, "traffic_source": src, "kernel": stage, "launches": n_s,
+                            "launch_ms": per, "algorithmic_per_launch": work, "peak_source": note}
 
     if precision == "fp64":
         dtype = "f64"
@@ -339,18 +399,16 @@ def main():
             "FP64 nominal 1.25 TFLOP/s (GB300 FP64 pipe); a DFMA probe measured 1.20")
     else:
         dtype = "f16x2-split/f32-acc + f64"
-        note = f"dense f16/bf16 tensor, sustained, {peaks_kind}"
-        put("exchange", "tensor", exchange_precontracted_flops(spec), tensor_peak, "TFLOP/s", note)
-        stages_taylor = stages["taylor"]
-        if stages_taylor[1]:
-            ms_t = stages_taylor[0] / stages_taylor[1]
-            rooflines["taylor"] = {"bound": "tensor", "achieved": taylor_flops(spec) / (ms_t * 1e-3) / 1e12,
-                                   "peak": tensor_peak, "unit": "TFLOP/s", "traffic": None, "kernel": "taylor",
-                                   "launch_ms": ms_t, "algorithmic_per_launch": taylor_flops(spec),
-                                   "peak_source": note + "; 6 GEMM launches + one-body kernels per stage"}
-            rooflines["taylor"]["frac"] = rooflines["taylor"]["achieved"] / tensor_peak
-        put("vhs", "hbm", vhs_bytes(spec), peaks.get("hbm_gbs", 6800.0), "GB/s", f"HBM copy, {peaks_kind}")
-    dom = max(rooflines, key=lambda k: rooflines[k]["launch_ms"] * stages[k][1]) if rooflines else None
+        note = f"dense f16/bf16 tensor, sustained (kernel timed inside the step), {peaks_kind}"
+        put("taylor", "tensor", taylor_term_flops(spec), tensor_peak, "TFLOP/s",
+            note + "; one Taylor-term GEMM per launch, algorithmic flops (the 3-product fp16 split "
+                   "issues 3x as many)")
+        put("exchange", "tensor", exchange_precontracted_flops(spec), tensor_peak, "TFLOP/s",
+            note + "; algorithmic flops")
+        put("vhs", "hbm", vhs_bytes(spec), peaks.get("hbm_gbs", 6800.0), "GB/s",
+            f"HBM copy, {peaks_kind}; stage = operand split + one GEMM launch")
+    # dominant kernel: the largest total time in the timed region
+    dom = max(rooflines, key=lambda k: stages[k][0]) if rooflines else None
     roofline = rooflines.get(dom)
 
     fp64_cmp = None

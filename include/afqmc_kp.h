@@ -234,13 +234,17 @@ typedef enum {
   AFQMC_STAGE_GREEN = 0,       /* overlap, LU / inverse / log det, Green's function */
   AFQMC_STAGE_FORCE_BIAS = 1,  /* Cholesky trace X and xbar                         */
   AFQMC_STAGE_VHS = 2,         /* vHS build                                         */
-  AFQMC_STAGE_TAYLOR = 3,      /* one-body halves and the Taylor series             */
+  AFQMC_STAGE_TAYLOR = 3,      /* Taylor series; tensor-core path: the GEMMs alone,
+                                  one interval per term (FP64 path: the one-body
+                                  halves included, one interval per step)           */
   AFQMC_STAGE_WEIGHT = 4,      /* new overlap, log det and hybrid weight            */
   AFQMC_STAGE_QR = 5,          /* re-orthonormalisation                             */
   AFQMC_STAGE_ENERGY = 6,      /* E1, EC and the final sums                         */
   AFQMC_STAGE_EXCHANGE = 7,    /* the exchange contraction kernel alone             */
   AFQMC_STAGE_BACKWARD = 8,    /* adjoint kernels                                   */
-  AFQMC_NSTAGES = 9
+  AFQMC_STAGE_ONEBODY = 9,     /* tensor-core path: the one-body halves around the
+                                  Taylor series and the split of the series' input  */
+  AFQMC_NSTAGES = 10
 } afqmc_stage;
 
 /* enable != 0 starts recording (allocates CUDA events on the host side as

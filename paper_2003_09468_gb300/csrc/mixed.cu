@@ -1058,6 +1058,13 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
         const bool canon = (Q < mQ) || (Q == mQ && k <= kx);
         if (canon) tri.push_back(make_int4(Q, k, kx, self ? 1 : 2));
       }
+  // Order the triples by the Green's-function block (k - Q, kx) that is their GEMM's A
+  // operand: the triples sharing a block then run on neighbouring CTAs at the same time
+  // and read it from HBM once.
+  std::stable_sort(tri.begin(), tri.end(), [&](const int4& a, const int4& b) {
+    const int ka = h->h_kminus[(size_t)a.y * nk + a.x], kb = h->h_kminus[(size_t)b.y * nk + b.x];
+    return ka != kb ? ka < kb : a.z < b.z;
+  });
   m->T = (int)tri.size();
   const int T = m->T;
   const int ntx = cdiv(nMp, BN);
@@ -1277,11 +1284,13 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   unsigned long long* mx_acc = m->mx + 2 * m->WS + 3 * h->W;
   MTRY(cudaMemsetAsync(mx_acc, 0, sizeof(unsigned long long) * h->W, st));
   float4* corr = reinterpret_cast<float4*>(m->acc);
+  prof_begin(h, AFQMC_STAGE_ONEBODY, st);
   onebody_in_kernel<<<g1, 256, onebody_smem(h), st>>>(phi, m->dhalf, corr, m->p32, mx_acc, h->nk, h->M, h->N,
                                                        h->NM);
   AFQMC_LAUNCHED(h);
   split_rows32_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->p32, R, h->NM, m->NMp, mx_acc, m->s_t, m->t_sp[0]);
   AFQMC_LAUNCHED(h);
+  prof_end(h, st);
   MTRY(cudaGetLastError());
   // Horner: u = phi'; u <- phi' + V u / j for j = order .. 1
   for (int j = h->order, step = 0; j >= 1; --j, ++step) {
@@ -1295,11 +1304,15 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
     p.inv_j = 1.f / (float)j;
     p.last = (j == 1);
     p.s_t = m->s_t; p.p32 = m->p32; p.corr = corr; p.t_next = m->t_sp[nxt];
+    prof_begin(h, AFQMC_STAGE_TAYLOR, st);   // one interval per term: the GEMM launch alone
     MTRY(run_gemm(m->m_t[cur], m->m_v, p, h->flags + 1, st));
+    prof_end(h, st);
     AFQMC_LAUNCHED(h);
   }
+  prof_begin(h, AFQMC_STAGE_ONEBODY, st);
   onebody_out_kernel<<<g1, 256, onebody_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
   AFQMC_LAUNCHED(h);
+  prof_end(h, st);
   return cudaGetLastError();
 }
 
@@ -1318,9 +1331,7 @@ cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logd
   e = vhs(h, st);
   prof_end(h, st);
   if (e != cudaSuccess) return e;
-  prof_begin(h, AFQMC_STAGE_TAYLOR, st);
-  e = taylor(h, phi, st);
-  prof_end(h, st);
+  e = taylor(h, phi, st);   // records its own ONEBODY and TAYLOR intervals
   if (e != cudaSuccess) return e;
   prof_begin(h, AFQMC_STAGE_WEIGHT, st);
   e = overlap_logdet(h, phi, h->ld_new, h->sing_new, st);
@@ -1455,7 +1466,7 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   }
   MSTAGE(AFQMC_STAGE_FORCE_BIAS, fp64::force_bias(h, x, h->xbar, st));
   MSTAGE(AFQMC_STAGE_VHS, vhs(h, st));
-  MSTAGE(AFQMC_STAGE_TAYLOR, taylor(h, phi, st));
+  MTRY(taylor(h, phi, st));   // records its own ONEBODY and TAYLOR intervals
   MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_new, h->sing_new, st));
   MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
   MSTAGE(AFQMC_STAGE_WEIGHT, fp64::weight_only(h, x, w, do_qr ? nullptr : logdet, st));
