@@ -323,8 +323,8 @@ struct TaylorP {
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
     const float st = inv_j / V_SCALE, sc = s_t[b];
     // all U reads of a batch are issued before its writes, so they overlap
-    constexpr int U = 16;
     if (last) {
+      constexpr int U = 8;
       const float inv_s = 1.f / sc;   // power of two: exact
       float4* cb = corr + (size_t)b * R * NM;
       const float2* pb = p32 + (size_t)b * R * NM;
@@ -349,6 +349,7 @@ struct TaylorP {
         }
       }
     } else {
+      constexpr int U = 8;
       const size_t ps = (size_t)R * NMp;
       __half* tb = t_next + (size_t)b * 4 * ps;
       const float2* pb = p32 + (size_t)b * R * NM;

@@ -266,20 +266,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!ok) continue;
         tc::fence_after_sync();
         const uint32_t d = tmem + lane_off + set * 4 * BNP;
+        // 8 columns of two accumulators per load round: few registers beyond the sums
 #pragma unroll
-        for (int gq = 0; gq < BNP / 16; ++gq) {
-          float x[16], y[16];
-          tc::tmem_ld16(d + 0 * BNP + gq * 16, x);   // P_rr
-          tc::tmem_ld16(d + 1 * BNP + gq * 16, y);   // P_ii
+        for (int gq = 0; gq < BNP / 8; ++gq) {
+          float x[8], y[8];
+          tc::tmem_ld8(d + 0 * BNP + gq * 8, x);   // P_rr
+          tc::tmem_ld8(d + 1 * BNP + gq * 8, y);   // P_ii
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) sre[gq * 16 + c] += P::kConjA ? x[c] + y[c] : x[c] - y[c];
-          tc::tmem_ld16(d + 2 * BNP + gq * 16, x);   // P_ri
-          tc::tmem_ld16(d + 3 * BNP + gq * 16, y);   // P_ir
+          for (int c = 0; c < 8; ++c) sre[gq * 8 + c] += P::kConjA ? x[c] + y[c] : x[c] - y[c];
+          tc::tmem_ld8(d + 2 * BNP + gq * 8, x);   // P_ri
+          tc::tmem_ld8(d + 3 * BNP + gq * 8, y);   // P_ir
           tc::tmem_ld_wait();
           // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
 #pragma unroll
-          for (int c = 0; c < 16; ++c) sim[gq * 16 + c] += P::kConjA ? x[c] - y[c] : x[c] + y[c];
+          for (int c = 0; c < 8; ++c) sim[gq * 8 + c] += P::kConjA ? x[c] - y[c] : x[c] + y[c];
         }
         tc::fence_before_sync();
         __syncwarp();
