@@ -209,13 +209,17 @@ class OracleStepper:
         self.osys = ok.System(spec.grid, gen.cholesky(spec), gen.one_body(spec), gen.trial(spec), spec.dt)
 
     def seconds(self, walker_index: int = 0, step: int = 0) -> float:
+        return self.run(walker_index, step)[0]
+
+    def run(self, walker_index: int = 0, step: int = 0):
+        """(seconds, propagated walker, weight for w = 1, (E1, EC, EX)) of one walker-step."""
         spec, ok = self.spec, self.ok
         phi = gen.walkers(spec, 1, first=walker_index)[0]
         x = gen.fields(spec, step, 1, first=walker_index)[0]
         t0 = time.perf_counter()
-        phi_new, _, _, _, _ = ok.propagate_walker(self.osys, phi, x, 1.0)
-        ok.local_energy(self.osys, phi_new)
-        return time.perf_counter() - t0
+        phi_new, w_new, _, _, _ = ok.propagate_walker(self.osys, phi, x, 1.0)
+        e = ok.local_energy(self.osys, phi_new)
+        return time.perf_counter() - t0, phi_new, w_new, np.array(e)
 
 
 def cpu_cores() -> int:
@@ -375,6 +379,25 @@ def main():
             dist.destroy_process_group()
         return
 
+    # the first step of walker 0 from the seeded walkers, for the parity report next to the
+    # oracle's timed walker-step (untimed; the walker batch is restarted)
+    gpu_first = None
+    if not args.no_cpu_baseline and world == 1:
+        phi.copy_(torch.from_numpy(phi0).to(dev))
+        w.fill_(1.0)
+        sys_.step(phi, xs[0], w, eloc, do_qr=False, reuse=False)
+        torch.cuda.synchronize()
+        gpu_first = (phi[0].cpu().numpy(), float(w[0].item()), eloc[0].cpu().numpy())
+
+    # derived rates from the per-stage times: propagation (with the Green's function that the
+    # fused step forms for the next step) and the local energy
+    steps_t = max(args.steps, 1)
+    prop_ms = sum(stages[k][0] for k in ("green", "force_bias", "vhs", "taylor", "onebody", "weight", "qr")) / steps_t
+    en_ms = sum(stages[k][0] for k in ("energy", "exchange")) / steps_t
+    rates = {"propagate_only": spec.nwalkers * world / (prop_ms * 1e-3) if prop_ms > 0 else None,
+             "local_energy_only": spec.nwalkers * world / (en_ms * 1e-3) if en_ms > 0 else None,
+             "unit": UNIT, "source": "per-stage CUDA-event times of the timed steps"}
+
     peaks, peaks_kind = load_peaks()
     rooflines = {}
     tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -433,11 +456,21 @@ def main():
         sys_ = None
 
     cpu_baseline = None
+    parity = None
     if not args.no_cpu_baseline and world == 1:
-        t = OracleStepper(spec).seconds(0, 0)
+        t, phi_ref, w_ref, e_ref = OracleStepper(spec).run(0, 0)
         cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                         "sample": f"1 walker x 1 step (propagate + E_L) of {args.workload}, FP64 NumPy, "
                                   f"{t:.1f} s"}
+        if gpu_first is not None:
+            phi_g, w_g, e_g = gpu_first
+            parity = {"walker": 0, "step": "first step from the seeded walkers, fields of step 0",
+                      "E_L_err_ha_per_cell": [float(abs(e_g[j] - e_ref[j]) / spec.nk) for j in range(3)],
+                      "E_L_parts": ["E1", "EC", "EX"],
+                      "phi_rel_err": float(np.linalg.norm(phi_g - phi_ref) / np.linalg.norm(phi_ref)),
+                      "weight_rel_err": float(abs(w_g - w_ref) / abs(w_ref)),
+                      "tolerance": {"E_L_ha_per_cell": 1e-5, "phi_rel": 1e-6, "weight_rel": 1e-5}
+                      if precision == "mixed" else {"all_rel": 1e-10}}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -451,6 +484,8 @@ def main():
         "rooflines": rooflines,
         "fp64_path": fp64_cmp,
         "cpu_baseline": cpu_baseline,
+        "parity": parity,
+        "rates": rates,
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clk,

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "attr.hpp"
 #include "ff.cuh"
 #include "ffla.hpp"
 #include "split.cuh"
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(GJ_THREADS)
 
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  return ensure_dyn_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 size_t gj_smem_bytes(int N, bool in_smem) {

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "mixed.hpp"
+#include "attr.hpp"
 #include "ffla.hpp"
 #include "split.cuh"
 #include "tc_gemm.cuh"
@@ -1029,10 +1030,7 @@ static cudaError_t run_gemm(const CUtensorMap& a, const CUtensorMap& b, const P&
   return tcg::launch_precise<STAGES>(a, b, p, err, st);
 }
 
-static cudaError_t set_smem_attr(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+static cudaError_t set_smem_attr(const void* fn, size_t bytes) { return ensure_dyn_smem(fn, bytes); }
 
 static size_t onebody_smem(const afqmc_kp* h) {
   return sizeof(float2) * h->M * h->M + sizeof(float2) * h->M * 64;

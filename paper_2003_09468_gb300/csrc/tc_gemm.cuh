@@ -23,6 +23,7 @@
 
 #include <cuda_fp16.h>
 
+#include "attr.hpp"
 #include "tc.cuh"
 
 namespace tcg {
@@ -338,19 +339,13 @@ template <int STAGES, class P>
 cudaError_t launch_precise(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
   using Lay = LayoutP<STAGES>;
   auto fn = cgemm_precise_kernel<STAGES, P>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(fn), Lay::SMEM);
+  if (e != cudaSuccess) return e;
   if (p.tiles <= 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-  }
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (sms <= 0) sms = 1;
   const int grid = p.tiles < sms ? p.tiles : sms;
   fn<<<grid, THREADS, Lay::SMEM, st>>>(a, b, p, err);
   return cudaGetLastError();
