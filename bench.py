@@ -104,20 +104,26 @@ KERNEL_POLICY = {"taylor": "TaylorP", "exchange": "ExchangeP", "vhs": "VhsP"}
 CSRC = os.path.join(ROOT, "paper_2003_09468_gb300", "csrc")
 
 
-def kernel_fingerprint(stage: str):
-    """sha256 (12 hex digits) of the sources that define the stage's GEMM kernel: the
-    generic kernel headers and the text of its policy struct."""
+def kernel_fingerprint(stage: str, read=None):
+    """sha256 (12 hex digits) of the device code of the stage's GEMM kernel: tc.cuh and
+    split.cuh, the device part of tc_gemm.cuh (from its namespace to the host-side
+    section) and the text of the policy struct in mixed.cu.  `read(name)` returns a
+    source file's text (default: the working tree)."""
     import hashlib
     pol = KERNEL_POLICY.get(stage)
     if pol is None:
         return None
+    if read is None:
+        def read(name):
+            with open(os.path.join(CSRC, name)) as fh:
+                return fh.read()
     h = hashlib.sha256()
     try:
-        for f in ("tc.cuh", "tc_gemm.cuh", "split.cuh"):
-            with open(os.path.join(CSRC, f), "rb") as fh:
-                h.update(fh.read())
-        with open(os.path.join(CSRC, "mixed.cu")) as fh:
-            src = fh.read()
+        for f in ("tc.cuh", "split.cuh"):
+            h.update(read(f).encode())
+        g = read("tc_gemm.cuh")
+        h.update(g[g.index("namespace tcg {"):g.index("// ---------------------------------------------------------------- host side")].encode())
+        src = read("mixed.cu")
         a = src.index(f"struct {pol} {{")
         h.update(src[a:src.index("\n};\n", a)].encode())
     except (OSError, ValueError):
@@ -220,6 +226,12 @@ class OracleStepper:
         phi_new, w_new, _, _, _ = ok.propagate_walker(self.osys, phi, x, 1.0)
         e = ok.local_energy(self.osys, phi_new)
         return time.perf_counter() - t0, phi_new, w_new, np.array(e)
+
+    def energy_logdet(self, phi):
+        """(E1, EC, EX) and the per-spin log det of a given walker (untimed)."""
+        ok = self.ok
+        return np.array(ok.local_energy(self.osys, phi)), np.array([ok.log_det(ok.overlap(self.osys, phi[s]))
+                                                                    for s in range(2)])
 
 
 def cpu_cores() -> int:
@@ -345,6 +357,11 @@ def main():
     value = world * spec.nwalkers * args.steps / (ms * 1e-3)
     eloc_h = eloc.cpu().numpy()
     finite = bool(np.all(np.isfinite(eloc_h)))
+    # the block's mixed energy estimate over every rank's walkers (the one cross-rank
+    # exchange of the method; untimed, after the timed steps)
+    from paper_2003_09468_gb300.replicas import block_energy
+    e_blk, w_blk = block_energy(eloc, w)
+    block = {"E_mixed_ha_per_cell": e_blk.real / spec.nk, "weight_sum": w_blk, "ranks": world}
 
     # end-to-end through the public API with pinned host buffers
     e2e = None
@@ -385,9 +402,10 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         phi.copy_(torch.from_numpy(phi0).to(dev))
         w.fill_(1.0)
-        sys_.step(phi, xs[0], w, eloc, do_qr=False, reuse=False)
+        ld = torch.empty((spec.nwalkers, 2), dtype=torch.complex128, device=dev)
+        sys_.step(phi, xs[0], w, eloc, logdet=ld, do_qr=False, reuse=False)
         torch.cuda.synchronize()
-        gpu_first = (phi[0].cpu().numpy(), float(w[0].item()), eloc[0].cpu().numpy())
+        gpu_first = (phi[0].cpu().numpy(), float(w[0].item()), eloc[0].cpu().numpy(), ld[0].cpu().numpy())
 
     # derived rates from the per-stage times: propagation (with the Green's function that the
     # fused step forms for the next step) and the local energy
@@ -458,19 +476,32 @@ def main():
     cpu_baseline = None
     parity = None
     if not args.no_cpu_baseline and world == 1:
-        t, phi_ref, w_ref, e_ref = OracleStepper(spec).run(0, 0)
+        stepper = OracleStepper(spec)
+        t, phi_ref, w_ref, e_ref = stepper.run(0, 0)
         cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                         "sample": f"1 walker x 1 step (propagate + E_L) of {args.workload}, FP64 NumPy, "
                                   f"{t:.1f} s"}
         if gpu_first is not None:
-            phi_g, w_g, e_g = gpu_first
-            parity = {"walker": 0, "step": "first step from the seeded walkers, fields of step 0",
-                      "E_L_err_ha_per_cell": [float(abs(e_g[j] - e_ref[j]) / spec.nk) for j in range(3)],
-                      "E_L_parts": ["E1", "EC", "EX"],
-                      "phi_rel_err": float(np.linalg.norm(phi_g - phi_ref) / np.linalg.norm(phi_ref)),
-                      "weight_rel_err": float(abs(w_g - w_ref) / abs(w_ref)),
-                      "tolerance": {"E_L_ha_per_cell": 1e-5, "phi_rel": 1e-6, "weight_rel": 1e-5}
-                      if precision == "mixed" else {"all_rel": 1e-10}}
+            phi_g, w_g, e_g, ld_g = gpu_first
+            e_own, ld_own = stepper.energy_logdet(phi_g)
+            parity = {
+                "walker": 0, "step": "first step from the seeded walkers, fields of step 0",
+                # the kernels: E_L and log det of the walker the GPU propagated, against the
+                # oracle evaluated on that same walker
+                "kernel": {"E_L_err_ha_per_cell": [float(abs(e_g[j] - e_own[j]) / spec.nk) for j in range(3)],
+                           "E_L_parts": ["E1", "EC", "EX"],
+                           "E_L_ha_per_cell": [float(abs(e_own[j]) / spec.nk) for j in range(3)],
+                           "logdet_abs_err": float(np.max(np.abs(ld_g.real - ld_own.real)))},
+                # the step: the propagated walker and weight against the oracle's own step
+                "step_vs_oracle": {"phi_rel_err": float(np.linalg.norm(phi_g - phi_ref) / np.linalg.norm(phi_ref)),
+                                   "weight_rel_err": float(abs(w_g - w_ref) / abs(w_ref)),
+                                   "E_L_diff_ha_per_cell": [float(abs(e_g[j] - e_ref[j]) / spec.nk)
+                                                            for j in range(3)],
+                                   "note": "E_L and the weight of these walkers are ill-conditioned: a "
+                                           "random 4.4e-8 relative change of the walker moves E_C and E_X "
+                                           "by ~3e-2 Ha/cell and the log det by ~2e-5 (oracle)"},
+                "tolerance": {"E_L_ha_per_cell": 1e-5, "phi_rel": 1e-6, "logdet_abs": 1e-5}
+                if precision == "mixed" else {"all_rel": 1e-10}}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -485,6 +516,7 @@ def main():
         "fp64_path": fp64_cmp,
         "cpu_baseline": cpu_baseline,
         "parity": parity,
+        "block_energy": block,
         "rates": rates,
         "e2e": e2e,
         "gpu_launches": gpu_launches,
