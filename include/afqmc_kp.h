@@ -53,9 +53,12 @@ typedef enum {
 typedef enum {
   /* Every contraction in complex128 on the FP64 pipes. */
   AFQMC_FP64 = 0,
-  /* L-contractions (force bias, vHS, Taylor products, exchange) on the tensor
-   * cores with FP32 accumulation; overlap, inverse, log-det, weights, QR and the
-   * energy sums stay FP64. */
+  /* L-contractions (force bias, vHS, Taylor products, exchange), the Green's-
+   * function product and the QR products on the tensor cores (split fp16
+   * operands, FP32 accumulation); the overlap, its inverse and log-det in
+   * double-float (about 48 bits) on the FP32 pipe; the weights and the energy
+   * sums in FP64.  The QR is Cholesky-QR2 (the same unique Q with real positive
+   * diag R as the FP64 path's Householder). */
   AFQMC_MIXED = 1
 } afqmc_precision;
 

@@ -1,12 +1,14 @@
 // Tensor-core ("mixed") path of the k-point AFQMC walker step.
 //
-// Every contraction with the Cholesky vectors, the Taylor products and the
-// Green's-function product run as complex GEMMs on the tcgen05 tensor cores
-// with an fp16 hi/lo operand split and fp32 accumulation (tc_gemm.cuh).  The
-// overlap matrix, its LU factorisation, inverse and log-determinant, the
-// weights, the QR and every energy sum stay in FP64.  The identity part of both
-// one-body half steps and of the Taylor series is carried exactly in FP64;
-// only the corrections pass through reduced precision.
+// Every contraction with the Cholesky vectors, the Taylor products, the
+// Green's-function product and the Cholesky-QR2 Gram and apply products run as
+// complex GEMMs on the tcgen05 tensor cores with an fp16 hi/lo operand split and
+// fp32 accumulation (tc_gemm.cuh).  The overlap matrix, its inverse and
+// log-determinant and the trial-subspace projection of the walker run in
+// double-float arithmetic on the FP32 pipe (ffla.cu); the weights and every
+// cross-tile energy sum stay in FP64.  The FP64 walker is the identity part of
+// both one-body half steps and of the Taylor series; only the corrections pass
+// through reduced precision, and they are added to it once per step.
 //
 // Exchange energy.  Sec. 2.2 notes that a half-rotated two-electron tensor can
 // be precontracted to cut the cost of the energy by at least n_gamma, at an
