@@ -291,6 +291,210 @@ __global__ void __launch_bounds__(GJ_THREADS)
   }
 }
 
+// Blocked form of the same Gauss-Jordan inverse, matrix in shared memory.  Pivots are taken
+// in panels of GJB columns: within a panel every step updates only the panel's columns
+// (all rows), so that afterwards those columns hold the panel's accumulated transform T
+// (T - I has non-zeros only there); every other column c then receives the panel's row
+// swaps and one rank-GJB update c <- T c = c + (T - I)[:, panel] c[panel rows].  The
+// arithmetic per element is unchanged (N^3 double-float multiply-adds in all); the
+// rank-GJB update reads and writes each element once per panel instead of once per pivot,
+// with the panel's multipliers and rows reused from registers.
+constexpr int GJB = 8;
+constexpr int GJB_MAXN = 112;   // N^2 + GJB N float4 + per-row arrays within SMEM_LIMIT
+
+__global__ void __launch_bounds__(GJ_THREADS)
+    gjb_ff_kernel(const float4* Sff, int N, zc* logdet, int* sing, int* flags, __half* out, int Np, float* s_out) {
+  extern __shared__ __align__(16) unsigned char gj_smem[];
+  __shared__ int s_p, s_sing, s_swaps;
+  __shared__ float4 s_pv, s_ajj;
+  __shared__ double s_red[GJ_WARPS];
+  __shared__ float s_redf[GJ_WARPS];
+  __shared__ int s_prow[GJB];
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float4* g = Sff + (size_t)b * N * N;
+  float4* a = reinterpret_cast<float4*>(gj_smem);        // [N][N]
+  float4* tmp = a + (size_t)N * N;                        // [GJB][N] panel rows before the update
+  float4* f = tmp + (size_t)GJB * N;                      // [N] multipliers
+  double2* piv = reinterpret_cast<double2*>(f + N);
+  int* perm = reinterpret_cast<int*>(piv + N);
+  int* iperm = perm + N;
+  for (int e = tid; e < N * N; e += GJ_THREADS) a[e] = g[e];
+  for (int i = tid; i < N; i += GJ_THREADS) perm[i] = i;
+  if (tid == 0) {
+    s_sing = 0;
+    s_swaps = 0;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < N && !s_sing; j0 += GJB) {
+    const int jb = min(GJB, N - j0);
+    // ---- panel: columns [j0, j0 + jb), every row
+    for (int jj = 0; jj < jb; ++jj) {
+      const int j = j0 + jj;
+      if (warp == 0) {
+        float best = -1.f;
+        int bi = j;
+        for (int i = j + lane; i < N; i += 32) {
+          const float4 v = a[(size_t)i * N + j];
+          const float m = fabsf(v.x) + fabsf(v.z);
+          if (m > best) {
+            best = m;
+            bi = i;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const float b2 = __shfl_xor_sync(FULL, best, o);
+          const int i2 = __shfl_xor_sync(FULL, bi, o);
+          if (b2 > best || (b2 == best && i2 < bi)) {
+            best = b2;
+            bi = i2;
+          }
+        }
+        if (lane == 0) {
+          s_p = bi;
+          s_prow[jj] = bi;
+          s_pv = a[(size_t)bi * N + j];
+          s_ajj = a[(size_t)j * N + j];
+          if (!(best > 0.f) || !isfinite(best)) {
+            s_sing = 1;
+          } else if (bi != j) {
+            const int t = perm[j];
+            perm[j] = perm[bi];
+            perm[bi] = t;
+            ++s_swaps;
+          }
+        }
+      }
+      __syncthreads();
+      if (s_sing) break;   // the same shared value for every thread after the barrier
+      const int p = s_p;
+      const float4 pv = s_pv, ajj = s_ajj;
+      const float4 inv = ffa::crecip(pv);
+      if (tid == 0) piv[j] = make_double2(ffa::to_double(ffa::re(pv)), ffa::to_double(ffa::im(pv)));
+      // swap rows j and p and scale row j, panel columns only
+      for (int cc = tid; cc < jb; cc += GJ_THREADS) {
+        const int c = j0 + cc;
+        const float4 tj = a[(size_t)j * N + c];
+        const float4 tp = (p == j) ? tj : a[(size_t)p * N + c];
+        a[(size_t)j * N + c] = (c == j) ? inv : ffa::cmul(tp, inv);
+        if (p != j) a[(size_t)p * N + c] = tj;
+      }
+      for (int i = tid; i < N; i += GJ_THREADS) {
+        if (i == j)
+          f[i] = ffa::czero();
+        else
+          f[i] = (i == p) ? ajj : a[(size_t)i * N + j];
+      }
+      __syncthreads();
+      // eliminate column j from every other row, panel columns only: one lane per row
+      for (int i = tid; i < N; i += GJ_THREADS) {
+        if (i == j) continue;
+        const float4 fi = f[i];
+        float4* ai = a + (size_t)i * N;
+        const float4* aj = a + (size_t)j * N;
+        for (int cc = 0; cc < jb; ++cc) {
+          const int c = j0 + cc;
+          if (c == j)
+            ai[c] = ffa::cneg(ffa::cmul(fi, inv));
+          else
+            ai[c] = ffa::cfms(ai[c], fi, aj[c]);
+        }
+      }
+      __syncthreads();
+    }
+    if (s_sing) break;
+    // ---- every other column: the panel's row swaps in order, a copy of the panel rows
+    const int R = N - jb;   // rest column r -> c = r < j0 ? r : r + jb
+    for (int r = tid; r < R; r += GJ_THREADS) {
+      const int c = (r < j0) ? r : r + jb;
+      for (int jj = 0; jj < jb; ++jj) {
+        const int j = j0 + jj, p = s_prow[jj];
+        if (p != j) {
+          const float4 t = a[(size_t)j * N + c];
+          a[(size_t)j * N + c] = a[(size_t)p * N + c];
+          a[(size_t)p * N + c] = t;
+        }
+      }
+      for (int jj = 0; jj < jb; ++jj) tmp[(size_t)jj * N + r] = a[(size_t)(j0 + jj) * N + c];
+    }
+    __syncthreads();
+    // ---- rank-jb update a[i][c] += sum_l (T - I)[i][j0 + l] tmp[l][c]: a warp takes two rows
+    // and 64 rest columns (lanes on consecutive columns), the multipliers are broadcast
+    {
+      const int row_pairs = (N + 1) / 2, col_blocks = (R + 63) / 64;
+      for (int u = warp; u < row_pairs * col_blocks; u += GJ_WARPS) {
+        const int i0 = 2 * (u / col_blocks), r0 = 64 * (u % col_blocks);
+        const int rA = r0 + lane, rB = r0 + lane + 32;
+        const bool okA = rA < R, okB = rB < R, ok1 = i0 + 1 < N;
+        const int cA = (rA < j0) ? rA : rA + jb, cB = (rB < j0) ? rB : rB + jb;
+        float4 x00 = okA ? a[(size_t)i0 * N + cA] : ffa::czero();
+        float4 x01 = okB ? a[(size_t)i0 * N + cB] : ffa::czero();
+        float4 x10 = (ok1 && okA) ? a[(size_t)(i0 + 1) * N + cA] : ffa::czero();
+        float4 x11 = (ok1 && okB) ? a[(size_t)(i0 + 1) * N + cB] : ffa::czero();
+        for (int l = 0; l < jb; ++l) {
+          float4 d0 = a[(size_t)i0 * N + j0 + l];
+          float4 d1 = ok1 ? a[(size_t)(i0 + 1) * N + j0 + l] : ffa::czero();
+          if (i0 == j0 + l) d0 = ffa::pack(ffa::add(ffa::re(d0), ffa::make(-1.f, 0.f)), ffa::im(d0));
+          if (i0 + 1 == j0 + l) d1 = ffa::pack(ffa::add(ffa::re(d1), ffa::make(-1.f, 0.f)), ffa::im(d1));
+          const float4 tA = okA ? tmp[(size_t)l * N + rA] : ffa::czero();
+          const float4 tB = okB ? tmp[(size_t)l * N + rB] : ffa::czero();
+          x00 = ffa::cfma(x00, d0, tA);
+          x01 = ffa::cfma(x01, d0, tB);
+          x10 = ffa::cfma(x10, d1, tA);
+          x11 = ffa::cfma(x11, d1, tB);
+        }
+        if (okA) a[(size_t)i0 * N + cA] = x00;
+        if (okB) a[(size_t)i0 * N + cB] = x01;
+        if (ok1 && okA) a[(size_t)(i0 + 1) * N + cA] = x10;
+        if (ok1 && okB) a[(size_t)(i0 + 1) * N + cB] = x11;
+      }
+    }
+    __syncthreads();
+  }
+  const int singular = s_sing;
+  double lg = 0.0, an = 0.0;
+  if (!singular)
+    for (int i = tid; i < N; i += GJ_THREADS) {
+      const double2 v = piv[i];
+      lg += 0.5 * log(v.x * v.x + v.y * v.y);
+      an += atan2(v.y, v.x);
+    }
+  lg = block_sum_d(lg, s_red);
+  an = block_sum_d(an, s_red);
+  if (tid == 0) {
+    if (singular) {
+      logdet[b] = make_double2(-INFINITY, 0.0);
+      sing[b] = 1;
+      atomicAdd(&flags[0], 1);
+    } else {
+      double ang = an + ((s_swaps & 1) ? M_PI : 0.0);
+      ang = remainder(ang, 2.0 * M_PI);
+      logdet[b] = make_double2(lg, ang);
+      sing[b] = 0;
+    }
+  }
+  const size_t ps = (size_t)N * Np;
+  __half* o = out + (size_t)b * 4 * ps;
+  if (singular) {
+    for (int e = tid; e < N * N; e += GJ_THREADS) mixed::put4f(o, ps, (size_t)(e / N) * Np + e % N, 0.f, 0.f);
+    if (tid == 0) s_out[b] = 1.f;
+    return;
+  }
+  for (int c = tid; c < N; c += GJ_THREADS) iperm[perm[c]] = c;
+  float m = 0.f;
+  for (int e = tid; e < N * N; e += GJ_THREADS) {
+    const float4 v = a[e];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.z)));
+  }
+  m = block_max_f(m, s_redf);   // its barriers also publish iperm
+  const float sc = mixed::pow2_scale((double)m);
+  if (tid == 0) s_out[b] = sc;
+  for (int e = tid; e < N * N; e += GJ_THREADS) {
+    const int i = e / N, c = e % N;
+    const float4 v = a[(size_t)c * N + iperm[i]];
+    mixed::put4f(o, ps, (size_t)i * Np + c, v.x * sc, v.z * sc);
+  }
+}
+
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   return ensure_dyn_smem(reinterpret_cast<const void*>(kernel), bytes);
@@ -325,9 +529,17 @@ cudaError_t overlap(const zc* A, const zc* phi, const zc* B, float4* Sff, float2
 
 cudaError_t invert(float4* Sff, int WS, int N, zc* logdet, int* sing, int* flags, __half* out, int Np, float* s_out,
                    cudaStream_t st) {
+  cudaError_t e;
+  if (out && N <= GJB_MAXN) {
+    const size_t bytes = ((size_t)N * N + (size_t)GJB * N) * sizeof(float4) + gj_smem_bytes(N, false);
+    if (bytes <= SMEM_LIMIT) {
+      if ((e = set_smem(gjb_ff_kernel, bytes)) != cudaSuccess) return e;
+      gjb_ff_kernel<<<WS, GJ_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
+      return cudaGetLastError();
+    }
+  }
   const bool in_smem = N <= GJ_SMEM_MAXN && gj_smem_bytes(N, true) <= SMEM_LIMIT;
   const size_t bytes = gj_smem_bytes(N, in_smem);
-  cudaError_t e;
 #define GJ_LAUNCH(S, I)                                                                              \
   do {                                                                                               \
     if ((e = set_smem(gj_ff_kernel<S, I>, bytes)) != cudaSuccess) return e;                         \
