@@ -385,19 +385,16 @@ __global__ void __launch_bounds__(GJ_THREADS)
           f[i] = (i == p) ? ajj : a[(size_t)i * N + j];
       }
       __syncthreads();
-      // eliminate column j from every other row, panel columns only: one lane per row
-      for (int i = tid; i < N; i += GJ_THREADS) {
+      // eliminate column j from every other row, panel columns only: one thread per
+      // (row, panel column)
+      for (int e = tid; e < N * jb; e += GJ_THREADS) {
+        const int i = e / jb, c = j0 + e % jb;
         if (i == j) continue;
         const float4 fi = f[i];
-        float4* ai = a + (size_t)i * N;
-        const float4* aj = a + (size_t)j * N;
-        for (int cc = 0; cc < jb; ++cc) {
-          const int c = j0 + cc;
-          if (c == j)
-            ai[c] = ffa::cneg(ffa::cmul(fi, inv));
-          else
-            ai[c] = ffa::cfms(ai[c], fi, aj[c]);
-        }
+        if (c == j)
+          a[(size_t)i * N + c] = ffa::cneg(ffa::cmul(fi, inv));
+        else
+          a[(size_t)i * N + c] = ffa::cfms(a[(size_t)i * N + c], fi, a[(size_t)j * N + c]);
       }
       __syncthreads();
     }
