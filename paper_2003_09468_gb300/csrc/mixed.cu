@@ -376,11 +376,12 @@ struct TaylorP {
 };
 
 // Exchange: rows = walker-spins, cols = (a, s) of Z_t in the padded order a*Mp + s, so the
-// matching 64 columns of Gh[(k,a),(kx+Q,s)] are one contiguous run per walker-spin; the
-// epilogue prefetches that tile into shared memory and dots each row in its own thread.
+// matching 64 columns of Gh[(k,a),(kx+Q,s)] are one contiguous run per walker-spin.  The
+// store warps dot each staged row with that run (one thread per row), reading Gh from
+// L2/HBM while the drain warps already accumulate the next tile.
 struct ExchangeP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = true;
+  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, WS, nk, nMp;
   const int* kminus;
@@ -400,32 +401,32 @@ struct ExchangeP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, t, 0}};
     return c;
   }
-  __device__ void prefetch(int t, int mt, int nt, float2* buf, int tid) const {
+  __device__ void store_tile(int t, int mt, int nt, const float2* tile, int tid, int, int) const {
+    const int ws = mt * 128 + tid, r = tid;
+    if (ws >= WS) return;
     const int4 q = tri[t];
     const int kxq = kminus[q.z * nk + minus[q.x]];  // kx + Q
-    const float2* src = g32 + (((size_t)q.y * nk + kxq) * WS + mt * 128) * nMp + nt * BN;
-    const int rows = min(128, WS - mt * 128);
-    const int pairs = min(BN, nMp - nt * BN) / 2;   // nMp is even: whole column pairs
-    for (int e = tid; e < rows * (BN / 2); e += 128) {
-      const int r = e / (BN / 2), j = e % (BN / 2);
-      if (j < pairs) tc::cp_async16(buf + r * tcg::ROWDOT_LD + 2 * j, src + (size_t)r * nMp + 2 * j);
-    }
-  }
-  __device__ void row_dot(int t, int mt, int nt, int r, const float* re, const float* im, const float2* buf) const {
-    const int ws = mt * 128 + r;
-    if (ws >= WS) return;
+    const float4* g4 = reinterpret_cast<const float4*>(
+        g32 + (((size_t)q.y * nk + kxq) * WS + ws) * nMp + nt * BN);
     // padding columns (s >= M) of Z_t are zero, so every column below n*Mp takes part
-    const float4* g4 = reinterpret_cast<const float4*>(buf + r * tcg::ROWDOT_LD);
     const int pairs = min(BN, nMp - nt * BN) / 2;
     float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
+    constexpr int U = 8;   // column pairs per batch of loads in flight
+    for (int j0 = 0; j0 < pairs; j0 += U) {
+      float4 gv[U];
 #pragma unroll
-    for (int j = 0; j < BN / 2; ++j) {
-      if (j >= pairs) break;
-      const float4 g = g4[j];
-      pr0 = fmaf(re[2 * j], g.x, fmaf(-im[2 * j], g.y, pr0));
-      pi0 = fmaf(re[2 * j], g.y, fmaf(im[2 * j], g.x, pi0));
-      pr1 = fmaf(re[2 * j + 1], g.z, fmaf(-im[2 * j + 1], g.w, pr1));
-      pi1 = fmaf(re[2 * j + 1], g.w, fmaf(im[2 * j + 1], g.z, pi1));
+      for (int u = 0; u < U; ++u)
+        if (j0 + u < pairs) gv[u] = g4[j0 + u];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u;
+        if (j >= pairs) break;
+        const float2 y0 = tile[r * tcg::STAGE_LD + 2 * j], y1 = tile[r * tcg::STAGE_LD + 2 * j + 1];
+        pr0 = fmaf(y0.x, gv[u].x, fmaf(-y0.y, gv[u].y, pr0));
+        pi0 = fmaf(y0.x, gv[u].y, fmaf(y0.y, gv[u].x, pi0));
+        pr1 = fmaf(y1.x, gv[u].z, fmaf(-y1.y, gv[u].w, pr1));
+        pi1 = fmaf(y1.x, gv[u].w, fmaf(y1.y, gv[u].z, pi1));
+      }
     }
     const float inv = 1.f / (s_g[ws] * s_z[t]);   // powers of two: exact after the sum
     xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)((pr0 + pr1) * inv), (double)((pi0 + pi1) * inv));
