@@ -279,17 +279,42 @@ struct VhsP {
     const int Q = b / nk, k = b % nk, kq = kminus[k * nk + Q];
     const size_t ps = (size_t)NM * NMp;
     bool bad = false;
-    // down the rows: consecutive threads write consecutive r of one (walker, p)
-    for (int e = tid; e < 128 * BN; e += 128) {
-      const int r = e % 128, c = e / 128;
-      const int pr = mt * 128 + r, w = nt * BN + c;
-      if (w >= W || pr >= M * M) continue;
-      const float st = V_SCALE / s_y[Q * W + w];
-      const float2 v = tile[r * tcg::STAGE_LD + c];
-      const float vr = v.x * st, vi = v.y * st;
-      bad |= !(fabsf(vr) < 60000.f && fabsf(vi) < 60000.f);
-      const int pp = pr / M, rr = pr % M;
-      put4f(v_sp + (size_t)w * 4 * ps, ps, (size_t)(k * M + pp) * NMp + kq * M + rr, vr, vi);
+    if ((M & 1) == 0) {
+      // M even: rows 2i, 2i+1 of a tile are r, r+1 of one (p, r) run and land on one
+      // 4-byte aligned pair of the output row, so each plane takes one 32-bit store
+      for (int e = tid; e < 64 * BN; e += 128) {
+        const int rp = e % 64, c = e / 64;
+        const int pr = mt * 128 + 2 * rp, w = nt * BN + c;
+        if (w >= W || pr >= M * M) continue;
+        const float st = V_SCALE / s_y[Q * W + w];
+        const float2 v0 = tile[(2 * rp) * tcg::STAGE_LD + c], v1 = tile[(2 * rp + 1) * tcg::STAGE_LD + c];
+        const float r0 = v0.x * st, i0 = v0.y * st, r1 = v1.x * st, i1 = v1.y * st;
+        bad |= !(fmaxf(fmaxf(fabsf(r0), fabsf(i0)), fmaxf(fabsf(r1), fabsf(i1))) < 60000.f);
+        const int pp = pr / M, rr = pr % M;
+        __half* base = v_sp + (size_t)w * 4 * ps + (size_t)(k * M + pp) * NMp + kq * M + rr;
+        __half h0, l0, h1, l1;
+        split_val(r0, h0, l0);
+        split_val(r1, h1, l1);
+        *reinterpret_cast<__half2*>(base) = __halves2half2(h0, h1);
+        *reinterpret_cast<__half2*>(base + ps) = __halves2half2(l0, l1);
+        split_val(i0, h0, l0);
+        split_val(i1, h1, l1);
+        *reinterpret_cast<__half2*>(base + 2 * ps) = __halves2half2(h0, h1);
+        *reinterpret_cast<__half2*>(base + 3 * ps) = __halves2half2(l0, l1);
+      }
+    } else {
+      // down the rows: consecutive threads write consecutive r of one (walker, p)
+      for (int e = tid; e < 128 * BN; e += 128) {
+        const int r = e % 128, c = e / 128;
+        const int pr = mt * 128 + r, w = nt * BN + c;
+        if (w >= W || pr >= M * M) continue;
+        const float st = V_SCALE / s_y[Q * W + w];
+        const float2 v = tile[r * tcg::STAGE_LD + c];
+        const float vr = v.x * st, vi = v.y * st;
+        bad |= !(fabsf(vr) < 60000.f && fabsf(vi) < 60000.f);
+        const int pp = pr / M, rr = pr % M;
+        put4f(v_sp + (size_t)w * 4 * ps, ps, (size_t)(k * M + pp) * NMp + kq * M + rr, vr, vi);
+      }
     }
     if (bad) atomicExch(overflow, 1);
   }
@@ -411,7 +436,7 @@ struct ExchangeP {
     // padding columns (s >= M) of Z_t are zero, so every column below n*Mp takes part
     const int pairs = min(BN, nMp - nt * BN) / 2;
     float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
-    constexpr int U = 8;   // column pairs per batch of loads in flight
+    constexpr int U = BN / 2;   // the whole row's loads in flight at once
     for (int j0 = 0; j0 < pairs; j0 += U) {
       float4 gv[U];
 #pragma unroll
