@@ -376,6 +376,37 @@ struct TaylorP {
           cb[(size_t)j * NM + i] = make_float4(dv[u].x + vr, dv[u].y + vi, pv[u].x + vr, pv[u].y + vi);
         }
       }
+    } else if ((NM & 1) == 0) {
+      // even NM: a thread takes two adjacent columns, one 16-byte load of phi' and one
+      // 32-bit store per plane
+      constexpr int U = 8;
+      const size_t ps = (size_t)R * NMp;
+      __half* tb = t_next + (size_t)b * 4 * ps;
+      const float4* pb = reinterpret_cast<const float4*>(p32 + (size_t)b * R * NM);
+      for (int e0 = tid; e0 < 128 * (BN / 2); e0 += 128 * U) {
+        float4 pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + 128 * u, j = mt * 128 + e / (BN / 2), i = nt * BN + 2 * (e % (BN / 2));
+          if (j < R && i < NM) pv[u] = pb[((size_t)j * NM + i) / 2];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + 128 * u, r = e / (BN / 2), c = 2 * (e % (BN / 2)), j = mt * 128 + r, i = nt * BN + c;
+          if (j >= R || i >= NM) continue;
+          const float2 v0 = tile[r * tcg::STAGE_LD + c], v1 = tile[r * tcg::STAGE_LD + c + 1];
+          __half h0, l0, h1, l1;
+          __half* o = tb + (size_t)j * NMp + i;
+          split_val(fmaf(pv[u].x, sc, v0.x * st), h0, l0);
+          split_val(fmaf(pv[u].z, sc, v1.x * st), h1, l1);
+          *reinterpret_cast<__half2*>(o) = __halves2half2(h0, h1);
+          *reinterpret_cast<__half2*>(o + ps) = __halves2half2(l0, l1);
+          split_val(fmaf(pv[u].y, sc, v0.y * st), h0, l0);
+          split_val(fmaf(pv[u].w, sc, v1.y * st), h1, l1);
+          *reinterpret_cast<__half2*>(o + 2 * ps) = __halves2half2(h0, h1);
+          *reinterpret_cast<__half2*>(o + 3 * ps) = __halves2half2(l0, l1);
+        }
+      }
     } else {
       constexpr int U = 8;
       const size_t ps = (size_t)R * NMp;
