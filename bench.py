@@ -500,8 +500,15 @@ def main():
                                    "note": "E_L and the weight of these walkers are ill-conditioned: a "
                                            "random 4.4e-8 relative change of the walker moves E_C and E_X "
                                            "by ~3e-2 Ha/cell and the log det by ~2e-5 (oracle)"},
-                "tolerance": {"E_L_ha_per_cell": 1e-5, "phi_rel": 1e-6, "logdet_abs": 1e-5}
+                "tolerance": {"E_L_ha_per_cell": "max(1e-5, 2e-6 |E_part|) per cell", "phi_rel": 1e-6,
+                              "logdet_abs": 1e-5}
                 if precision == "mixed" else {"all_rel": 1e-10}}
+            if precision == "mixed":
+                bars = [max(1e-5, 2e-6 * abs(e_own[j]) / spec.nk) for j in range(3)]
+                parity["kernel"]["E_L_bar_ha_per_cell"] = bars
+                parity["kernel"]["pass"] = bool(
+                    all(parity["kernel"]["E_L_err_ha_per_cell"][j] < bars[j] for j in range(3))
+                    and parity["kernel"]["logdet_abs_err"] < 1e-5)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -171,7 +171,6 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
 // layout.  B = A (A^dag A)^-1 and phi_perp = phi - B S (see green()).
 struct GreenP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
   const float* s_sinv;
@@ -211,7 +210,6 @@ struct GreenP {
 // blocks are summed in FP64 by xsum_kernel.
 struct ForceBiasP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, W, G, nk;
   const int* kminus;
@@ -257,7 +255,6 @@ __global__ void xsum_kernel(const double2* Xk, zc* X, int nk, size_t per) {
 // V[w][(k,p)][(k-Q,r)] = sum_g y[w,Q,g] L[Q,k,g,p,r]  -> split planes with a fixed scale
 struct VhsP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, W, M, nk, NM, NMp;
   const int* kminus;
@@ -330,7 +327,6 @@ struct VhsP {
 //   last step:   acc = phi' (FP64) + V u, the identity part exact.
 struct TaylorP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, R, NM, NMp;
   float inv_j;
@@ -437,7 +433,6 @@ struct TaylorP {
 // L2/HBM while the drain warps already accumulate the next tile.
 struct ExchangeP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, WS, nk, nMp;
   const int* kminus;
@@ -492,7 +487,6 @@ struct ExchangeP {
 // Gram[ws] = phi_ws^dag phi_ws from the transposed split planes (rows = columns of phi).
 struct GramP {
   static constexpr bool kConjA = true;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, N;
   const float* s_t;   // per walker
@@ -523,7 +517,6 @@ struct GramP {
 // phi[ws] <- phi[ws] R^-1 : rows r = (k,p), columns j; B = (R^-1)^T split planes.
 struct ApplyRP {
   static constexpr bool kConjA = false;
-  static constexpr bool kRowDot = false;
   int tiles, kchunks;
   int mt_n, nt_n, NM, N;
   const float* s_phi;

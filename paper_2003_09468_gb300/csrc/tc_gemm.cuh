@@ -42,23 +42,14 @@ struct Coords {
 
 // Policy P provides:
 //   static constexpr bool kConjA;     D = sum conj(A) B instead of sum A B
-//   static constexpr bool kRowDot;    epilogue form (below)
 //   int tiles;                        number of output tiles
 //   int kchunks;                      k chunks of BK per tile
 //   __device__ void tile(int t, int& b, int& mt, int& nt) const;
 //   __device__ Coords coords(int b, int mt, int nt, int kc) const;
-// and, for kRowDot == false,
 //   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int ewarp, int lane) const;
 //       the finished 128 x 64 tile in shared memory, tile[r * STAGE_LD + c] = (re, im);
 //       called by the 128 store threads (tid 0..127, ewarp 0..3) while the drain warps
 //       already accumulate the next tile
-// or, for kRowDot == true (a per-row dot product of D with a second operand tile),
-//   __device__ void prefetch(int b, int mt, int nt, float2* buf, int tid) const;
-//       issues cp.async copies of the 128 x 64 operand tile into buf[r * ROWDOT_LD + c];
-//       runs while the tile's chunks are drained
-//   __device__ void row_dot(int b, int mt, int nt, int r, const float* re, const float* im,
-//                           const float2* buf) const;
-//       row r of D in registers (re[c], im[c], c < 64) and the operand tile in buf.
 
 // ---------------------------------------------------------------- precise variant
 // The tensor-core accumulator adds each MMA's partial sum with truncation, so a
@@ -74,17 +65,13 @@ constexpr int BNP = 64;
 // Epilogue staging: the finished 128 x 64 tile as (re, im) fp32 pairs, rows padded to 65
 // entries so that row-per-thread and column-per-thread accesses both avoid bank conflicts.
 constexpr int STAGE_LD = BNP + 1;
-// Row-dot policies receive a 128 x 64 operand tile in the same buffer, rows padded to 66
-// entries: 16-byte aligned rows for cp.async, and 16-byte reads of one column pair by a
-// quarter warp (consecutive rows) fall in eight different bank groups.
-constexpr int ROWDOT_LD = BNP + 2;
 
 template <int STAGES>
 struct LayoutP {
   static constexpr int A_BYTES = NPLANE * BM * 64;
   static constexpr int B_BYTES = NPLANE * BNP * 64;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int TILE_BYTES = BM * ROWDOT_LD * 8;
+  static constexpr int TILE_BYTES = BM * STAGE_LD * 8;
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = STAGES * STAGE_BYTES + TILE_BYTES + BAR_BYTES + 1024;
   static constexpr uint32_t TMEM_COLS = 512;
@@ -246,13 +233,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = t0; t < p.tiles; t += tstep, ++ntile) {
       int b, mt, nt;
       p.tile(t, b, mt, nt);
-      if constexpr (P::kRowDot) {
-        // the previous tile's rows are all dotted: fetch this tile's operand while its
-        // chunks are drained
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (!*abort) p.prefetch(b, mt, nt, tile_buf, threadIdx.x - 64);
-        tc::cp_async_commit();
-      }
       float sre[BNP], sim[BNP];
 #pragma unroll
       for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
@@ -287,33 +267,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce[set]);
       }
-      if constexpr (P::kRowDot) {
-        tc::cp_async_wait_all();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (!*abort) p.row_dot(b, mt, nt, r, sre, sim, tile_buf);
-      } else {
-        if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");   // previous tile stored
+      if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");   // previous tile stored
 #pragma unroll
-        for (int c = 0; c < BNP; ++c) tile_buf[r * STAGE_LD + c] = make_float2(sre[c], sim[c]);
-        __threadfence_block();
-        asm volatile("bar.arrive 2, 256;" ::: "memory");
-      }
+      for (int c = 0; c < BNP; ++c) tile_buf[r * STAGE_LD + c] = make_float2(sre[c], sim[c]);
+      __threadfence_block();
+      asm volatile("bar.arrive 2, 256;" ::: "memory");
     }
-    if constexpr (!P::kRowDot) {
-      if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");
-    }
+    if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");
   } else {
     // Store warps: write each staged tile with the policy's own (coalesced) mapping.
-    if constexpr (!P::kRowDot) {
-      const int tid = threadIdx.x - 192, ew = warp - 6;
-      for (int t = t0; t < p.tiles; t += tstep) {
-        int b, mt, nt;
-        p.tile(t, b, mt, nt);
-        asm volatile("bar.sync 2, 256;" ::: "memory");
-        if (!*abort) p.store_tile(b, mt, nt, tile_buf, tid, ew, lane);
-        __threadfence_block();
-        asm volatile("bar.arrive 3, 256;" ::: "memory");
-      }
+    const int tid = threadIdx.x - 192, ew = warp - 6;
+    for (int t = t0; t < p.tiles; t += tstep) {
+      int b, mt, nt;
+      p.tile(t, b, mt, nt);
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (!*abort) p.store_tile(b, mt, nt, tile_buf, tid, ew, lane);
+      __threadfence_block();
+      asm volatile("bar.arrive 3, 256;" ::: "memory");
     }
   }
   tc::fence_before_sync();
