@@ -62,6 +62,7 @@ struct MixedState {
   float* inv_s_lh = nullptr;                             // 1 / s_lh
   zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
   float4* s_ff = nullptr;                                // [WS][N][N] double-float overlap matrices
+  double* logr = nullptr;                                // [WS] log det R of the last Cholesky-QR2
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
@@ -221,16 +222,18 @@ struct ForceBiasP {
     mt = (t / nt_n) % mt_n;
     b = t / (nt_n * mt_n);   // b = Q * nk + k
   }
+  // rows = Cholesky index g of LH[Q][k] (A), columns = walkers (B = spin-summed Gh)
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
     const int Q = b / nk, k = b % nk, c0 = kc * 32;
-    tcg::Coords c = {{c0, mt * 128, 0, kminus[k * nk + Q], k}, {c0, nt * BN, 0, k, Q}};
+    tcg::Coords c = {{c0, mt * 128, 0, k, Q}, {c0, nt * BN, 0, kminus[k * nk + Q], k}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
     const int Q = b / nk, k = b % nk;
+    // down the rows: consecutive threads write consecutive g of one walker
     for (int e = tid; e < 128 * BN; e += 128) {
-      const int r = e / BN, c = e % BN;
-      const int w = mt * 128 + r, g = nt * BN + c;
+      const int r = e % 128, c = e / 128;
+      const int g = mt * 128 + r, w = nt * BN + c;
       if (w >= W || g >= G) continue;
       const float f = inv_s_lh[Q * G + g] / s_gsum[w];
       const float2 v = tile[r * tcg::STAGE_LD + c];
@@ -832,7 +835,7 @@ __global__ void split_T_kernel(const zc* phi, const unsigned long long* mx, floa
 constexpr int CI_THREADS = 512;
 template <bool SMEM>
 __global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(float2* gram, __half* out, float* scale, int* flags,
-                                                              int N, int Np) {
+                                                              int N, int Np, double* logr) {
   extern __shared__ __align__(16) unsigned char ci_smem[];
   constexpr int NW = CI_THREADS / 32;
   __shared__ int s_fail;
@@ -874,6 +877,23 @@ __global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(float2* gram, __ha
   __syncthreads();
   const int fail = s_fail;
   if (fail && tid == 0) atomicAdd(&flags[0], 1);
+  if (logr) {
+    // log det R = sum_j log r_jj (real, r_jj > 0): the change of log det (A^dag phi)
+    // under phi <- phi R^-1; nothing on failure (the walker is kept as it is)
+    double lr = 0.0;
+    if (!fail)
+      for (int j = tid; j < N; j += CI_THREADS) lr += log((double)a[(size_t)j * N + j].x);
+    for (int o = 16; o > 0; o >>= 1) lr += __shfl_xor_sync(0xffffffffu, lr, o);
+    __shared__ double s_lr[NW];
+    if (lane == 0) s_lr[warp] = lr;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += s_lr[w];
+      logr[ws] += t;
+    }
+    __syncthreads();
+  }
   if (!fail) {
     for (int j = 0; j < N; ++j) {
       const float inv = 1.f / a[(size_t)j * N + j].x;   // r_jj is real and positive
@@ -930,6 +950,12 @@ __global__ void __launch_bounds__(CI_THREADS) chol_inv_kernel(float2* gram, __ha
       v = a[(size_t)i * N + jr];
     put4f(o, ps, (size_t)jr * Np + i, v.x * sc, v.y * sc);
   }
+}
+
+// ld[ws] -= (logr[ws], 0) for every walker-spin that is not singular
+__global__ void ld_shift_kernel(zc* ld, const double* logr, const int* sing, int WS) {
+  const int ws = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ws < WS && !sing[ws]) ld[ws].x -= logr[ws];
 }
 
 __global__ void to_f32_kernel(const zc* in, float2* out, size_t n) {
@@ -1154,6 +1180,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   const int zctas = std::min(T, ZCTAS);
   MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
   MTRY(dalloc(h, &m->s_ff, (size_t)WS * h->N * h->N, false, st));
+  MTRY(dalloc(h, &m->logr, (size_t)WS, true, st));
   MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
 
   // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
@@ -1180,9 +1207,9 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(map5(&m->m_phi, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, BN));
   MTRY(map5(&m->m_gsum, m->gsum_sp, {(uint64_t)nMp, (uint64_t)W, 4, (uint64_t)nk, (uint64_t)nk},
-            {(uint64_t)nMp, (uint64_t)nk * nk * W * nMp, (uint64_t)W * nMp, (uint64_t)nk * W * nMp}, 128));
+            {(uint64_t)nMp, (uint64_t)nk * nk * W * nMp, (uint64_t)W * nMp, (uint64_t)nk * W * nMp}, BN));
   MTRY(map5(&m->m_lh, m->lh_sp, {(uint64_t)nMp, (uint64_t)G, 4, (uint64_t)nk, (uint64_t)nk},
-            {(uint64_t)nMp, (uint64_t)nk * nk * G * nMp, (uint64_t)G * nMp, (uint64_t)nk * G * nMp}, BN));
+            {(uint64_t)nMp, (uint64_t)nk * nk * G * nMp, (uint64_t)G * nMp, (uint64_t)nk * G * nMp}, 128));
   MTRY(map5(&m->m_y, m->y_sp, {(uint64_t)Gp, (uint64_t)W, 4, (uint64_t)nk, 1},
             {(uint64_t)Gp, (uint64_t)nk * W * Gp, (uint64_t)W * Gp, (uint64_t)nk * W * Gp * 4}, BN));
   MTRY(map5(&m->m_lt, m->lt_sp, {(uint64_t)Gp, (uint64_t)M * M, 4, (uint64_t)nk, (uint64_t)nk},
@@ -1285,13 +1312,13 @@ static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStre
 static cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
   ForceBiasP p;
-  p.mt_n = cdiv(h->W, 128);
-  p.nt_n = cdiv(h->G, BN);
+  p.mt_n = cdiv(h->G, 128);
+  p.nt_n = cdiv(h->W, BN);
   p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
   p.kchunks = m->nMp / 32;
   p.W = h->W; p.G = h->G; p.nk = h->nk;
   p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.inv_s_lh = m->inv_s_lh; p.Xk = m->xk;
-  MTRY(run_gemm(m->m_gsum, m->m_lh, p, h->flags + 1, st));
+  MTRY(run_gemm(m->m_lh, m->m_gsum, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   const size_t per = (size_t)h->W * h->nk * h->G;
   xsum_kernel<<<(int)std::min<size_t>((per + 255) / 256, 4096), 256, 0, st>>>(m->xk, h->X, h->nk, per);
@@ -1393,7 +1420,7 @@ cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logd
   return cudaSuccess;
 }
 
-static cudaError_t chol_inv(afqmc_kp* h, cudaStream_t st) {
+static cudaError_t chol_inv(afqmc_kp* h, double* logr, cudaStream_t st) {
   MixedState* m = h->mixed;
   const int N = h->N;
   const size_t full = (size_t)N * N * sizeof(float2) + (size_t)N * sizeof(float2);
@@ -1402,10 +1429,10 @@ static cudaError_t chol_inv(afqmc_kp* h, cudaStream_t st) {
   float2* gram = reinterpret_cast<float2*>(h->P);
   if (in_smem) {
     MTRY(set_smem_attr((const void*)chol_inv_kernel<true>, bytes));
-    chol_inv_kernel<true><<<m->WS, CI_THREADS, bytes, st>>>(gram, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np);
+    chol_inv_kernel<true><<<m->WS, CI_THREADS, bytes, st>>>(gram, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np, logr);
   } else {
     MTRY(set_smem_attr((const void*)chol_inv_kernel<false>, bytes));
-    chol_inv_kernel<false><<<m->WS, CI_THREADS, bytes, st>>>(gram, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np);
+    chol_inv_kernel<false><<<m->WS, CI_THREADS, bytes, st>>>(gram, m->sinvt_sp, m->s_sinv, h->flags, N, m->Np, logr);
   }
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
@@ -1414,8 +1441,10 @@ static cudaError_t chol_inv(afqmc_kp* h, cudaStream_t st) {
 // Cholesky-QR2: twice { Gram = phi^dag phi on the tensor cores; R = chol(Gram) and R^-1 in
 // fp32; phi <- phi R^-1 on the tensor cores }.  R has a real positive diagonal, so
 // phi ends as the unique Q factor of the Householder QR with diag(R) > 0.
-static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
+// logr != nullptr: logr[ws] receives sum_j log R_jj over both passes (R = R2 R1).
+static cudaError_t cholqr2(afqmc_kp* h, zc* phi, double* logr, cudaStream_t st) {
   MixedState* m = h->mixed;
+  if (logr) MTRY(cudaMemsetAsync(logr, 0, sizeof(double) * m->WS, st));
   const int WS = m->WS, N = h->N, NM = h->NM, W = h->W;
   unsigned long long* mx_phi = m->mx;
   unsigned long long* mx_w = m->mx + 2 * WS + 3 * W;
@@ -1434,7 +1463,7 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
     g.N = N; g.s_t = m->s_t; g.gram = reinterpret_cast<float2*>(h->P);
     MTRY(run_gemm(m->m_t[0], m->m_t0_b, g, h->flags + 1, st));
     AFQMC_LAUNCHED(h);
-    MTRY(chol_inv(h, st));
+    MTRY(chol_inv(h, logr, st));
     maxabs_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, (size_t)NM * N, mx_phi);
     AFQMC_LAUNCHED(h);
     split_rows_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, NM, N, m->Np, mx_phi, m->s_phi, m->phi_sp);
@@ -1454,7 +1483,7 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, cudaStream_t st) {
 
 cudaError_t orthonormalise(afqmc_kp* h, zc* phi, zc* logdet, cudaStream_t st) {
   prof_begin(h, AFQMC_STAGE_QR, st);
-  cudaError_t e = cholqr2(h, phi, st);
+  cudaError_t e = cholqr2(h, phi, nullptr, st);
   if (e == cudaSuccess && logdet) e = overlap_logdet(h, phi, logdet, h->sing_new, st);
   prof_end(h, st);
   return e;
@@ -1525,8 +1554,13 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   MSTAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
   MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
   if (do_qr) {
-    MSTAGE(AFQMC_STAGE_QR, cholqr2(h, phi, st));
-    MSTAGE(AFQMC_STAGE_QR, overlap_logdet(h, phi, h->ld_new, h->sing_new, st));
+    // log det (A^dag phi R^-1) = log det (A^dag phi) - log det R, R with a real positive
+    // diagonal, so only the real part of the step's new log det changes
+    MixedState* m = h->mixed;
+    MSTAGE(AFQMC_STAGE_QR, cholqr2(h, phi, m->logr, st));
+    ld_shift_kernel<<<cdiv(m->WS, 128), 128, 0, st>>>(h->ld_new, m->logr, h->sing_new, m->WS);
+    AFQMC_LAUNCHED(h);
+    MTRY(cudaGetLastError());
     if (logdet)
       MTRY(cudaMemcpyAsync(logdet, h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, st));
   }

@@ -45,8 +45,13 @@ def test_two_steps_with_reuse_and_qr(name, prec):
                 pn = np.stack([ok.orthonormalise(pn[sp]) for sp in range(2)])
             ref_phi.append(pn)
             ref_w.append(wn)
-        e = host(sys_.step(phi, dev(x), w, do_qr=do_qr, reuse=True))
+        ld = torch.empty((spec.nwalkers, 2), dtype=torch.complex128, device="cuda")
+        e = host(sys_.step(phi, dev(x), w, logdet=ld, do_qr=do_qr, reuse=True))
         got_phi, got_w = host(phi), host(w)
+        # the returned log det belongs to the walkers as they leave the step (after the QR)
+        ref_ld = np.array([[ok.log_det(ok.overlap(osys, got_phi[i][sp])) for sp in range(2)]
+                           for i in range(spec.nwalkers)])
+        assert np.abs(host(ld).real - ref_ld.real).max() < (1e-10 if prec == "fp64" else 1e-5), s
         assert rel(got_phi, np.array(ref_phi)) < bar["phi"], s
         assert rel(got_w, np.array(ref_w)) < bar["w"], s
         ref_e = np.array([ok.local_energy(osys, got_phi[i]) for i in range(spec.nwalkers)])
