@@ -687,10 +687,31 @@ __global__ void split_y_kernel(const zc* y, const float* s_l, __half* out, float
   }
 }
 
-// First one-body half step, phi' = phi + D phi with D = exp(-dt/2 H1') - I (Sec. 3.2 step
-// 3), in the transposed (row = (spin, column), column = orbital) layout of the Taylor
-// series, as fp32 parts only: p32 = phi' (rounded) and corr.xy = D phi.  The FP64 walker
-// itself is added back once, after the series (onebody_out_kernel).  mx[w] = max |p32|.
+// Both one-body half steps apply D = exp(-dt/2 H1') - I of one k block to 64 walker
+// columns staged in shared memory (blk[q][j], j < 64, rows padded to OB_LD so that the
+// transposing fill of the second half step is free of bank conflicts).  D is staged transposed,
+// Dt[q][p], and a thread forms orbital p for the four columns jq, jq+16, jq+32, jq+48: the
+// four products share each D element from a register.
+constexpr int OB_LD = 65;
+__device__ __forceinline__ void onebody_apply4(const float2* Dt, const float2* blk, int M, int p, int jq,
+                                               float2 (&c)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) c[u] = make_float2(0.f, 0.f);
+  for (int q = 0; q < M; ++q) {
+    const float2 d = Dt[q * M + p];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 b = blk[q * OB_LD + jq + 16 * u];
+      c[u].x = fmaf(d.x, b.x, fmaf(-d.y, b.y, c[u].x));
+      c[u].y = fmaf(d.x, b.y, fmaf(d.y, b.x, c[u].y));
+    }
+  }
+}
+
+// First one-body half step, phi' = phi + D phi (Sec. 3.2 step 3), in the transposed
+// (row = (spin, column), column = orbital) layout of the Taylor series, as fp32 parts only:
+// p32 = phi' (rounded) and corr.xy = D phi.  The FP64 walker itself is added back once,
+// after the series (onebody_out_kernel).  mx[w] = max |p32|.
 // grid (k, ws, j-chunk of 64)
 __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, float4* corr, float2* p32,
                                   unsigned long long* mx, int nk, int M, int N, int NM) {
@@ -699,32 +720,39 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, float4* co
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* blk = reinterpret_cast<float2*>(smraw);          // [M][64]
-  float2* D = blk + M * 64;                                  // [M][M]
-  for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
+  float2* blk = reinterpret_cast<float2*>(smraw);          // [M][OB_LD]
+  float2* Dt = blk + M * OB_LD;                                 // [M][M], Dt[q][p] = D[p][q]
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    const int p = e / M, q = e % M;
+    Dt[q * M + p] = dhalf[(size_t)k * M * M + e];
+  }
   const zc* src = phi + (size_t)ws * NM * N;
-  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
-    const int q = e / jn, j = e % jn;
-    const zc v = src[(size_t)(k * M + q) * N + j0 + j];
-    blk[q * 64 + j] = make_float2((float)v.x, (float)v.y);
+  for (int e = threadIdx.x; e < M * 64; e += blockDim.x) {
+    const int q = e / 64, j = e % 64;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < jn) {
+      const zc x = src[(size_t)(k * M + q) * N + j0 + j];
+      v = make_float2((float)x.x, (float)x.y);
+    }
+    blk[q * OB_LD + j] = v;
   }
   __syncthreads();
   double m = 0.0;
-  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
-    const int j = e / M, p = e % M;
-    float cr = 0.f, ci = 0.f;
-    for (int q = 0; q < M; ++q) {
-      const float2 d = D[p * M + q];
-      const float2 b = blk[q * 64 + j];
-      cr = fmaf(d.x, b.x, fmaf(-d.y, b.y, cr));
-      ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
+  for (int e = threadIdx.x; e < M * 16; e += blockDim.x) {
+    const int p = e % M, jq = e / M;
+    float2 c[4];
+    onebody_apply4(Dt, blk, M, p, jq, c);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jq + 16 * u;
+      if (j >= jn) continue;
+      const size_t o = ((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p;
+      reinterpret_cast<float2*>(corr)[2 * o] = c[u];
+      const float2 b = blk[p * OB_LD + j];
+      const float2 v = make_float2(b.x + c[u].x, b.y + c[u].y);
+      p32[o] = v;
+      m = fmax(m, (double)fmaxf(fabsf(v.x), fabsf(v.y)));
     }
-    const size_t o = ((size_t)w * 2 * N + sp * N + j0 + j) * NM + k * M + p;
-    reinterpret_cast<float2*>(corr)[2 * o] = make_float2(cr, ci);
-    const float2 b = blk[p * 64 + j];
-    const float2 v = make_float2(b.x + cr, b.y + ci);
-    p32[o] = v;
-    m = fmax(m, (double)fmaxf(fabsf(v.x), fabsf(v.y)));
   }
   m = block_max(m, red);
   if (threadIdx.x == 0) atomic_max_pos(mx + w, m);
@@ -738,31 +766,38 @@ __global__ void onebody_out_kernel(const float4* corr, const float2* dhalf, zc* 
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* blk = reinterpret_cast<float2*>(smraw);          // [64][M]
-  float2* D = blk + 64 * M;                                  // [M][M]
-  for (int e = threadIdx.x; e < M * M; e += blockDim.x) D[e] = dhalf[(size_t)k * M * M + e];
+  float2* blk = reinterpret_cast<float2*>(smraw);          // [M][OB_LD]
+  float2* Dt = blk + M * OB_LD;                                 // [M][M]
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    const int p = e / M, q = e % M;
+    Dt[q * M + p] = dhalf[(size_t)k * M * M + e];
+  }
   const float4* src = corr + ((size_t)w * 2 * N + sp * N + j0) * NM + k * M;
-  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
+  for (int e = threadIdx.x; e < M * 64; e += blockDim.x) {
     const int j = e / M, q = e % M;
-    const float4 v = src[(size_t)j * NM + q];
-    blk[j * M + q] = make_float2(v.z, v.w);
+    float2 v = make_float2(0.f, 0.f);
+    if (j < jn) {
+      const float4 x = src[(size_t)j * NM + q];
+      v = make_float2(x.z, x.w);
+    }
+    blk[q * OB_LD + j] = v;
   }
   __syncthreads();
   zc* dst = phi + (size_t)ws * NM * N;
-  for (int e = threadIdx.x; e < M * jn; e += blockDim.x) {
-    const int p = e / jn, j = e % jn;
-    float cr = 0.f, ci = 0.f;
-    for (int q = 0; q < M; ++q) {
-      const float2 d = D[p * M + q];
-      const float2 b = blk[j * M + q];
-      cr = fmaf(d.x, b.x, fmaf(-d.y, b.y, cr));
-      ci = fmaf(d.x, b.y, fmaf(d.y, b.x, ci));
+  for (int e = threadIdx.x; e < M * 16; e += blockDim.x) {
+    const int p = e % M, jq = e / M;
+    float2 c[4];
+    onebody_apply4(Dt, blk, M, p, jq, c);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jq + 16 * u;
+      if (j >= jn) continue;
+      const float2 dd = reinterpret_cast<const float2*>(src)[2 * ((size_t)j * NM + p)];
+      zc v = dst[(size_t)(k * M + p) * N + j0 + j];
+      v.x += (double)(dd.x + c[u].x);
+      v.y += (double)(dd.y + c[u].y);
+      dst[(size_t)(k * M + p) * N + j0 + j] = v;
     }
-    const float2 dd = reinterpret_cast<const float2*>(src)[2 * ((size_t)j * NM + p)];
-    zc v = dst[(size_t)(k * M + p) * N + j0 + j];
-    v.x += (double)(dd.x + cr);
-    v.y += (double)(dd.y + ci);
-    dst[(size_t)(k * M + p) * N + j0 + j] = v;
   }
 }
 
@@ -1111,7 +1146,7 @@ static cudaError_t run_gemm(const CUtensorMap& a, const CUtensorMap& b, const P&
 static cudaError_t set_smem_attr(const void* fn, size_t bytes) { return ensure_dyn_smem(fn, bytes); }
 
 static size_t onebody_smem(const afqmc_kp* h) {
-  return sizeof(float2) * h->M * h->M + sizeof(float2) * h->M * 64;
+  return sizeof(float2) * h->M * h->M + sizeof(float2) * h->M * OB_LD;
 }
 
 static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
