@@ -560,15 +560,27 @@ __device__ __forceinline__ float scale_from_bits(const unsigned long long* a) {
 }
 
 // max |.| over each of nmat contiguous arrays of `per` complex doubles; grid (nmat, chunks)
+// The maximum is taken on the bit patterns of |x|: for non-negative doubles they order like
+// the values (NaN patterns sort above every finite value, as the scale wants), and
+// integer max keeps the FP64 pipe free.
 __global__ void maxabs_kernel(const zc* src, size_t per, unsigned long long* out) {
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   const size_t chunk = (per + gridDim.y - 1) / gridDim.y;
   const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
-  const zc* p = src + (size_t)blockIdx.x * per;
-  double m = 0.0;
-  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) m = fmax(m, cabs_d(p[e]));
-  m = block_max(m, red);
-  if (threadIdx.x == 0) atomic_max_pos(out + blockIdx.x, m);
+  const unsigned long long* p = reinterpret_cast<const unsigned long long*>(src + (size_t)blockIdx.x * per);
+  constexpr unsigned long long ABS = 0x7fffffffffffffffull;
+  unsigned long long m = 0;
+  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+    const unsigned long long re = p[2 * e] & ABS, im = p[2 * e + 1] & ABS;
+    m = max(m, max(re, im));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = max(m, red[i]);
+    atomicMax(out + blockIdx.x, m);
+  }
 }
 
 // src[m][rows][cols] (FP64) -> dst[m][4][rows][ldd] with the per-matrix scale; grid (nmat, chunks)
@@ -845,17 +857,29 @@ __global__ void trial_projector_kernel(const zc* A, zc* B, zc* scratch, int M, i
 // per-walker scale; grid (W, chunks)
 __global__ void split_T_kernel(const zc* phi, const unsigned long long* mx, float* scale, __half* out, int NM, int N,
                                int NMp) {
-  const int w = blockIdx.x;
+  // one 32 x 32 block (orbital rows r, columns j) of one walker-spin, transposed through
+  // shared memory so that both the FP64 reads (along j) and the fp16 writes (along r)
+  // are coalesced; grid (ceil(NM/32), ceil(N/32), 2W)
+  __shared__ float2 t[32][33];
+  const int r0 = blockIdx.x * 32, j0 = blockIdx.y * 32, w = blockIdx.z >> 1, sp = blockIdx.z & 1;
   const float s = scale_from_bits(mx + w);
-  if (blockIdx.y == 0 && threadIdx.x == 0) scale[w] = s;
-  const size_t per = (size_t)2 * NM * N, chunk = (per + gridDim.y - 1) / gridDim.y;
-  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
-  const zc* p = phi + (size_t)w * per;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && sp == 0 && threadIdx.x == 0) scale[w] = s;
+  const zc* p = phi + ((size_t)w * 2 + sp) * NM * N;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int rr = e / 32, jj = e % 32, r = r0 + rr, j = j0 + jj;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < NM && j < N) {
+      const zc x = p[(size_t)r * N + j];
+      v = make_float2((float)x.x * s, (float)x.y * s);
+    }
+    t[rr][jj] = v;
+  }
+  __syncthreads();
   const size_t ps = (size_t)2 * N * NMp;
   __half* o = out + (size_t)w * 4 * ps;
-  for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
-    const size_t sp = e / ((size_t)NM * N), r = (e / N) % NM, j = e % N;
-    put4(o, ps, (sp * N + j) * NMp + r, p[e].x, p[e].y, s);
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int jj = e / 32, rr = e % 32, r = r0 + rr, j = j0 + jj;
+    if (r < NM && j < N) put4f(o, ps, ((size_t)sp * N + j) * NMp + r, t[rr][jj].x, t[rr][jj].y);
   }
 }
 
@@ -1487,7 +1511,8 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, double* logr, cudaStream_t st) 
     MTRY(cudaMemsetAsync(m->mx, 0, sizeof(unsigned long long) * (2 * WS + 3 * W + W), st));
     maxabs_kernel<<<dim3(W, SPLIT_CHUNKS), 256, 0, st>>>(phi, (size_t)2 * NM * N, mx_w);
     AFQMC_LAUNCHED(h);
-    split_T_kernel<<<dim3(W, SPLIT_CHUNKS), 256, 0, st>>>(phi, mx_w, m->s_t, m->t_sp[0], NM, N, m->NMp);
+    split_T_kernel<<<dim3(cdiv(NM, 32), cdiv(N, 32), 2 * W), 256, 0, st>>>(phi, mx_w, m->s_t, m->t_sp[0], NM, N,
+                                                                          m->NMp);
     AFQMC_LAUNCHED(h);
     MTRY(cudaGetLastError());
     GramP g;
