@@ -106,6 +106,29 @@ __device__ __forceinline__ f2 from_double(double x) {
 }
 __device__ __forceinline__ double to_double(f2 x) { return (double)x.hi + (double)x.lo; }
 
+// Accumulator for a run of products: value = s + t, kept unnormalised between terms (t
+// collects the TwoSum and TwoProduct errors); get() renormalises once at the end.
+struct acc {
+  float s, t;
+};
+__device__ __forceinline__ acc acc_from(f2 x) { return acc{x.hi, x.lo}; }
+// a += x y
+__device__ __forceinline__ void acc_fma(acc& a, f2 x, f2 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  float s, u;
+  two_sum(a.s, p, s, u);
+  a.s = s;
+  a.t = __fadd_rn(a.t, __fadd_rn(u, e));
+}
+__device__ __forceinline__ f2 acc_get(acc a) {
+  float s, e;
+  two_sum(a.s, a.t, s, e);   // not fast_two_sum: after cancellation |t| may exceed |s|
+  return f2{s, e};
+}
+
 // ---------------------------------------------------------------- complex
 __device__ __forceinline__ f2 re(float4 v) { return f2{v.x, v.y}; }
 __device__ __forceinline__ f2 im(float4 v) { return f2{v.z, v.w}; }
@@ -126,6 +149,33 @@ __device__ __forceinline__ float4 cfms(float4 a, float4 x, float4 y) {
   const f2 i = fma(fma(im(a), neg(re(x)), im(y)), neg(im(x)), re(y));
   return pack(r, i);
 }
+// complex accumulator (re, im) and a += x y on it
+struct cacc {
+  acc r, i;
+};
+__device__ __forceinline__ cacc cacc_from(float4 v) { return cacc{acc_from(re(v)), acc_from(im(v))}; }
+__device__ __forceinline__ void cacc_fma(cacc& a, float4 x, float4 y) {
+  acc_fma(a.r, re(x), re(y));
+  acc_fma(a.r, neg(im(x)), im(y));
+  acc_fma(a.i, re(x), im(y));
+  acc_fma(a.i, im(x), re(y));
+}
+// a += conj(x) y
+__device__ __forceinline__ void cacc_fma_conj(cacc& a, float4 x, float4 y) {
+  acc_fma(a.r, re(x), re(y));
+  acc_fma(a.r, im(x), im(y));
+  acc_fma(a.i, re(x), im(y));
+  acc_fma(a.i, neg(im(x)), re(y));
+}
+// a -= x y
+__device__ __forceinline__ void cacc_fms(cacc& a, float4 x, float4 y) {
+  acc_fma(a.r, neg(re(x)), re(y));
+  acc_fma(a.r, im(x), im(y));
+  acc_fma(a.i, neg(re(x)), im(y));
+  acc_fma(a.i, neg(im(x)), re(y));
+}
+__device__ __forceinline__ float4 cacc_get(cacc a) { return pack(acc_get(a.r), acc_get(a.i)); }
+
 // a + conj(x) y
 __device__ __forceinline__ float4 cfma_conj(float4 a, float4 x, float4 y) {
   const f2 r = fma(fma(re(a), re(x), re(y)), im(x), im(y));

@@ -78,18 +78,20 @@ __global__ void __launch_bounds__(OV_THREADS)
   __syncthreads();
   for (int e = tid; e < n * jc; e += OV_THREADS) {
     const int a = e / jc, jj = e % jc;
-    float4 acc = ffa::czero();
-    for (int p = 0; p < M; ++p) acc = ffa::cfma_conj(acc, Ak[p * n + a], ph[p * JC + jj]);
-    Sk[a * JC + jj] = acc;
-    Sff[((size_t)ws * N + (size_t)k * n + a) * N + j0 + jj] = acc;
+    ffa::cacc acc = ffa::cacc_from(ffa::czero());
+    for (int p = 0; p < M; ++p) ffa::cacc_fma_conj(acc, Ak[p * n + a], ph[p * JC + jj]);
+    const float4 v = ffa::cacc_get(acc);
+    Sk[a * JC + jj] = v;
+    Sff[((size_t)ws * N + (size_t)k * n + a) * N + j0 + jj] = v;
   }
   if (!PROJECT) return;
   __syncthreads();
   float m = 0.f;
   for (int e = tid; e < M * jc; e += OV_THREADS) {
     const int p = e / jc, jj = e % jc;
-    float4 v = ph[p * JC + jj];
-    for (int a = 0; a < n; ++a) v = ffa::cfms(v, Bk[p * n + a], Sk[a * JC + jj]);
+    ffa::cacc pa = ffa::cacc_from(ph[p * JC + jj]);
+    for (int a = 0; a < n; ++a) ffa::cacc_fms(pa, Bk[p * n + a], Sk[a * JC + jj]);
+    const float4 v = ffa::cacc_get(pa);
     const float2 o = make_float2(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w));
     phi_perp[(row0 + p) * N + j0 + jj] = o;
     m = fmaxf(m, fmaxf(fabsf(o.x), fabsf(o.y)));
@@ -423,10 +425,10 @@ __global__ void __launch_bounds__(GJ_THREADS)
         const int rA = r0 + lane, rB = r0 + lane + 32;
         const bool okA = rA < R, okB = rB < R, ok1 = i0 + 1 < N;
         const int cA = (rA < j0) ? rA : rA + jb, cB = (rB < j0) ? rB : rB + jb;
-        float4 x00 = okA ? a[(size_t)i0 * N + cA] : ffa::czero();
-        float4 x01 = okB ? a[(size_t)i0 * N + cB] : ffa::czero();
-        float4 x10 = (ok1 && okA) ? a[(size_t)(i0 + 1) * N + cA] : ffa::czero();
-        float4 x11 = (ok1 && okB) ? a[(size_t)(i0 + 1) * N + cB] : ffa::czero();
+        ffa::cacc x00 = ffa::cacc_from(okA ? a[(size_t)i0 * N + cA] : ffa::czero());
+        ffa::cacc x01 = ffa::cacc_from(okB ? a[(size_t)i0 * N + cB] : ffa::czero());
+        ffa::cacc x10 = ffa::cacc_from((ok1 && okA) ? a[(size_t)(i0 + 1) * N + cA] : ffa::czero());
+        ffa::cacc x11 = ffa::cacc_from((ok1 && okB) ? a[(size_t)(i0 + 1) * N + cB] : ffa::czero());
         for (int l = 0; l < jb; ++l) {
           float4 d0 = a[(size_t)i0 * N + j0 + l];
           float4 d1 = ok1 ? a[(size_t)(i0 + 1) * N + j0 + l] : ffa::czero();
@@ -434,15 +436,15 @@ __global__ void __launch_bounds__(GJ_THREADS)
           if (i0 + 1 == j0 + l) d1 = ffa::pack(ffa::add(ffa::re(d1), ffa::make(-1.f, 0.f)), ffa::im(d1));
           const float4 tA = okA ? tmp[(size_t)l * N + rA] : ffa::czero();
           const float4 tB = okB ? tmp[(size_t)l * N + rB] : ffa::czero();
-          x00 = ffa::cfma(x00, d0, tA);
-          x01 = ffa::cfma(x01, d0, tB);
-          x10 = ffa::cfma(x10, d1, tA);
-          x11 = ffa::cfma(x11, d1, tB);
+          ffa::cacc_fma(x00, d0, tA);
+          ffa::cacc_fma(x01, d0, tB);
+          ffa::cacc_fma(x10, d1, tA);
+          ffa::cacc_fma(x11, d1, tB);
         }
-        if (okA) a[(size_t)i0 * N + cA] = x00;
-        if (okB) a[(size_t)i0 * N + cB] = x01;
-        if (ok1 && okA) a[(size_t)(i0 + 1) * N + cA] = x10;
-        if (ok1 && okB) a[(size_t)(i0 + 1) * N + cB] = x11;
+        if (okA) a[(size_t)i0 * N + cA] = ffa::cacc_get(x00);
+        if (okB) a[(size_t)i0 * N + cB] = ffa::cacc_get(x01);
+        if (ok1 && okA) a[(size_t)(i0 + 1) * N + cA] = ffa::cacc_get(x10);
+        if (ok1 && okB) a[(size_t)(i0 + 1) * N + cB] = ffa::cacc_get(x11);
       }
     }
     __syncthreads();
