@@ -63,6 +63,7 @@ struct MixedState {
   zc* zscratch = nullptr;                                // [ZCTAS][nM*nM]
   float4* s_ff = nullptr;                                // [WS][N][N] double-float overlap matrices
   double* logr = nullptr;                                // [WS] log det R of the last Cholesky-QR2
+  double2* expart = nullptr;                             // [EX_CHUNKS][WS] exchange partial sums
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
@@ -606,11 +607,32 @@ __global__ void split_rows32_kernel(const float2* src, int rows, int cols, int l
   const int mI = blockIdx.x;
   const float s = scale_from_bits(mx + mI);
   if (blockIdx.y == 0 && threadIdx.x == 0) scale[mI] = s;
-  const size_t per = (size_t)rows * cols, chunk = (per + gridDim.y - 1) / gridDim.y;
-  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
-  const float2* p = src + (size_t)mI * per;
+  const float2* p = src + (size_t)mI * rows * cols;
   const size_t ps = (size_t)rows * ldd;
   __half* o = dst + (size_t)mI * 4 * ps;
+  if ((cols & 1) == 0 && (ldd & 1) == 0) {
+    // column pairs: one 16-byte load and one 32-bit store per plane
+    const size_t per = (size_t)rows * (cols / 2), chunk = (per + gridDim.y - 1) / gridDim.y;
+    const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
+      const size_t i = e / (cols / 2), j = 2 * (e % (cols / 2));
+      const float4 v = p4[(i * cols + j) / 2];
+      __half h0, l0, h1, l1;
+      __half* q = o + i * ldd + j;
+      split_val(v.x * s, h0, l0);
+      split_val(v.z * s, h1, l1);
+      *reinterpret_cast<__half2*>(q) = __halves2half2(h0, h1);
+      *reinterpret_cast<__half2*>(q + ps) = __halves2half2(l0, l1);
+      split_val(v.y * s, h0, l0);
+      split_val(v.w * s, h1, l1);
+      *reinterpret_cast<__half2*>(q + 2 * ps) = __halves2half2(h0, h1);
+      *reinterpret_cast<__half2*>(q + 3 * ps) = __halves2half2(l0, l1);
+    }
+    return;
+  }
+  const size_t per = (size_t)rows * cols, chunk = (per + gridDim.y - 1) / gridDim.y;
+  const size_t b = blockIdx.y * chunk, e_end = min(per, b + chunk);
   for (size_t e = b + threadIdx.x; e < e_end; e += blockDim.x) {
     const size_t i = e / cols, j = e % cols;
     put4f(o, ps, i * ldd + j, p[e].x * s, p[e].y * s);
@@ -1060,16 +1082,41 @@ __global__ void e1_ec_mixed_kernel(const zc* AhH, const float2* g32, const zc* X
 }
 
 // EX[w] = -1/2 sum_t weight_t sum_nt sum_s xpart[t][nt][2w+s]
-__global__ void ex_reduce_mixed_kernel(const double2* xpart, const int4* tri, zc* eloc, int T, int nt_n, int WS) {
+// Two passes in a fixed order (deterministic): part[c][ws] = sum over the c-th chunk of the
+// (t, nt) rows of weight_t xpart[t][nt][ws], rows read whole (coalesced), four rows' loads in
+// flight at a time; then per walker EX[w] = -1/2 sum_c (part[c][2w] + part[c][2w+1]) with a
+// fixed-order tree over the chunks.
+constexpr int EX_CHUNKS = 608;
+__global__ void ex_partial_kernel(const double2* xpart, const int4* tri, double2* part, int T, int nt_n, int WS) {
+  const int rows = T * nt_n, per = (rows + gridDim.x - 1) / gridDim.x;
+  const int e0 = blockIdx.x * per, e1 = min(rows, e0 + per);
+  for (int ws = threadIdx.x; ws < WS; ws += blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int e = e0; e < e1; e += 4) {
+      double2 v[4];
+      double wt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = e + u < e1;
+        v[u] = in ? xpart[(size_t)(e + u) * WS + ws] : make_double2(0.0, 0.0);
+        wt[u] = in ? (double)tri[(e + u) / nt_n].w : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s.x += wt[u] * v[u].x;
+        s.y += wt[u] * v[u].y;
+      }
+    }
+    part[(size_t)blockIdx.x * WS + ws] = s;
+  }
+}
+__global__ void ex_reduce_mixed_kernel(const double2* part, zc* eloc, int chunks, int WS) {
   const int w = blockIdx.x;
   __shared__ zc red[32];
   zc s = zzero();
-  for (int e = threadIdx.x; e < T * nt_n; e += blockDim.x) {
-    const int t = e / nt_n;
-    const double wt = (double)tri[t].w;
-    const double2 a = xpart[(size_t)e * WS + 2 * w];
-    const double2 b = xpart[(size_t)e * WS + 2 * w + 1];
-    s = zadd(s, zmake(wt * (a.x + b.x), wt * (a.y + b.y)));
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const double2 a = part[(size_t)c * WS + 2 * w], b = part[(size_t)c * WS + 2 * w + 1];
+    s = zadd(s, zmake(a.x + b.x, a.y + b.y));
   }
   s = block_zsum(s, red);
   if (threadIdx.x == 0) eloc[3 * w + 2] = zscale(s, -0.5);
@@ -1240,6 +1287,7 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
   MTRY(dalloc(h, &m->s_ff, (size_t)WS * h->N * h->N, false, st));
   MTRY(dalloc(h, &m->logr, (size_t)WS, true, st));
+  MTRY(dalloc(h, &m->expart, (size_t)EX_CHUNKS * WS, true, st));
   MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
 
   // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
@@ -1574,7 +1622,9 @@ static cudaError_t exchange(afqmc_kp* h, cudaStream_t st) {
 
 static cudaError_t ex_reduce(afqmc_kp* h, zc* eloc, cudaStream_t st) {
   MixedState* m = h->mixed;
-  ex_reduce_mixed_kernel<<<h->W, 256, 0, st>>>(m->xpart, m->tri, eloc, m->T, cdiv(m->nMp, BN), m->WS);
+  ex_partial_kernel<<<EX_CHUNKS, 128, 0, st>>>(m->xpart, m->tri, m->expart, m->T, cdiv(m->nMp, BN), m->WS);
+  AFQMC_LAUNCHED(h);
+  ex_reduce_mixed_kernel<<<h->W, 128, 0, st>>>(m->expart, eloc, EX_CHUNKS, m->WS);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }
