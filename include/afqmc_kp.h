@@ -220,8 +220,9 @@ afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const
  * afqmc_kp_last_error -- synchronise `stream`, read and clear the handle's
  * sticky device flags.  Returns AFQMC_ERR_SINGULAR if any walker had a singular
  * overlap since the last call (their count goes to *n_singular if non-NULL),
- * AFQMC_ERR_TIMEOUT if a bounded device wait gave up, AFQMC_ERR_CUDA on an
- * asynchronous CUDA fault, else AFQMC_OK.
+ * AFQMC_ERR_TIMEOUT if a bounded device wait gave up, AFQMC_ERR_INVALID if a comb
+ * met a total weight that was not positive and finite, AFQMC_ERR_CUDA on an
+ * asynchronous CUDA fault, else AFQMC_OK (in that order of precedence).
  */
 afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular);
 
@@ -297,6 +298,81 @@ const char* afqmc_last_message(void);
  */
 #define AFQMC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 afqmc_status afqmc_orthonormalise_noalloc(void* phi, int rows, int cols, int nmat, void* stream);
+
+/*
+ * afqmc_kp_fields -- the auxiliary fields of one step drawn on the device:
+ * x[w][2][Nk][G] ~ N(0,1), independent (Sec. 2.1: x is drawn from the standard
+ * normal distribution at every step).  Uniform 32-bit words come from the
+ * counter-based generator Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC 2011) with key = seed and counter
+ * (q, w, c_lo, c_hi), q = field index / 4, c = *counter; each word pair (a, b)
+ * becomes two normals by the Box-Muller transform in fp32:
+ *   u1 = ((a >> 9) + 1/2) 2^-23, u2 = ((b >> 9) + 1/2) 2^-23 (exact in fp32, inside (0, 1)),
+ *   r = sqrt(-2 ln u1), x = (r cos 2 pi u2, r sin 2 pi u2).
+ *   seed     generator key (64 bits)
+ *   counter  device pointer to one 64-bit step counter; the call draws with *counter and
+ *            then increments it, in stream order, so a captured CUDA graph draws new
+ *            fields on every replay
+ *   x        device [W][2][Nk][G] double
+ * Allocates nothing; AFQMC_ERR_INVALID on NULL arguments.
+ */
+afqmc_status afqmc_kp_fields(afqmc_kp_t h, unsigned long long seed, unsigned long long* counter, double* x,
+                             void* stream);
+
+/*
+ * afqmc_philox4x32_10 -- the raw generator behind afqmc_kp_fields and afqmc_kp_comb:
+ * out[i] = Philox4x32-10(ctr[i], key = (seed_lo, seed_hi)) for i < n.
+ *   ctr   DEVICE uint32 [n][4] counters (c0, c1, c2, c3)
+ *   out   DEVICE uint32 [n][4] words
+ * Needs no handle; n = 0 is a no-op; AFQMC_ERR_INVALID on NULL pointers with n > 0.
+ */
+afqmc_status afqmc_philox4x32_10(const unsigned int* ctr, unsigned long long seed, unsigned int* out, size_t n,
+                                 void* stream);
+
+/*
+ * afqmc_kp_comb -- population control by the comb.  The paper leaves population
+ * control out; this is the standard comb (one uniform u per call): with cumulative
+ * weights C_j = sum_{i<=j} w_i (in walker order) and total C = C_{W-1}, new walker k
+ * is old walker j_k = min{ j : C_j > (k + u) C / W } and all new weights are C / W.
+ * u = (a + 1/2) 2^-32 with a the first Philox4x32-10 word of counter
+ * (0, 0xffffffff, c_lo, c_hi), c = *counter (the counter is not incremented; the
+ * field counter of afqmc_kp_fields never takes that form while w < 2^32 - 1).
+ * A total weight that is not positive and finite leaves everything as it is and is
+ * counted in the sticky flags (afqmc_kp_last_error returns AFQMC_ERR_INVALID).
+ *   phi     device [W][2][NM][N] complex128, in/out
+ *   weight  device [W] double, in/out
+ * Invalidates the stored Green's function, so the next afqmc_kp_step forms the
+ * overlaps of the new population afresh.  A caller that keeps per-walker log dets
+ * permutes them with the same indices: idx (device [W] int, may be NULL) receives j_k.
+ * Allocates nothing (the gather goes through the handle's adjoint workspace).
+ */
+afqmc_status afqmc_kp_comb(afqmc_kp_t h, void* phi, double* weight, unsigned long long seed,
+                           const unsigned long long* counter, int* idx, void* stream);
+
+/*
+ * afqmc_kp_block -- one block of the driver (Sec. 3.1: many steps, the walkers
+ * re-orthonormalised every few steps, the energy measured along the way),
+ * fully on the device: for s = 0 .. nsteps-1
+ *   afqmc_kp_fields(seed, counter, x); afqmc_kp_step(phi, x, weight, eloc_hist[s],
+ *   do_qr = ((s + 1) % qr_period == 0 or s == nsteps - 1));
+ * then, when comb != 0, afqmc_kp_comb(phi, weight, seed, counter, idx).  The result
+ * is bitwise that of the same calls made one by one.  Nothing synchronises with
+ * the host, so the whole block can be captured in one CUDA graph and replayed
+ * (the counter advances by nsteps per replay, so every replay draws new fields).
+ *   phi, weight    in/out, as for afqmc_kp_step
+ *   x              DEVICE double [W][2][Nk][G] scratch: the fields of the last step
+ *   eloc_hist      DEVICE c128 [nsteps][W][3]: (E1, EC, EX) after step s
+ *   weight_hist    DEVICE double [nsteps][W]: the weights after step s, or NULL
+ *   logdet         DEVICE c128 [W][2]: log dets after the last step, or NULL
+ *   nsteps >= 1, qr_period >= 1
+ *   flags          0 or AFQMC_STEP_REUSE_GREEN (applies to the first step only)
+ *   comb           0 or 1; idx as for afqmc_kp_comb (NULL allowed)
+ * AFQMC_ERR_INVALID on NULL required pointers or counts out of range.
+ */
+afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, void* eloc_hist,
+                            double* weight_hist, void* logdet, int nsteps, int qr_period, int flags,
+                            int comb, unsigned long long seed, unsigned long long* counter, int* idx,
+                            void* stream);
 
 /* Static, NUL-terminated description of a status code. */
 const char* afqmc_status_string(afqmc_status s);

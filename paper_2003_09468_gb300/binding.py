@@ -41,6 +41,10 @@ SIGNATURES = {
     "afqmc_status_string": [_I],
     "afqmc_last_message": [],
     "afqmc_orthonormalise_noalloc": [_VP, _I, _I, _I, _VP],
+    "afqmc_philox4x32_10": [_VP, ctypes.c_ulonglong, _VP, ctypes.c_size_t, _VP],
+    "afqmc_kp_fields": [_VP, ctypes.c_ulonglong, _VP, _VP, _VP],
+    "afqmc_kp_comb": [_VP, _VP, _VP, ctypes.c_ulonglong, _VP, _VP, _VP],
+    "afqmc_kp_block": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, ctypes.c_ulonglong, _VP, _VP, _VP],
 }
 
 
@@ -213,6 +217,41 @@ class KPointAFQMC:
             "afqmc_kp_local_energy_backward")
         return gphi, gh1
 
+    def fields(self, counter: torch.Tensor, seed: int, x: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Standard normal fields x[W][2][Nk][G] from Philox4x32-10 at (seed, counter); advances the counter."""
+        if x is None:
+            x = torch.empty(self.field_shape, dtype=torch.float64, device=counter.device)
+        _check(self.lib.afqmc_kp_fields(self.handle, int(seed) & (2**64 - 1),
+                                        _ptr(counter, torch.int64, (1,), "counter"),
+                                        _ptr(x, torch.float64, self.field_shape, "x"), _stream(stream)),
+               "afqmc_kp_fields")
+        return x
+
+    def comb(self, phi, weight, counter: torch.Tensor, seed: int, idx: Optional[torch.Tensor] = None, stream=None):
+        """Comb population control in place on (phi, weight); returns the selected old walker per slot."""
+        if idx is None:
+            idx = torch.empty((self.W,), dtype=torch.int32, device=phi.device)
+        _check(self.lib.afqmc_kp_comb(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                      _ptr(weight, torch.float64, (self.W,), "weight"), int(seed) & (2**64 - 1),
+                                      _ptr(counter, torch.int64, (1,), "counter"),
+                                      _ptr(idx, torch.int32, (self.W,), "idx"), _stream(stream)), "afqmc_kp_comb")
+        return idx
+
+    def block(self, phi, weight, x, eloc_hist, counter: torch.Tensor, seed: int, qr_period: int = 5,
+              weight_hist=None, logdet=None, comb=True, reuse=False, idx=None, stream=None):
+        """nsteps = len(eloc_hist) device-driven steps, then the comb (afqmc_kp_block)."""
+        nsteps = int(eloc_hist.shape[0])
+        eh = _ptr(eloc_hist, torch.complex128, (nsteps, self.W, 3), "eloc_hist")
+        wh = 0 if weight_hist is None else _ptr(weight_hist, torch.float64, (nsteps, self.W), "weight_hist")
+        lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
+        ip = 0 if idx is None else _ptr(idx, torch.int32, (self.W,), "idx")
+        _check(self.lib.afqmc_kp_block(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
+                                       _ptr(weight, torch.float64, (self.W,), "weight"),
+                                       _ptr(x, torch.float64, self.field_shape, "x"), eh, wh, lp, nsteps,
+                                       int(qr_period), 1 if reuse else 0, 1 if comb else 0,
+                                       int(seed) & (2**64 - 1), _ptr(counter, torch.int64, (1,), "counter"), ip,
+                                       _stream(stream)), "afqmc_kp_block")
+
     def last_error(self, stream=None) -> Tuple[int, int]:
         n = ctypes.c_int(0)
         s = self.lib.afqmc_kp_last_error(self.handle, _stream(stream), ctypes.byref(n))
@@ -239,6 +278,16 @@ class KPointAFQMC:
         n = ctypes.c_int(0)
         _check(self.lib.afqmc_kp_launch_count(self.handle, ctypes.byref(n)), "afqmc_kp_launch_count")
         return n.value
+
+
+def philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Raw Philox4x32-10 words of device counters ctr[n][4] (int32 storage of uint32 values)."""
+    lib = load_library()
+    n = int(ctr.shape[0])
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    _check(lib.afqmc_philox4x32_10(_ptr(ctr, torch.int32, (n, 4), "ctr"), int(seed) & (2**64 - 1),
+                                   out.data_ptr(), n, _stream(stream)), "afqmc_philox4x32_10")
+    return out
 
 
 class LocalEnergy(torch.autograd.Function):

@@ -9,6 +9,7 @@
 
 #include "handle.hpp"
 #include "mixed.hpp"
+#include "rng.hpp"
 
 namespace {
 
@@ -333,6 +334,7 @@ afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular) {
   if (n_singular) *n_singular = f[0];
   if (f[1]) return AFQMC_ERR_TIMEOUT;
   if (f[0]) return AFQMC_ERR_SINGULAR;
+  if (f[2]) return AFQMC_ERR_INVALID;
   return AFQMC_OK;
 }
 
@@ -363,6 +365,69 @@ afqmc_status afqmc_kp_stage_times(afqmc_kp_t h, double* ms, int* count) {
     h->event_pool.push_back(r.b);
   }
   h->recs.clear();
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_philox4x32_10(const unsigned int* ctr, unsigned long long seed, unsigned int* out, size_t n,
+                                 void* stream) {
+  if (n > 0 && (!ctr || !out)) return AFQMC_ERR_INVALID;
+  return from_cuda(rng::philox(ctr, seed, out, n, as_stream(stream)));
+}
+
+afqmc_status afqmc_kp_fields(afqmc_kp_t h, unsigned long long seed, unsigned long long* counter, double* x,
+                             void* stream) {
+  if (!h || !counter || !x) return AFQMC_ERR_INVALID;
+  h->launches = 0;
+  return from_cuda(rng::fields(h, seed, counter, x, as_stream(stream)));
+}
+
+afqmc_status afqmc_kp_comb(afqmc_kp_t h, void* phi, double* weight, unsigned long long seed,
+                           const unsigned long long* counter, int* idx, void* stream) {
+  if (!h || !phi || !weight || !counter) return AFQMC_ERR_INVALID;
+  if (rng::comb_smem_bytes(h->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
+  h->launches = 0;
+  h->green_valid = false;
+  return from_cuda(rng::comb(h, static_cast<zc*>(phi), weight, seed, counter, idx, as_stream(stream)));
+}
+
+afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, void* eloc_hist,
+                            double* weight_hist, void* logdet, int nsteps, int qr_period, int flags,
+                            int comb, unsigned long long seed, unsigned long long* counter, int* idx,
+                            void* stream) {
+  if (!h || !phi || !weight || !x || !eloc_hist || !counter || nsteps < 1 || qr_period < 1 ||
+      (flags & ~AFQMC_STEP_REUSE_GREEN) || (comb != 0 && comb != 1))
+    return AFQMC_ERR_INVALID;
+  if (comb && rng::comb_smem_bytes(h->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
+  h->launches = 0;
+  cudaStream_t st = as_stream(stream);
+  int reuse = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi;
+  h->green_valid = false;
+  zc* ph = static_cast<zc*>(phi);
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e = rng::fields(h, seed, counter, x, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    const int do_qr = ((s + 1) % qr_period == 0) || s == nsteps - 1;
+    zc* el = static_cast<zc*>(eloc_hist) + (size_t)s * h->W * 3;
+    zc* ld = s == nsteps - 1 ? static_cast<zc*>(logdet) : nullptr;
+    if (h->mixed)
+      e = mixed::step(h, ph, x, weight, el, ld, do_qr, reuse, st);
+    else
+      e = fp64::step(h, ph, x, weight, el, ld, do_qr, reuse, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (weight_hist) {
+      e = cudaMemcpyAsync(weight_hist + (size_t)s * h->W, weight, sizeof(double) * h->W, cudaMemcpyDeviceToDevice,
+                          st);
+      if (e != cudaSuccess) return from_cuda(e);
+    }
+    reuse = 1;
+  }
+  h->green_valid = true;
+  h->green_phi = phi;
+  if (comb) {
+    h->green_valid = false;
+    cudaError_t e = rng::comb(h, ph, weight, seed, counter, idx, st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
   return AFQMC_OK;
 }
 
