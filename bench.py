@@ -35,6 +35,8 @@ import gen  # noqa: E402
 METRIC = "walker-steps/s (propagate+E_L)"
 UNIT = "walker-steps/s"
 QR_PERIOD = 5
+PAPER_BLOCK_STEPS = 20      # a block: 20 propagation steps, one energy, one orthogonalisation (Sec. 3.1)
+BLOCK_SEED = 0x2003094680000001
 WORKLOADS = {
     "diamond-3x3x3": gen.DIAMOND_3x3x3,
     "small-2x2x2": gen.SMALL_2x2x2,
@@ -273,6 +275,7 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="diamond-3x3x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-block", action="store_true", help="skip the graph-captured paper block")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
@@ -390,6 +393,50 @@ def main():
         e2e = {"value": world * spec.nwalkers * args.steps / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(xs[0].numel() * 8),
                "d2h_bytes_per_step": int(e_host.numel() * 16 + w_host.numel() * 8)}
+
+    # the paper's block (20 propagation steps, then one energy evaluation and one walker
+    # orthogonalisation, Sec. 3.1), fields drawn on the device and the comb at the end, all in
+    # one captured CUDA graph; reported beside the step metric, untimed by the step clock
+    paper_block = None
+    if not args.no_block:
+        nb = PAPER_BLOCK_STEPS
+        xb = torch.empty_like(xs[0])
+        ehb = torch.empty((1, spec.nwalkers, 3), dtype=torch.complex128, device=dev)
+        counter = torch.tensor([1 << 20], dtype=torch.int64, device=dev)
+        phi.copy_(torch.from_numpy(phi0).to(dev))
+        w.fill_(1.0)
+
+        def blk():
+            sys_.block(phi, w, xb, ehb, counter, BLOCK_SEED + rank, nsteps=nb, qr_period=nb, energy_period=nb,
+                       comb=True)
+
+        blk()                      # eager: one-time kernel attributes, and the launch count
+        blk_launches = sys_.launch_count()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            blk()
+        g.replay()
+        torch.cuda.synchronize()
+        reps = 3
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms_blk = b0.elapsed_time(b1) / reps
+        if world > 1:
+            t = torch.tensor([ms_blk], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_blk = float(t.item())
+        eb = ehb[0].cpu().numpy()
+        paper_block = {"ms_per_block": ms_blk, "walker_steps_per_s": world * spec.nwalkers * nb / (ms_blk * 1e-3),
+                       "unit": UNIT, "steps_per_block": nb, "energy_evaluations": 1, "qr": 1, "comb": True,
+                       "fields": "Philox4x32-10 + Box-Muller on the device", "cuda_graph": True,
+                       "replays_timed": reps, "gpu_launches_per_block": blk_launches,
+                       "finite": bool(np.all(np.isfinite(eb)))}
+        del g
 
     if rank != 0:
         if world > 1:
@@ -525,6 +572,7 @@ def main():
         "parity": parity,
         "block_energy": block,
         "rates": rates,
+        "paper_block": paper_block,
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clk,

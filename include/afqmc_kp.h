@@ -165,7 +165,9 @@ afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double
  * step's force bias.
  *   phi, x, weight, logdet, do_qr   as for afqmc_kp_propagate.
  *   eloc   DEVICE c128 [W][3] output: (E1, EC, EX) of the propagated walkers
- *          (a QR does not change them).
+ *          (a QR does not change them), or NULL for a propagation-only step: the
+ *          Green's function of the new walkers is still formed (it gives their
+ *          log det and the next force bias), the energy kernels are skipped.
  *   flags  0 or AFQMC_STEP_REUSE_GREEN.  With the flag, the caller promises
  *          that phi is the output of the previous afqmc_kp_step call on this
  *          handle and was not modified since; the stored Green's function,
@@ -350,28 +352,33 @@ afqmc_status afqmc_kp_comb(afqmc_kp_t h, void* phi, double* weight, unsigned lon
                            const unsigned long long* counter, int* idx, void* stream);
 
 /*
- * afqmc_kp_block -- one block of the driver (Sec. 3.1: many steps, the walkers
- * re-orthonormalised every few steps, the energy measured along the way),
- * fully on the device: for s = 0 .. nsteps-1
- *   afqmc_kp_fields(seed, counter, x); afqmc_kp_step(phi, x, weight, eloc_hist[s],
- *   do_qr = ((s + 1) % qr_period == 0 or s == nsteps - 1));
+ * afqmc_kp_block -- one block of the driver, fully on the device.  The paper's
+ * block is 20 propagation steps followed by one energy evaluation and one walker
+ * orthogonalisation (Sec. 3.1, Fig. timing); the hybrid weight needs no energy
+ * in between.  Here, for s = 0 .. nsteps-1:
+ *   afqmc_kp_fields(seed, counter, x);
+ *   one hybrid step (afqmc_kp_step) of every walker, with
+ *     do_qr  = ((s + 1) % qr_period == 0 or s == nsteps - 1),
+ *     energy = ((s + 1) % energy_period == 0 or s == nsteps - 1), written to
+ *              eloc_hist[m], m = s / energy_period (the steps without it skip the
+ *              energy kernels: a propagation-only step);
  * then, when comb != 0, afqmc_kp_comb(phi, weight, seed, counter, idx).  The result
  * is bitwise that of the same calls made one by one.  Nothing synchronises with
  * the host, so the whole block can be captured in one CUDA graph and replayed
  * (the counter advances by nsteps per replay, so every replay draws new fields).
  *   phi, weight    in/out, as for afqmc_kp_step
  *   x              DEVICE double [W][2][Nk][G] scratch: the fields of the last step
- *   eloc_hist      DEVICE c128 [nsteps][W][3]: (E1, EC, EX) after step s
+ *   eloc_hist      DEVICE c128 [ceil(nsteps / energy_period)][W][3]: (E1, EC, EX)
  *   weight_hist    DEVICE double [nsteps][W]: the weights after step s, or NULL
  *   logdet         DEVICE c128 [W][2]: log dets after the last step, or NULL
- *   nsteps >= 1, qr_period >= 1
+ *   nsteps, qr_period, energy_period >= 1 (the paper's block: 20, 20, 20)
  *   flags          0 or AFQMC_STEP_REUSE_GREEN (applies to the first step only)
  *   comb           0 or 1; idx as for afqmc_kp_comb (NULL allowed)
  * AFQMC_ERR_INVALID on NULL required pointers or counts out of range.
  */
 afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, void* eloc_hist,
-                            double* weight_hist, void* logdet, int nsteps, int qr_period, int flags,
-                            int comb, unsigned long long seed, unsigned long long* counter, int* idx,
+                            double* weight_hist, void* logdet, int nsteps, int qr_period, int energy_period,
+                            int flags, int comb, unsigned long long seed, unsigned long long* counter, int* idx,
                             void* stream);
 
 /* Static, NUL-terminated description of a status code. */

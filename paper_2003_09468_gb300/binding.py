@@ -44,7 +44,7 @@ SIGNATURES = {
     "afqmc_philox4x32_10": [_VP, ctypes.c_ulonglong, _VP, ctypes.c_size_t, _VP],
     "afqmc_kp_fields": [_VP, ctypes.c_ulonglong, _VP, _VP, _VP],
     "afqmc_kp_comb": [_VP, _VP, _VP, ctypes.c_ulonglong, _VP, _VP, _VP],
-    "afqmc_kp_block": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, ctypes.c_ulonglong, _VP, _VP, _VP],
+    "afqmc_kp_block": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, ctypes.c_ulonglong, _VP, _VP, _VP],
 }
 
 
@@ -181,17 +181,19 @@ class KPointAFQMC:
                                            _ptr(weight, torch.float64, (self.W,), "weight"), lp,
                                            1 if do_qr else 0, _stream(stream)), "afqmc_kp_propagate")
 
-    def step(self, phi, x, weight, eloc=None, logdet=None, do_qr=False, reuse=True, stream=None) -> torch.Tensor:
-        """Propagate every walker one step and return the local energy of the new walkers."""
-        if eloc is None:
+    def step(self, phi, x, weight, eloc=None, logdet=None, do_qr=False, reuse=True, energy=True,
+             stream=None) -> Optional[torch.Tensor]:
+        """Propagate every walker one step and return the local energy of the new walkers
+        (energy=False: a propagation-only step, returns None)."""
+        if eloc is None and energy:
             eloc = torch.empty((self.W, 3), dtype=torch.complex128, device=phi.device)
+        ep = _ptr(eloc, torch.complex128, (self.W, 3), "eloc") if energy else 0
         lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
         _check(self.lib.afqmc_kp_step(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
                                       _ptr(x, torch.float64, self.field_shape, "x"),
-                                      _ptr(weight, torch.float64, (self.W,), "weight"),
-                                      _ptr(eloc, torch.complex128, (self.W, 3), "eloc"), lp,
+                                      _ptr(weight, torch.float64, (self.W,), "weight"), ep, lp,
                                       1 if do_qr else 0, 1 if reuse else 0, _stream(stream)), "afqmc_kp_step")
-        return eloc
+        return eloc if energy else None
 
     def orthonormalise(self, phi, logdet=None, stream=None):
         lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
@@ -237,18 +239,24 @@ class KPointAFQMC:
                                       _ptr(idx, torch.int32, (self.W,), "idx"), _stream(stream)), "afqmc_kp_comb")
         return idx
 
-    def block(self, phi, weight, x, eloc_hist, counter: torch.Tensor, seed: int, qr_period: int = 5,
-              weight_hist=None, logdet=None, comb=True, reuse=False, idx=None, stream=None):
-        """nsteps = len(eloc_hist) device-driven steps, then the comb (afqmc_kp_block)."""
-        nsteps = int(eloc_hist.shape[0])
-        eh = _ptr(eloc_hist, torch.complex128, (nsteps, self.W, 3), "eloc_hist")
+    def block(self, phi, weight, x, eloc_hist, counter: torch.Tensor, seed: int, nsteps: Optional[int] = None,
+              qr_period: int = 5, energy_period: int = 1, weight_hist=None, logdet=None, comb=True, reuse=False,
+              idx=None, stream=None):
+        """One device-driven block (afqmc_kp_block): nsteps steps (default: one per eloc_hist row times
+        energy_period), energy every energy_period steps and after the last, then the comb."""
+        nmeas = int(eloc_hist.shape[0])
+        if nsteps is None:
+            nsteps = nmeas * int(energy_period)
+        if nmeas != -(-int(nsteps) // int(energy_period)):
+            raise ValueError("eloc_hist needs ceil(nsteps / energy_period) rows")
+        eh = _ptr(eloc_hist, torch.complex128, (nmeas, self.W, 3), "eloc_hist")
         wh = 0 if weight_hist is None else _ptr(weight_hist, torch.float64, (nsteps, self.W), "weight_hist")
         lp = 0 if logdet is None else _ptr(logdet, torch.complex128, (self.W, 2), "logdet")
         ip = 0 if idx is None else _ptr(idx, torch.int32, (self.W,), "idx")
         _check(self.lib.afqmc_kp_block(self.handle, _ptr(phi, torch.complex128, self.phi_shape, "phi"),
                                        _ptr(weight, torch.float64, (self.W,), "weight"),
-                                       _ptr(x, torch.float64, self.field_shape, "x"), eh, wh, lp, nsteps,
-                                       int(qr_period), 1 if reuse else 0, 1 if comb else 0,
+                                       _ptr(x, torch.float64, self.field_shape, "x"), eh, wh, lp, int(nsteps),
+                                       int(qr_period), int(energy_period), 1 if reuse else 0, 1 if comb else 0,
                                        int(seed) & (2**64 - 1), _ptr(counter, torch.int64, (1,), "counter"), ip,
                                        _stream(stream)), "afqmc_kp_block")
 

@@ -259,7 +259,7 @@ afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double
 
 afqmc_status afqmc_kp_step(afqmc_kp_t h, void* phi, const double* x, double* weight, void* eloc, void* logdet,
                            int do_qr, int flags, void* stream) {
-  if (!h || !phi || !x || !weight || !eloc || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
+  if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
     return AFQMC_ERR_INVALID;
   h->launches = 0;
   const int reuse = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi;
@@ -391,10 +391,10 @@ afqmc_status afqmc_kp_comb(afqmc_kp_t h, void* phi, double* weight, unsigned lon
 }
 
 afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, void* eloc_hist,
-                            double* weight_hist, void* logdet, int nsteps, int qr_period, int flags,
-                            int comb, unsigned long long seed, unsigned long long* counter, int* idx,
+                            double* weight_hist, void* logdet, int nsteps, int qr_period, int energy_period,
+                            int flags, int comb, unsigned long long seed, unsigned long long* counter, int* idx,
                             void* stream) {
-  if (!h || !phi || !weight || !x || !eloc_hist || !counter || nsteps < 1 || qr_period < 1 ||
+  if (!h || !phi || !weight || !x || !eloc_hist || !counter || nsteps < 1 || qr_period < 1 || energy_period < 1 ||
       (flags & ~AFQMC_STEP_REUSE_GREEN) || (comb != 0 && comb != 1))
     return AFQMC_ERR_INVALID;
   if (comb && rng::comb_smem_bytes(h->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
@@ -407,7 +407,8 @@ afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, 
     cudaError_t e = rng::fields(h, seed, counter, x, st);
     if (e != cudaSuccess) return from_cuda(e);
     const int do_qr = ((s + 1) % qr_period == 0) || s == nsteps - 1;
-    zc* el = static_cast<zc*>(eloc_hist) + (size_t)s * h->W * 3;
+    const int measure = ((s + 1) % energy_period == 0) || s == nsteps - 1;
+    zc* el = measure ? static_cast<zc*>(eloc_hist) + (size_t)(s / energy_period) * h->W * 3 : nullptr;
     zc* ld = s == nsteps - 1 ? static_cast<zc*>(logdet) : nullptr;
     if (h->mixed)
       e = mixed::step(h, ph, x, weight, el, ld, do_qr, reuse, st);

@@ -937,9 +937,11 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   STAGE(AFQMC_STAGE_GREEN, green_impl(h, phi, h->ld_new, h->sing_new, st));
   STAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
   STAGE(AFQMC_STAGE_WEIGHT, weight_only(h, x, w, do_qr ? nullptr : logdet, st));
-  STAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
-  STAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
-  STAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  if (eloc) {   // NULL: a propagation-only step of a block (the energy is measured less often)
+    STAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
+    STAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
+    STAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  }
   if (do_qr) {
     // the Green's function is invariant under phi -> phi R^-1; only the log det moves
     STAGE(AFQMC_STAGE_QR, qr(h, phi, st));

@@ -1670,9 +1670,11 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_new, h->sing_new, st));
   MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
   MSTAGE(AFQMC_STAGE_WEIGHT, fp64::weight_only(h, x, w, do_qr ? nullptr : logdet, st));
-  MSTAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
-  MSTAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
-  MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  if (eloc) {   // NULL: a propagation-only step of a block (the energy is measured less often)
+    MSTAGE(AFQMC_STAGE_ENERGY, e1_ec(h, eloc, st));
+    MSTAGE(AFQMC_STAGE_EXCHANGE, exchange(h, st));
+    MSTAGE(AFQMC_STAGE_ENERGY, ex_reduce(h, eloc, st));
+  }
   if (do_qr) {
     // log det (A^dag phi R^-1) = log det (A^dag phi) - log det R, R with a real positive
     // diagonal, so only the real part of the step's new log det changes

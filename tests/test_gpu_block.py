@@ -117,13 +117,14 @@ def test_comb_rejects_unusable_total(bad):
     assert err[0] == 1                        # AFQMC_ERR_INVALID from the sticky flags
 
 
-def run_block(precision, how, nsteps=4, qr_period=2, blocks=2):
+def run_block(precision, how, nsteps=4, qr_period=2, blocks=2, energy_period=1):
     """Final (phi, weight, eloc history, weight history, counter) of `blocks` blocks."""
+    nmeas = -(-nsteps // energy_period)
     sys_, _ = make(SPEC, precision)
     phi = dev(gen.walkers(SPEC))
     w = torch.ones(SPEC.nwalkers, dtype=torch.float64, device="cuda")
     x = torch.empty(sys_.field_shape, dtype=torch.float64, device="cuda")
-    eh = torch.zeros((nsteps, SPEC.nwalkers, 3), dtype=torch.complex128, device="cuda")
+    eh = torch.zeros((nmeas, SPEC.nwalkers, 3), dtype=torch.complex128, device="cuda")
     wh = torch.zeros((nsteps, SPEC.nwalkers), dtype=torch.float64, device="cuda")
     counter = torch.tensor([100], dtype=torch.int64, device="cuda")
     hist = []
@@ -131,24 +132,28 @@ def run_block(precision, how, nsteps=4, qr_period=2, blocks=2):
         for _ in range(blocks):
             for s in range(nsteps):
                 sys_.fields(counter, SEED, x)
-                sys_.step(phi, x, w, eh[s], do_qr=((s + 1) % qr_period == 0 or s == nsteps - 1), reuse=s > 0)
+                measure = (s + 1) % energy_period == 0 or s == nsteps - 1
+                sys_.step(phi, x, w, eh[s // energy_period] if measure else None,
+                          do_qr=((s + 1) % qr_period == 0 or s == nsteps - 1), reuse=s > 0, energy=measure)
                 wh[s].copy_(w)
             sys_.comb(phi, w, counter, SEED)
             hist.append((host(eh).copy(), host(wh).copy()))
     elif how == "block":
         for _ in range(blocks):
-            sys_.block(phi, w, x, eh, counter, SEED, qr_period=qr_period, weight_hist=wh)
+            sys_.block(phi, w, x, eh, counter, SEED, nsteps=nsteps, qr_period=qr_period,
+                       energy_period=energy_period, weight_hist=wh)
             hist.append((host(eh).copy(), host(wh).copy()))
     else:
         # one eager block on a throwaway handle sets the kernels' one-time attributes first
         warm, _ = make(SPEC, precision)
         warm.block(phi.clone(), w.clone(), torch.empty_like(x), torch.empty_like(eh), counter.clone(), SEED,
-                   qr_period=qr_period)
+                   nsteps=nsteps, qr_period=qr_period, energy_period=energy_period)
         torch.cuda.synchronize()
         warm.close()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            sys_.block(phi, w, x, eh, counter, SEED, qr_period=qr_period, weight_hist=wh)
+            sys_.block(phi, w, x, eh, counter, SEED, nsteps=nsteps, qr_period=qr_period,
+                       energy_period=energy_period, weight_hist=wh)
         for _ in range(blocks):
             g.replay()
             hist.append((host(eh).copy(), host(wh).copy()))
@@ -157,11 +162,11 @@ def run_block(precision, how, nsteps=4, qr_period=2, blocks=2):
     return out
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_block_equals_calls_and_graph_replay(precision):
-    calls = run_block(precision, "calls")
-    block = run_block(precision, "block")
-    graph = run_block(precision, "graph")
+@pytest.mark.parametrize("precision,energy_period", [("mixed", 1), ("fp64", 1), ("mixed", 3)])
+def test_block_equals_calls_and_graph_replay(precision, energy_period):
+    calls = run_block(precision, "calls", energy_period=energy_period)
+    block = run_block(precision, "block", energy_period=energy_period)
+    graph = run_block(precision, "graph", energy_period=energy_period)
     for other in (block, graph):
         assert np.array_equal(calls[0], other[0])
         assert np.array_equal(calls[1], other[1])
