@@ -265,6 +265,137 @@ def run_reference(args, spec, wl_name):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+GROUP_WORKLOAD = "batched-uneven-8"
+
+
+def run_group(args):
+    """Eight uneven systems (1024 walkers) advanced as one group: one stream per member,
+    forked and joined around every group step.  Timed three ways on the same inputs:
+    eager group steps, a captured graph of two group steps, and the members stepped one
+    after another on one stream (what the group's concurrency is measured against)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2003_09468_gb300 import KPointAFQMC, KPointGroup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = gen.BATCHED_UNEVEN
+    systems = [KPointAFQMC(s.grid, gen.cholesky(s), gen.one_body(s), gen.trial(s), s.nwalkers, s.dt,
+                           precision="mixed") for s in specs]
+    grp = KPointGroup(systems)
+    nw = sum(s.nwalkers for s in specs)
+    nsteps = args.warmup + args.steps
+    xs = [[torch.from_numpy(gen.fields(s, i, s.nwalkers, first=rank * s.nwalkers)).to(dev) for s in specs]
+          for i in range(nsteps)]
+    phi0 = [torch.from_numpy(gen.walkers(s, s.nwalkers, first=rank * s.nwalkers)).to(dev) for s in specs]
+    phis = [p.clone() for p in phi0]
+    ws = [torch.ones(s.nwalkers, dtype=torch.float64, device=dev) for s in specs]
+    els = [torch.empty((s.nwalkers, 3), dtype=torch.complex128, device=dev) for s in specs]
+    stream = torch.cuda.current_stream()
+
+    def restart():
+        for p, q, w in zip(phis, phi0, ws):
+            p.copy_(q)
+            w.fill_(1.0)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # eager group steps
+    launches = [0]
+
+    def group_steps(lo, hi, count=False):
+        for i in range(lo, hi):
+            grp.step(phis, xs[i], ws, els, do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
+            if count:
+                launches[0] += grp.launch_count()
+
+    group_steps(0, args.warmup)
+    clocks = Clocks(local)
+    clocks.start()
+    ms_group = timed(lambda: group_steps(args.warmup, nsteps, count=True))
+    clk = clocks.stop()
+    finite = all(bool(torch.isfinite(e).all()) for e in els)
+
+    # the same steps, members one after another on one stream
+    restart()
+
+    def seq_steps(lo, hi):
+        for i in range(lo, hi):
+            for j, s_ in enumerate(systems):
+                s_.step(phis[j], xs[i][j], ws[j], els[j], do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
+
+    seq_steps(0, args.warmup)
+    ms_seq = timed(lambda: seq_steps(args.warmup, nsteps))
+
+    # a captured graph of two group steps, replayed with each step's fields copied in
+    restart()
+    group_steps(0, 1)
+    xa = [torch.empty_like(x) for x in xs[0]]
+    xb = [torch.empty_like(x) for x in xs[0]]
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        grp.step(phis, xa, ws, els, do_qr=False)
+        grp.step(phis, xb, ws, els, do_qr=True)
+    pairs = max(1, args.steps // 2)
+
+    def replays():
+        for r in range(pairs):
+            i = args.warmup + 2 * r
+            for a, b, x0, x1 in zip(xa, xb, xs[i % nsteps], xs[(i + 1) % nsteps]):
+                a.copy_(x0)
+                b.copy_(x1)
+            g.replay()
+
+    replays()
+    ms_graph = timed(replays)
+    del g
+    grp.close()
+    for s_ in systems:
+        s_.close()
+    if rank == 0:
+        value = world * nw * 2 * pairs / (ms_graph * 1e-3)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 2 * pairs,
+            "warmup": args.warmup, "ms_per_step": ms_graph / (2 * pairs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x2-split/f32-acc + f64", "data": "synthetic",
+            "config": {"workload": GROUP_WORKLOAD, "systems": [
+                {"grid": list(s.grid), "M": s.M, "nocc": s.nocc, "nchol": s.nchol, "walkers": s.nwalkers}
+                for s in specs], "walkers_per_gpu": nw, "taylor_order": 6, "qr_period": QR_PERIOD,
+                "precision": "mixed", "parallelism": f"replicas x{world}",
+                "timing": "CUDA graph of two group steps, replayed; fields copied in before each replay"},
+            "eager_group": {"value": world * nw * args.steps / (ms_group * 1e-3), "ms_per_step": ms_group / args.steps,
+                            "gpu_launches": launches[0]},
+            "sequential_members": {"value": world * nw * args.steps / (ms_seq * 1e-3),
+                                   "ms_per_step": ms_seq / args.steps},
+            "speedup_graph_over_sequential": (ms_seq / args.steps) / (ms_graph / (2 * pairs)),
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches[0],
+            "clocks": clk, "finite": finite,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,12 +403,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "mixed", "fp64"], default="auto")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="diamond-3x3x3")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + [GROUP_WORKLOAD], default="diamond-3x3x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-block", action="store_true", help="skip the graph-captured paper block")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
     args = ap.parse_args()
+    if args.workload == GROUP_WORKLOAD:
+        if args.impl == "reference":
+            # the oracle on one walker-step of the smallest member, as for the other workloads
+            return run_reference(args, gen.BATCHED_UNEVEN[0], GROUP_WORKLOAD)
+        return run_group(args)
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, spec, args.workload)

@@ -76,6 +76,14 @@ SMALL_2x2x2 = SystemSpec(grid=(2, 2, 2), M=8, nocc=2, nchol=48, nwalkers=16)
 DIAMOND_3x3x3 = SystemSpec(grid=(3, 3, 3), M=26, nocc=4, nchol=208, nwalkers=64)
 # 4x4x4 grid, 52 orbitals per k (the synthetic analogue of the 4x4x4 TZVP run).
 DIAMOND_4x4x4 = SystemSpec(grid=(4, 4, 4), M=52, nocc=4, nchol=416, nwalkers=256)
+# Eight uneven systems run as one group (1024 walkers in all): grids 2x2x2 .. 3x3x3,
+# M in {16, 26}, n in {2, 4}, 8M Cholesky vectors per Q, each with its own seed.
+BATCHED_UNEVEN = [
+    SystemSpec(grid=g, M=m, nocc=n, nchol=8 * m, nwalkers=w, seed=100 + i)
+    for i, (g, m, n, w) in enumerate([
+        ((2, 2, 2), 16, 2, 256), ((2, 2, 2), 26, 4, 128), ((2, 2, 3), 16, 2, 160), ((2, 2, 3), 26, 4, 96),
+        ((2, 3, 3), 16, 4, 128), ((2, 3, 3), 26, 2, 96), ((3, 3, 3), 16, 2, 128), ((3, 3, 3), 26, 4, 32)])
+]
 
 
 def _rng(seed: int, *key: int) -> np.random.Generator:

@@ -381,6 +381,53 @@ afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, 
                             int flags, int comb, unsigned long long seed, unsigned long long* counter, int* idx,
                             void* stream);
 
+/*
+ * Groups: several independent systems (each its own handle, of any sizes and
+ * precision) advanced by one call.  A group call forks from `stream` onto one
+ * stream per member, runs every member's work there and joins back, so one
+ * captured CUDA graph holds the whole group as concurrent branches and the small,
+ * latency-bound kernels of different systems overlap on the GPU.  Each member
+ * computes exactly what the same call on the member alone computes (bit for bit).
+ * The walker sets of the members are the independent units of the paper's batching
+ * (Sec. 3.2: operate on as many walkers at once as possible).
+ */
+typedef struct afqmc_kp_group* afqmc_kp_group_t;
+
+/*
+ * afqmc_kp_group_create -- a group of nsys (1..64) distinct handles.  The group
+ * refers to the handles and does not own them: they must outlive the group, and
+ * no other call may use them while a group call's work is in flight.  Creates one
+ * non-blocking stream and one event per member.
+ */
+afqmc_status afqmc_kp_group_create(const afqmc_kp_t* systems, int nsys, afqmc_kp_group_t* out);
+
+/* Synchronises the member streams and frees the group (not the member handles). */
+afqmc_status afqmc_kp_group_destroy(afqmc_kp_group_t g);
+
+/*
+ * afqmc_kp_group_step -- afqmc_kp_step on every member.  phi, x, weight, eloc and
+ * logdet are HOST arrays of nsys DEVICE pointers, entry i laid out as for member
+ * i's afqmc_kp_step; eloc (the array, or an entry) and logdet may be NULL.
+ * do_qr and flags apply to every member.
+ */
+afqmc_status afqmc_kp_group_step(afqmc_kp_group_t g, void* const* phi, const double* const* x,
+                                 double* const* weight, void* const* eloc, void* const* logdet, int do_qr,
+                                 int flags, void* stream);
+
+/*
+ * afqmc_kp_group_block -- afqmc_kp_block on every member (HOST arrays of DEVICE
+ * pointers as above; weight_hist and logdet may be NULL; counter[i] is member i's
+ * step counter).  The comb acts within each member's population.
+ */
+afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* const* weight,
+                                  double* const* x, void* const* eloc_hist, double* const* weight_hist,
+                                  void* const* logdet, int nsteps, int qr_period, int energy_period,
+                                  int flags, int comb, unsigned long long seed,
+                                  unsigned long long* const* counter, void* stream);
+
+/* Kernel launches of the last group call, all members together. */
+afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches);
+
 /* Static, NUL-terminated description of a status code. */
 const char* afqmc_status_string(afqmc_status s);
 

@@ -41,6 +41,11 @@ SIGNATURES = {
     "afqmc_status_string": [_I],
     "afqmc_last_message": [],
     "afqmc_orthonormalise_noalloc": [_VP, _I, _I, _I, _VP],
+    "afqmc_kp_group_create": [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP)],
+    "afqmc_kp_group_destroy": [_VP],
+    "afqmc_kp_group_step": [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP],
+    "afqmc_kp_group_block": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, ctypes.c_ulonglong, _VP, _VP],
+    "afqmc_kp_group_launch_count": [_VP, ctypes.POINTER(_I)],
     "afqmc_philox4x32_10": [_VP, ctypes.c_ulonglong, _VP, ctypes.c_size_t, _VP],
     "afqmc_kp_fields": [_VP, ctypes.c_ulonglong, _VP, _VP, _VP],
     "afqmc_kp_comb": [_VP, _VP, _VP, ctypes.c_ulonglong, _VP, _VP, _VP],
@@ -285,6 +290,75 @@ class KPointAFQMC:
     def launch_count(self) -> int:
         n = ctypes.c_int(0)
         _check(self.lib.afqmc_kp_launch_count(self.handle, ctypes.byref(n)), "afqmc_kp_launch_count")
+        return n.value
+
+
+def _ptr_array(ptrs):
+    """Host array of device pointers (kept alive by the caller for the call)."""
+    return (_VP * len(ptrs))(*ptrs)
+
+
+class KPointGroup:
+    """Several KPointAFQMC systems advanced together, one CUDA stream per member."""
+
+    def __init__(self, systems):
+        self.lib = load_library()
+        self.systems = list(systems)
+        arr = _ptr_array([s.handle.value for s in self.systems])
+        g = ctypes.c_void_p()
+        _check(self.lib.afqmc_kp_group_create(ctypes.cast(arr, ctypes.POINTER(_VP)), len(self.systems),
+                                              ctypes.byref(g)), "afqmc_kp_group_create")
+        self.group = g
+
+    def close(self):
+        if getattr(self, "group", None):
+            _check(self.lib.afqmc_kp_group_destroy(self.group), "afqmc_kp_group_destroy")
+            self.group = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arr(self, ts, dtype, shapes, name, optional=False):
+        if ts is None:
+            if optional:
+                return None
+            raise ValueError(f"{name} is required")
+        if len(ts) != len(self.systems):
+            raise ValueError(f"{name}: one entry per member")
+        return _ptr_array([0 if (t is None and optional) else _ptr(t, dtype, shp, f"{name}[{i}]")
+                           for i, (t, shp) in enumerate(zip(ts, shapes))])
+
+    def step(self, phis, xs, weights, elocs=None, logdets=None, do_qr=False, reuse=True, stream=None):
+        S = self.systems
+        pa = self._arr(phis, torch.complex128, [s.phi_shape for s in S], "phi")
+        xa = self._arr(xs, torch.float64, [s.field_shape for s in S], "x")
+        wa = self._arr(weights, torch.float64, [(s.W,) for s in S], "weight")
+        ea = self._arr(elocs, torch.complex128, [(s.W, 3) for s in S], "eloc", optional=True)
+        la = self._arr(logdets, torch.complex128, [(s.W, 2) for s in S], "logdet", optional=True)
+        _check(self.lib.afqmc_kp_group_step(self.group, pa, xa, wa, ea, la, 1 if do_qr else 0, 1 if reuse else 0,
+                                            _stream(stream)), "afqmc_kp_group_step")
+
+    def block(self, phis, weights, xs, eloc_hists, counters, seed: int, nsteps: int, qr_period: int = 5,
+              energy_period: int = 1, weight_hists=None, logdets=None, comb=True, reuse=False, stream=None):
+        S = self.systems
+        nmeas = -(-int(nsteps) // int(energy_period))
+        pa = self._arr(phis, torch.complex128, [s.phi_shape for s in S], "phi")
+        wa = self._arr(weights, torch.float64, [(s.W,) for s in S], "weight")
+        xa = self._arr(xs, torch.float64, [s.field_shape for s in S], "x")
+        ea = self._arr(eloc_hists, torch.complex128, [(nmeas, s.W, 3) for s in S], "eloc_hist")
+        ha = self._arr(weight_hists, torch.float64, [(nsteps, s.W) for s in S], "weight_hist", optional=True)
+        la = self._arr(logdets, torch.complex128, [(s.W, 2) for s in S], "logdet", optional=True)
+        ca = self._arr(counters, torch.int64, [(1,) for _ in S], "counter")
+        _check(self.lib.afqmc_kp_group_block(self.group, pa, wa, xa, ea, ha, la, int(nsteps), int(qr_period),
+                                             int(energy_period), 1 if reuse else 0, 1 if comb else 0,
+                                             int(seed) & (2**64 - 1), ca, _stream(stream)), "afqmc_kp_group_block")
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int(0)
+        _check(self.lib.afqmc_kp_group_launch_count(self.group, ctypes.byref(n)), "afqmc_kp_group_launch_count")
         return n.value
 
 

@@ -82,6 +82,106 @@ bool valid_desc(const afqmc_kp_desc* d) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// One fused step (afqmc_kp_step after validation); keeps the stored-Green bookkeeping.
+cudaError_t step_impl(afqmc_kp* h, void* phi, const double* x, double* weight, void* eloc, void* logdet, int do_qr,
+                      int flags, cudaStream_t st) {
+  const int reuse = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi;
+  h->green_valid = false;
+  cudaError_t e;
+  if (h->mixed)
+    e = mixed::step(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(eloc), static_cast<zc*>(logdet), do_qr,
+                    reuse, st);
+  else
+    e = fp64::step(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(eloc), static_cast<zc*>(logdet), do_qr,
+                   reuse, st);
+  if (e == cudaSuccess) {
+    h->green_valid = true;
+    h->green_phi = phi;
+  }
+  return e;
+}
+
+bool block_args_ok(int nsteps, int qr_period, int energy_period, int flags, int comb) {
+  return nsteps >= 1 && qr_period >= 1 && energy_period >= 1 && !(flags & ~AFQMC_STEP_REUSE_GREEN) &&
+         (comb == 0 || comb == 1);
+}
+
+// One block (afqmc_kp_block after validation): fields, step, ..., then the comb.
+cudaError_t block_impl(afqmc_kp* h, void* phi, double* weight, double* x, void* eloc_hist, double* weight_hist,
+                       void* logdet, int nsteps, int qr_period, int energy_period, int flags, int comb,
+                       unsigned long long seed, unsigned long long* counter, int* idx, cudaStream_t st) {
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e = rng::fields(h, seed, counter, x, st);
+    if (e != cudaSuccess) return e;
+    const int do_qr = ((s + 1) % qr_period == 0) || s == nsteps - 1;
+    const int measure = ((s + 1) % energy_period == 0) || s == nsteps - 1;
+    void* el = measure ? static_cast<void*>(static_cast<zc*>(eloc_hist) + (size_t)(s / energy_period) * h->W * 3)
+                       : nullptr;
+    void* ld = s == nsteps - 1 ? logdet : nullptr;
+    e = step_impl(h, phi, x, weight, el, ld, do_qr, s == 0 ? flags : AFQMC_STEP_REUSE_GREEN, st);
+    if (e != cudaSuccess) return e;
+    if (weight_hist) {
+      e = cudaMemcpyAsync(weight_hist + (size_t)s * h->W, weight, sizeof(double) * h->W, cudaMemcpyDeviceToDevice,
+                          st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (comb) {
+    h->green_valid = false;
+    return rng::comb(h, static_cast<zc*>(phi), weight, seed, counter, idx, st);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// A group of handles stepped together: one stream per member, forked from and joined
+// back to the caller's stream, so that a whole group call captures as one CUDA graph
+// whose branches run concurrently.
+struct afqmc_kp_group {
+  std::vector<afqmc_kp*> members;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  int launches = 0;
+};
+
+namespace {
+
+void group_free(afqmc_kp_group* g) {
+  for (auto s : g->streams) cudaStreamDestroy(s);
+  for (auto e : g->joins) cudaEventDestroy(e);
+  if (g->fork) cudaEventDestroy(g->fork);
+  delete g;
+}
+
+// Runs fn(i, member, member stream) for every member between a fork and a join on st.
+// Every member that was forked is joined, also after an error.
+template <typename F>
+cudaError_t group_run(afqmc_kp_group* g, cudaStream_t st, F&& fn) {
+  g->launches = 0;
+  cudaError_t e = cudaEventRecord(g->fork, st);
+  if (e != cudaSuccess) return e;
+  size_t forked = 0;
+  cudaError_t err = cudaSuccess;
+  for (size_t i = 0; i < g->members.size(); ++i) {
+    e = cudaStreamWaitEvent(g->streams[i], g->fork, 0);
+    if (e != cudaSuccess) { err = e; break; }
+    ++forked;
+    afqmc_kp* h = g->members[i];
+    h->launches = 0;
+    e = fn(i, h, g->streams[i]);
+    g->launches += h->launches;
+    if (e != cudaSuccess) { err = e; break; }
+  }
+  for (size_t i = 0; i < forked; ++i) {
+    e = cudaEventRecord(g->joins[i], g->streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->joins[i], 0);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+  return err;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,21 +362,7 @@ afqmc_status afqmc_kp_step(afqmc_kp_t h, void* phi, const double* x, double* wei
   if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
     return AFQMC_ERR_INVALID;
   h->launches = 0;
-  const int reuse = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi;
-  h->green_valid = false;
-  cudaStream_t st = as_stream(stream);
-  cudaError_t e;
-  if (h->mixed)
-    e = mixed::step(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(eloc), static_cast<zc*>(logdet), do_qr,
-                    reuse, st);
-  else
-    e = fp64::step(h, static_cast<zc*>(phi), x, weight, static_cast<zc*>(eloc), static_cast<zc*>(logdet), do_qr,
-                   reuse, st);
-  if (e == cudaSuccess) {
-    h->green_valid = true;
-    h->green_phi = phi;
-  }
-  return from_cuda(e);
+  return from_cuda(step_impl(h, phi, x, weight, eloc, logdet, do_qr, flags, as_stream(stream)));
 }
 
 afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void* stream) {
@@ -394,41 +480,91 @@ afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, 
                             double* weight_hist, void* logdet, int nsteps, int qr_period, int energy_period,
                             int flags, int comb, unsigned long long seed, unsigned long long* counter, int* idx,
                             void* stream) {
-  if (!h || !phi || !weight || !x || !eloc_hist || !counter || nsteps < 1 || qr_period < 1 || energy_period < 1 ||
-      (flags & ~AFQMC_STEP_REUSE_GREEN) || (comb != 0 && comb != 1))
+  if (!h || !phi || !weight || !x || !eloc_hist || !counter || !block_args_ok(nsteps, qr_period, energy_period, flags,
+                                                                            comb))
     return AFQMC_ERR_INVALID;
   if (comb && rng::comb_smem_bytes(h->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
   h->launches = 0;
-  cudaStream_t st = as_stream(stream);
-  int reuse = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi;
-  h->green_valid = false;
-  zc* ph = static_cast<zc*>(phi);
-  for (int s = 0; s < nsteps; ++s) {
-    cudaError_t e = rng::fields(h, seed, counter, x, st);
-    if (e != cudaSuccess) return from_cuda(e);
-    const int do_qr = ((s + 1) % qr_period == 0) || s == nsteps - 1;
-    const int measure = ((s + 1) % energy_period == 0) || s == nsteps - 1;
-    zc* el = measure ? static_cast<zc*>(eloc_hist) + (size_t)(s / energy_period) * h->W * 3 : nullptr;
-    zc* ld = s == nsteps - 1 ? static_cast<zc*>(logdet) : nullptr;
-    if (h->mixed)
-      e = mixed::step(h, ph, x, weight, el, ld, do_qr, reuse, st);
-    else
-      e = fp64::step(h, ph, x, weight, el, ld, do_qr, reuse, st);
-    if (e != cudaSuccess) return from_cuda(e);
-    if (weight_hist) {
-      e = cudaMemcpyAsync(weight_hist + (size_t)s * h->W, weight, sizeof(double) * h->W, cudaMemcpyDeviceToDevice,
-                          st);
-      if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(block_impl(h, phi, weight, x, eloc_hist, weight_hist, logdet, nsteps, qr_period, energy_period,
+                              flags, comb, seed, counter, idx, as_stream(stream)));
+}
+
+afqmc_status afqmc_kp_group_create(const afqmc_kp_t* systems, int nsys, afqmc_kp_group_t* out) {
+  if (!systems || !out || nsys < 1 || nsys > 64) return AFQMC_ERR_INVALID;
+  for (int i = 0; i < nsys; ++i) {
+    if (!systems[i]) return AFQMC_ERR_INVALID;
+    for (int j = 0; j < i; ++j)
+      if (systems[j] == systems[i]) return AFQMC_ERR_INVALID;   // members share no workspace
+  }
+  afqmc_kp_group* g = new (std::nothrow) afqmc_kp_group();
+  if (!g) return AFQMC_ERR_OOM;
+  try {
+    g->members.assign(systems, systems + nsys);
+    cudaError_t e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+    for (int i = 0; i < nsys && e == cudaSuccess; ++i) {
+      cudaStream_t s = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e == cudaSuccess) g->streams.push_back(s);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) g->joins.push_back(ev);
     }
-    reuse = 1;
+    if (e != cudaSuccess) {
+      group_free(g);
+      return from_cuda(e);
+    }
+  } catch (...) {
+    group_free(g);
+    return AFQMC_ERR_OOM;
   }
-  h->green_valid = true;
-  h->green_phi = phi;
-  if (comb) {
-    h->green_valid = false;
-    cudaError_t e = rng::comb(h, ph, weight, seed, counter, idx, st);
-    if (e != cudaSuccess) return from_cuda(e);
+  *out = g;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_group_destroy(afqmc_kp_group_t g) {
+  if (!g) return AFQMC_ERR_INVALID;
+  cudaError_t e = cudaSuccess;
+  for (auto s : g->streams) {
+    cudaError_t f = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = f;
   }
+  group_free(g);
+  return from_cuda(e);
+}
+
+afqmc_status afqmc_kp_group_step(afqmc_kp_group_t g, void* const* phi, const double* const* x, double* const* weight,
+                                 void* const* eloc, void* const* logdet, int do_qr, int flags, void* stream) {
+  if (!g || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
+    return AFQMC_ERR_INVALID;
+  for (size_t i = 0; i < g->members.size(); ++i)
+    if (!phi[i] || !x[i] || !weight[i]) return AFQMC_ERR_INVALID;
+  return from_cuda(group_run(g, as_stream(stream), [&](size_t i, afqmc_kp* h, cudaStream_t s) {
+    return step_impl(h, phi[i], x[i], weight[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr, do_qr,
+                     flags, s);
+  }));
+}
+
+afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* const* weight, double* const* x,
+                                  void* const* eloc_hist, double* const* weight_hist, void* const* logdet, int nsteps,
+                                  int qr_period, int energy_period, int flags, int comb, unsigned long long seed,
+                                  unsigned long long* const* counter, void* stream) {
+  if (!g || !phi || !weight || !x || !eloc_hist || !counter ||
+      !block_args_ok(nsteps, qr_period, energy_period, flags, comb))
+    return AFQMC_ERR_INVALID;
+  for (size_t i = 0; i < g->members.size(); ++i) {
+    if (!phi[i] || !weight[i] || !x[i] || !eloc_hist[i] || !counter[i]) return AFQMC_ERR_INVALID;
+    if (comb && rng::comb_smem_bytes(g->members[i]->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
+  }
+  return from_cuda(group_run(g, as_stream(stream), [&](size_t i, afqmc_kp* h, cudaStream_t s) {
+    return block_impl(h, phi[i], weight[i], x[i], eloc_hist[i], weight_hist ? weight_hist[i] : nullptr,
+                      logdet ? logdet[i] : nullptr, nsteps, qr_period, energy_period, flags, comb, seed, counter[i],
+                      nullptr, s);
+  }));
+}
+
+afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches) {
+  if (!g || !launches) return AFQMC_ERR_INVALID;
+  *launches = g->launches;
   return AFQMC_OK;
 }
 
