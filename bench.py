@@ -407,6 +407,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-block", action="store_true", help="skip the graph-captured paper block")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip timing the local-energy adjoint")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
     args = ap.parse_args()
     if args.workload == GROUP_WORKLOAD:
@@ -635,6 +636,29 @@ def main():
     dom = max(rooflines, key=lambda k: stages[k][0]) if rooflines else None
     roofline = rooflines.get(dom)
 
+    # the adjoint (dE/dphi and dE/dh for every walker; configs of the adjoint study use the
+    # same system), timed with CUDA events after one warm-up call
+    adjoint = None
+    g_up = torch.from_numpy(gen.upstream(spec)).to(dev)
+    phi.copy_(torch.from_numpy(phi0).to(dev))
+
+    def time_backward(s_, reps):
+        s_.local_energy_backward(phi, g_up)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            s_.local_energy_backward(phi, g_up)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps, s_.launch_count()
+
+    if not args.no_adjoint:
+        ms_adj, adj_launches = time_backward(sys_, 3)
+        adjoint = {"ms_per_call": ms_adj, "walker_gradients_per_s": world * spec.nwalkers / (ms_adj * 1e-3),
+                   "precision": precision, "gpu_launches_per_call": adj_launches,
+                   "outputs": "dE/dphi [W][2][NM][N] and dE/dh [Nk][M][M] for upstream g[W][3]"}
+
     fp64_cmp = None
     if precision == "mixed" and args.compare_fp64 and world == 1:
         del sys_
@@ -653,6 +677,10 @@ def main():
         ms64 = e0.elapsed_time(e1)
         fp64_cmp = {"value": spec.nwalkers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": 1,
                     "speedup_mixed_over_fp64": value / (spec.nwalkers / (ms64 * 1e-3))}
+        if adjoint is not None:
+            ms_adj64, _ = time_backward(s64, 1)
+            adjoint["fp64_ms_per_call"] = ms_adj64
+            adjoint["speedup_mixed_over_fp64"] = ms_adj64 / adjoint["ms_per_call"]
         s64.close()
         sys_ = None
 
@@ -709,6 +737,7 @@ def main():
         "block_energy": block,
         "rates": rates,
         "paper_block": paper_block,
+        "adjoint": adjoint,
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clk,

@@ -1055,24 +1055,18 @@ __global__ void grad_h1_kernel(const zc* A, const zc* Gh, const zc* grad_e, zc* 
   }
 }
 
-static cudaError_t backward_impl(afqmc_kp* h, const zc* grad_e, zc* grad_phi, zc* grad_h1, cudaStream_t st) {
+cudaError_t grad_h1(afqmc_kp* h, const zc* grad_e, zc* gh1, cudaStream_t st) {
+  grad_h1_kernel<<<h->nk, 256, 0, st>>>(h->A, h->Gh, grad_e, gh1, h->nk, h->M, h->n, h->W);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+// dE/dphi from Gam = conj(grad_e)-weighted dE/dGh: with Gh = S^-T phi^T and S = A^dag phi,
+// dGh = S^-T dphi^T (I - A* Gh), so grad_phi = [S^-1 (Gam - (Gam Gh^T) A^dag)]^H in the
+// conjugate convention of the binding.
+cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st) {
   cudaError_t e;
   const int nk = h->nk, M = h->M, n = h->n, N = h->N, NM = h->NM, W = h->W;
-  if (grad_h1) {
-    grad_h1_kernel<<<nk, 256, 0, st>>>(h->A, h->Gh, grad_e, grad_h1, nk, M, n, W);
-    AFQMC_LAUNCHED(h);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (!grad_phi) return cudaSuccess;
-  if ((e = cholesky_trace(h, st)) != cudaSuccess) return e;
-  gamma_init_kernel<<<dim3(2 * W, nk, nk), 128, 0, st>>>(h->LH, h->X, h->AhH, grad_e, h->Gam, h->kminus, h->minus,
-                                                          nk, h->G, M, n);
-  AFQMC_LAUNCHED(h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  gamma_exchange_kernel<<<dim3(2 * W, nk, nk), 256, sizeof(zc) * (n * M + h->G * n * n), st>>>(
-      h->LH, h->Gh, grad_e, h->Gam, h->kminus, h->minus, nk, h->G, M, n);
-  AFQMC_LAUNCHED(h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {  // P = Gam Gh^T  (N x N)
     ZGemm g = gemm_init(N, N, NM, 0, 1);
     g.A = h->Gam; g.lda = NM; g.sA[0] = (long)N * NM;
@@ -1100,6 +1094,23 @@ static cudaError_t backward_impl(afqmc_kp* h, const zc* grad_e, zc* grad_phi, zc
     if ((e = gemm_launch(h, g, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+static cudaError_t backward_impl(afqmc_kp* h, const zc* grad_e, zc* grad_phi, zc* gh1, cudaStream_t st) {
+  cudaError_t e;
+  const int nk = h->nk, M = h->M, n = h->n, W = h->W;
+  if (gh1 && (e = grad_h1(h, grad_e, gh1, st)) != cudaSuccess) return e;
+  if (!grad_phi) return cudaSuccess;
+  if ((e = cholesky_trace(h, st)) != cudaSuccess) return e;
+  gamma_init_kernel<<<dim3(2 * W, nk, nk), 128, 0, st>>>(h->LH, h->X, h->AhH, grad_e, h->Gam, h->kminus, h->minus,
+                                                          nk, h->G, M, n);
+  AFQMC_LAUNCHED(h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  gamma_exchange_kernel<<<dim3(2 * W, nk, nk), 256, sizeof(zc) * (n * M + h->G * n * n), st>>>(
+      h->LH, h->Gh, grad_e, h->Gam, h->kminus, h->minus, nk, h->G, M, n);
+  AFQMC_LAUNCHED(h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return project_gamma(h, grad_phi, st);
 }
 
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,

@@ -56,6 +56,10 @@ struct MixedState {
   __half* lt_sp = nullptr;    float* s_l = nullptr;     // [4][Nk][Nk][M*M][Gp], s_l[Q][G]
   __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][T][n*Mp][n*Mp]
   int4* tri = nullptr;                                   // [T] (Q, k, kx, weight)
+  // adjoint of the exchange: Z for every triple (the partner of a canonical triple holds
+  // the transpose), in the order t = (Q nk + k) nk + kx, and dEX/dGh per block
+  __half* zf_sp = nullptr;    float* s_zf = nullptr;    // [4][Nk^3][n*Mp][n*Mp]
+  float2* gam32 = nullptr;                               // [Nk][Nk][WS][n*Mp]
   float2* dhalf = nullptr;                               // [Nk][M][M] exp(-dt/2 H1') - I
   zc* bproj = nullptr;                                   // [Nk][M][n] A (A^dag A)^-1 per k
   float2* bproj32 = nullptr;                             // the same in fp32 (Green epilogue)
@@ -64,7 +68,7 @@ struct MixedState {
   float4* s_ff = nullptr;                                // [WS][N][N] double-float overlap matrices
   double* logr = nullptr;                                // [WS] log det R of the last Cholesky-QR2
   double2* expart = nullptr;                             // [EX_CHUNKS][WS] exchange partial sums
-  CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z;
+  CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z, m_zf;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
 };
@@ -493,6 +497,61 @@ struct ExchangeP {
     }
     const float inv = 1.f / (s_g[ws] * s_z[t]);   // powers of two: exact after the sum
     xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)((pr0 + pr1) * inv), (double)((pi0 + pi1) * inv));
+  }
+};
+
+// Adjoint of the exchange energy.  EX = -1/2 sum over all triples t = (Q, k, kx) of
+// Gh_beta^T Z_t Gh_alpha with alpha = (kx, k-Q), beta = (k, kx+Q), and the partner
+// (-Q, kx, k) of t swaps alpha and beta and transposes Z, so for a block beta = (k1, k2)
+//   dEX/dGh_beta[ws][(a,s)] = - sum_Q sum_{(b,r)} Z_t[(a,s)][(b,r)] Gh[(kx,b),(k1-Q,r)],
+//   t = (Q, k1, kx), kx = k2 - Q.
+// One tile per (beta, walker-spin rows, column block); the k loop runs over Q and the
+// (b, r) chunks of each triple, and every triple's own Z scale is folded in as its
+// chunks are drained.  gam32 receives the sum without the minus sign.
+struct AdjointP {
+  static constexpr bool kConjA = false;
+  static constexpr bool kChunkScale = true;
+  static constexpr int kStages = STAGES_LIGHT;
+  int tiles, kchunks;  // kchunks = nk * kcb
+  int kcb, mt_n, nt_n, WS, nk, nMp;
+  const int* kminus;
+  const float* s_g;
+  const float* s_zf;
+  float2* gam32;
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    nt = t % nt_n;
+    mt = (t / nt_n) % mt_n;
+    b = t / (nt_n * mt_n);
+  }
+  __device__ void split_k(int b, int kc, int& tf, int& km, int& kx, int& kk) const {
+    const int Q = kc / kcb;
+    kk = kc - Q * kcb;
+    const int k1 = b / nk, k2 = b - k1 * nk;
+    kx = kminus[k2 * nk + Q];   // k2 - Q
+    km = kminus[k1 * nk + Q];   // k1 - Q
+    tf = (Q * nk + k1) * nk + kx;
+  }
+  __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
+    int tf, km, kx, kk;
+    split_k(b, kc, tf, km, kx, kk);
+    tcg::Coords c = {{kk * 32, mt * 128, 0, km, kx}, {kk * 32, nt * BN, 0, tf, 0}};
+    return c;
+  }
+  __device__ float chunk_scale(int b, int kc) const {
+    int tf, km, kx, kk;
+    split_k(b, kc, tf, km, kx, kk);
+    return 1.f / s_zf[tf];   // a power of two: exact
+  }
+  __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
+    const int cols = min(BN, nMp - nt * BN);
+    for (int e = tid; e < 128 * BN; e += 128) {
+      const int r = e / BN, c = e % BN;
+      const int ws = mt * 128 + r;
+      if (ws >= WS || c >= cols) continue;
+      const float inv = 1.f / s_g[ws];
+      const float2 v = tile[r * tcg::STAGE_LD + c];
+      gam32[((size_t)b * WS + ws) * nMp + nt * BN + c] = make_float2(v.x * inv, v.y * inv);
+    }
   }
 };
 
@@ -1210,6 +1269,77 @@ __global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, 
   }
 }
 
+// Z of every triple from the canonical ones: zf[tf] = z[i] or its transpose (the partner).
+__global__ void z_full_kernel(const __half* z_sp, const float* s_z, const int2* zmap, __half* zf_sp, float* s_zf,
+                              int T, int Tf, int nMp) {
+  const size_t per = (size_t)nMp * nMp, ps = (size_t)T * per, pf = (size_t)Tf * per;
+  for (int tf = blockIdx.x; tf < Tf; tf += gridDim.x) {
+    const int2 zm = zmap[tf];
+    if (threadIdx.x == 0) s_zf[tf] = s_z[zm.x];
+    for (int pl = 0; pl < 4; ++pl) {
+      const __half* src = z_sp + pl * ps + (size_t)zm.x * per;
+      __half* dst = zf_sp + pl * pf + (size_t)tf * per;
+      for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
+        const size_t row = e / nMp, col = e % nMp;
+        dst[e] = zm.y ? src[col * nMp + row] : src[e];
+      }
+    }
+  }
+}
+
+// Gam[ws][(k1,a)][(k2,r)] of the adjoint, k2 = k1 - Q, in FP64 from
+//   c2 sum_g X[w][-Q][g] LH[Q][k1][g][a][r]   (Coulomb; fp32 sum over g)
+// + c1 AhH[k1][a][r] on the diagonal blocks  (one-body)
+// - c3 gam32[k1][k2][ws][(a,r)]              (exchange, from the adjoint GEMM)
+// with c = conj(grad_e) per walker.  Block (k1, Q, group of GA_W walkers).
+constexpr int GA_W = 16;
+__global__ void __launch_bounds__(128) gamma_assemble_kernel(const zc* LH, const zc* X, const zc* AhH,
+                                                             const zc* grad_e, const float2* gam32, zc* Gam,
+                                                             const int* kminus, const int* minus, int nk, int G,
+                                                             int M, int n, int Mp, int W) {
+  const int k1 = blockIdx.x, Q = blockIdx.y, w0 = blockIdx.z * GA_W;
+  const int k2 = kminus[k1 * nk + Q], mQ = minus[Q];
+  const int nw = min(GA_W, W - w0);
+  const int nM = n * M, N = nk * n, NM = nk * M, WS = 2 * W, nMp = n * Mp;
+  extern __shared__ float2 xs[];   // [GA_W][G]
+  for (int e = threadIdx.x; e < GA_W * G; e += blockDim.x) {
+    const int wi = e / G, g = e % G;
+    const zc v = wi < nw ? X[((size_t)(w0 + wi) * nk + mQ) * G + g] : zzero();
+    xs[e] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  const zc* lh = LH + ((size_t)Q * nk + k1) * G * nM;
+  for (int e = threadIdx.x; e < nM; e += blockDim.x) {
+    float2 acc[GA_W];
+#pragma unroll
+    for (int i = 0; i < GA_W; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int g = 0; g < G; ++g) {
+      const zc l = lh[(size_t)g * nM + e];
+      const float lr = (float)l.x, li = (float)l.y;
+#pragma unroll
+      for (int i = 0; i < GA_W; ++i) {
+        const float2 x = xs[i * G + g];
+        acc[i].x = fmaf(x.x, lr, fmaf(-x.y, li, acc[i].x));
+        acc[i].y = fmaf(x.x, li, fmaf(x.y, lr, acc[i].y));
+      }
+    }
+    const int a = e / M, r = e % M;
+#pragma unroll
+    for (int i = 0; i < GA_W; ++i) {
+      if (i >= nw) break;
+      const int w = w0 + i;
+      const zc c1 = zconj(grad_e[3 * w + 0]), c2 = zconj(grad_e[3 * w + 1]), c3 = zconj(grad_e[3 * w + 2]);
+      zc base = zmul(c2, zmake((double)acc[i].x, (double)acc[i].y));
+      if (Q == 0) base = zfma(c1, AhH[(size_t)k1 * nM + e], base);
+      for (int sp = 0; sp < 2; ++sp) {
+        const int ws = 2 * w + sp;
+        const float2 gx = gam32[(((size_t)k1 * nk + k2) * WS + ws) * nMp + a * Mp + r];
+        Gam[((size_t)ws * N + k1 * n + a) * NM + k2 * M + r] = zsub(base, zmul(c3, zmake(gx.x, gx.y)));
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -1289,6 +1419,12 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->z_sp, (size_t)4 * T * nMp * nMp, true, st));
   MTRY(dalloc(h, &m->s_z, T, true, st));
   MTRY(dalloc(h, &m->tri, T, false, st));
+  const int Tf = nk * nk * nk;
+  MTRY(dalloc(h, &m->zf_sp, (size_t)4 * Tf * nMp * nMp, true, st));
+  MTRY(dalloc(h, &m->s_zf, Tf, true, st));
+  MTRY(dalloc(h, &m->gam32, (size_t)nk * nk * WS * nMp, true, st));
+  int2* zmap = nullptr;
+  MTRY(dalloc(h, &zmap, Tf, false, st));
   MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
   MTRY(dalloc(h, &m->bproj, (size_t)nk * M * n, true, st));
   MTRY(dalloc(h, &m->bproj32, (size_t)nk * M * n, true, st));
@@ -1299,6 +1435,17 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->logr, (size_t)WS, true, st));
   MTRY(dalloc(h, &m->expart, (size_t)EX_CHUNKS * WS, true, st));
   MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
+  // every triple's canonical member, and whether it is the transposed partner
+  std::vector<int2> zmap_h((size_t)Tf, make_int2(-1, 0));
+  for (int i = 0; i < T; ++i) {
+    const int4 q = tri[i];
+    zmap_h[((size_t)q.x * nk + q.y) * nk + q.z] = make_int2(i, 0);
+    if (q.w == 2) zmap_h[((size_t)h->h_minus[q.x] * nk + q.z) * nk + q.y] = make_int2(i, 1);
+  }
+  for (const int2& v : zmap_h)
+    if (v.x < 0) return cudaErrorInvalidValue;   // every triple has a canonical member
+  MTRY(cudaMemcpyAsync(zmap, zmap_h.data(), sizeof(int2) * Tf, cudaMemcpyHostToDevice, st));
+  MTRY(cudaStreamSynchronize(st));   // zmap_h is a host temporary
 
   // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
   trial_projector_kernel<<<nk, 256, 0, st>>>(h->A, m->bproj, m->zscratch, M, n);
@@ -1314,6 +1461,8 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
                                                n);
   AFQMC_LAUNCHED(h);
   z_build_kernel<<<zctas, 256, 0, st>>>(h->LH, m->tri, h->minus, m->zscratch, m->z_sp, m->s_z, T, nk, G, M, n, Mp);
+  AFQMC_LAUNCHED(h);
+  z_full_kernel<<<std::min(Tf, 4096), 256, 0, st>>>(m->z_sp, m->s_z, zmap, m->zf_sp, m->s_zf, T, Tf, nMp);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
   MTRY(set_one_body(h, st));
@@ -1340,12 +1489,15 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
             {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
   MTRY(map5(&m->m_z, m->z_sp, {(uint64_t)nMp, (uint64_t)nMp, 4, (uint64_t)T, 1},
             {(uint64_t)nMp, (uint64_t)T * nMp * nMp, (uint64_t)nMp * nMp, (uint64_t)T * nMp * nMp * 4}, BN));
+  MTRY(map5(&m->m_zf, m->zf_sp, {(uint64_t)nMp, (uint64_t)nMp, 4, (uint64_t)Tf, 1},
+            {(uint64_t)nMp, (uint64_t)Tf * nMp * nMp, (uint64_t)nMp * nMp, (uint64_t)Tf * nMp * nMp * 4}, BN));
   MTRY(map5(&m->m_phi_a, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, 128));
   MTRY(map5(&m->m_sinvt_b, m->sinvt_sp, {(uint64_t)Np, (uint64_t)N, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)N * Np, (uint64_t)4 * N * Np, (uint64_t)WS * 4 * N * Np}, BN));
   MTRY(map5(&m->m_t0_b, m->t_sp[0], {(uint64_t)NMp, (uint64_t)2 * N, 4, (uint64_t)W, 1},
             {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, BN));
+  MTRY(set_smem_attr((const void*)gamma_assemble_kernel, sizeof(float2) * GA_W * G));
   MTRY(set_smem_attr((const void*)onebody_in_kernel, onebody_smem(h)));
   MTRY(set_smem_attr((const void*)onebody_out_kernel, onebody_smem(h)));
   return cudaSuccess;
@@ -1691,10 +1843,43 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   return cudaSuccess;
 }
 
+// dEX/dGh for every block (AdjointP GEMM into gam32).
+static cudaError_t adjoint_exchange(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  AdjointP p;
+  p.kcb = cdiv(m->nMp, 32);
+  p.kchunks = h->nk * p.kcb;
+  p.mt_n = cdiv(m->WS, 128);
+  p.nt_n = cdiv(m->nMp, BN);
+  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
+  p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
+  p.kminus = h->kminus; p.s_g = m->s_g; p.s_zf = m->s_zf; p.gam32 = m->gam32;
+  return run_gemm(m->m_g, m->m_zf, p, h->flags + 1, st);
+}
+
+// The adjoint: Gam = conj(grad_e)-weighted dE/dGh with the exchange part from the
+// tensor-core GEMM over the full precontracted tensor and the Coulomb and one-body parts in
+// fp32, then the FP64 projection onto dE/dphi (through the FP64 Green's function and S^-1)
+// and dE/dh.
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
                                   cudaStream_t st) {
-  // The adjoint runs on the FP64 kernels (exact); a tensor-core adjoint is not built yet.
-  return fp64::local_energy_backward(h, phi, grad_e, grad_phi, grad_h1, st);
+  MixedState* m = h->mixed;
+  if (grad_phi) {
+    MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_old, h->sing_old, st));
+    MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
+    MSTAGE(AFQMC_STAGE_BACKWARD, adjoint_exchange(h, st));
+    prof_begin(h, AFQMC_STAGE_BACKWARD, st);
+    gamma_assemble_kernel<<<dim3(h->nk, h->nk, cdiv(h->W, GA_W)), 128, sizeof(float2) * GA_W * h->G, st>>>(
+        h->LH, h->X, h->AhH, grad_e, m->gam32, h->Gam, h->kminus, h->minus, h->nk, h->G, h->M, h->n, m->Mp, h->W);
+    AFQMC_LAUNCHED(h);
+    prof_end(h, st);
+    MTRY(cudaGetLastError());
+  }
+  // FP64 Green's function and inverse of the same walkers for the projection
+  MTRY(fp64::green(h, phi, st));
+  if (grad_h1) MSTAGE(AFQMC_STAGE_BACKWARD, fp64::grad_h1(h, grad_e, grad_h1, st));
+  if (grad_phi) MSTAGE(AFQMC_STAGE_BACKWARD, fp64::project_gamma(h, grad_phi, st));
+  return cudaSuccess;
 }
 
 }  // namespace mixed

@@ -50,6 +50,26 @@ struct Coords {
 //       the finished 128 x 64 tile in shared memory, tile[r * STAGE_LD + c] = (re, im);
 //       called by the 128 store threads (tid 0..127, ewarp 0..3) while the drain warps
 //       already accumulate the next tile
+// and optionally
+//   static constexpr bool kChunkScale = true;
+//   __device__ float chunk_scale(int b, int kc) const;
+//       a factor applied to k chunk kc's partial sums as they are drained (operands whose
+//       scale changes along k; a power of two keeps the fold exact)
+template <class P, class = void>
+struct ChunkScaled {
+  static constexpr bool value = false;
+};
+template <class P>
+struct ChunkScaled<P, decltype((void)P::kChunkScale)> {
+  static constexpr bool value = P::kChunkScale;
+};
+template <class P>
+__device__ __forceinline__ float chunk_factor(const P& p, int b, int kc) {
+  if constexpr (ChunkScaled<P>::value)
+    return p.chunk_scale(b, kc);
+  else
+    return 1.f;
+}
 
 // ---------------------------------------------------------------- precise variant
 // The tensor-core accumulator adds each MMA's partial sum with truncation, so a
@@ -247,6 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!ok) continue;
         tc::fence_after_sync();
         const uint32_t d = tmem + lane_off + set * 4 * BNP;
+        const float cf = chunk_factor(p, b, kc);
         // 8 columns of two accumulators per load round: few registers beyond the sums
 #pragma unroll
         for (int gq = 0; gq < BNP / 8; ++gq) {
@@ -255,13 +276,25 @@ __global__ void __launch_bounds__(THREADS, 1)
           tc::tmem_ld8(d + 1 * BNP + gq * 8, y);   // P_ii
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 8; ++c) sre[gq * 8 + c] += P::kConjA ? x[c] + y[c] : x[c] - y[c];
+          for (int c = 0; c < 8; ++c) {
+            const float v = P::kConjA ? x[c] + y[c] : x[c] - y[c];
+            if constexpr (ChunkScaled<P>::value)
+              sre[gq * 8 + c] = fmaf(cf, v, sre[gq * 8 + c]);
+            else
+              sre[gq * 8 + c] += v;
+          }
           tc::tmem_ld8(d + 2 * BNP + gq * 8, x);   // P_ri
           tc::tmem_ld8(d + 3 * BNP + gq * 8, y);   // P_ir
           tc::tmem_ld_wait();
           // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
 #pragma unroll
-          for (int c = 0; c < 8; ++c) sim[gq * 8 + c] += P::kConjA ? x[c] - y[c] : x[c] + y[c];
+          for (int c = 0; c < 8; ++c) {
+            const float v = P::kConjA ? x[c] - y[c] : x[c] + y[c];
+            if constexpr (ChunkScaled<P>::value)
+              sim[gq * 8 + c] = fmaf(cf, v, sim[gq * 8 + c]);
+            else
+              sim[gq * 8 + c] += v;
+          }
         }
         tc::fence_before_sync();
         __syncwarp();
