@@ -84,6 +84,13 @@ def exchange_precontracted_flops(spec) -> float:
     return 8.0 * canonical_triples(spec) * nM * nM * 2 * spec.nwalkers
 
 
+def adjoint_exchange_flops(spec) -> float:
+    """Exchange adjoint through the precontracted tensor: for every block and every Q one
+    (nM x nM) x WS complex GEMM, i.e. all Nk^3 triples, 8 real flops per complex MAC."""
+    nM = spec.nocc * spec.M
+    return 8.0 * spec.nk ** 3 * nM * nM * 2 * spec.nwalkers
+
+
 def taylor_flops(spec, order=6) -> float:
     return 8.0 * order * spec.nwalkers * spec.NM * spec.NM * 2 * spec.N
 
@@ -102,7 +109,7 @@ def vhs_bytes(spec) -> float:
 # ---------------------------------------------------------------------------
 # measured DRAM traffic of a kernel, from its committed ncu summary
 # ---------------------------------------------------------------------------
-KERNEL_POLICY = {"taylor": "TaylorP", "exchange": "ExchangeP", "vhs": "VhsP"}
+KERNEL_POLICY = {"taylor": "TaylorP", "exchange": "ExchangeP", "vhs": "VhsP", "adjoint": "AdjointP"}
 CSRC = os.path.join(ROOT, "paper_2003_09468_gb300", "csrc")
 
 
@@ -642,22 +649,43 @@ def main():
     g_up = torch.from_numpy(gen.upstream(spec)).to(dev)
     phi.copy_(torch.from_numpy(phi0).to(dev))
 
-    def time_backward(s_, reps):
+    def time_backward(s_, reps, profile=False):
         s_.local_energy_backward(phi, g_up)
         torch.cuda.synchronize()
+        if profile:
+            s_.profile(True)
+            s_.stage_times()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(reps):
             s_.local_energy_backward(phi, g_up)
         a1.record(stream)
         torch.cuda.synchronize()
-        return a0.elapsed_time(a1) / reps, s_.launch_count()
+        st_ = None
+        if profile:
+            st_ = s_.stage_times()
+            s_.profile(False)
+        return a0.elapsed_time(a1) / reps, s_.launch_count(), st_
 
     if not args.no_adjoint:
-        ms_adj, adj_launches = time_backward(sys_, 3)
+        ms_adj, adj_launches, adj_stages = time_backward(sys_, 3, profile=True)
         adjoint = {"ms_per_call": ms_adj, "walker_gradients_per_s": world * spec.nwalkers / (ms_adj * 1e-3),
                    "precision": precision, "gpu_launches_per_call": adj_launches,
+                   "stages_ms_per_call": {k: round(v[0] / 3, 3) for k, v in adj_stages.items() if v[1]},
                    "outputs": "dE/dphi [W][2][NM][N] and dE/dh [Nk][M][M] for upstream g[W][3]"}
+        if precision == "mixed":
+            ms_s, n_s = adj_stages["adjoint_gemm"]
+            if n_s:
+                per = ms_s / n_s
+                work = adjoint_exchange_flops(spec)
+                ach = work / (per * 1e-3) / 1e12
+                traffic, src = measured_traffic("adjoint", args.workload)
+                rooflines["adjoint_gemm"] = {
+                    "bound": "tensor", "achieved": ach, "peak": tensor_peak, "unit": "TFLOP/s",
+                    "frac": ach / tensor_peak, "traffic": traffic, "traffic_source": src, "kernel": "adjoint_gemm",
+                    "launches": n_s, "launch_ms": per, "algorithmic_per_launch": work,
+                    "peak_source": f"dense f16/bf16 tensor, sustained, {peaks_kind}; algorithmic flops of the "
+                                   "exchange adjoint over all Nk^3 triples (outside the step)"}
 
     fp64_cmp = None
     if precision == "mixed" and args.compare_fp64 and world == 1:
@@ -678,7 +706,7 @@ def main():
         fp64_cmp = {"value": spec.nwalkers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": 1,
                     "speedup_mixed_over_fp64": value / (spec.nwalkers / (ms64 * 1e-3))}
         if adjoint is not None:
-            ms_adj64, _ = time_backward(s64, 1)
+            ms_adj64, _, _ = time_backward(s64, 1)
             adjoint["fp64_ms_per_call"] = ms_adj64
             adjoint["speedup_mixed_over_fp64"] = ms_adj64 / adjoint["ms_per_call"]
         s64.close()

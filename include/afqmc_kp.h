@@ -250,7 +250,9 @@ typedef enum {
   AFQMC_STAGE_BACKWARD = 8,    /* adjoint kernels                                   */
   AFQMC_STAGE_ONEBODY = 9,     /* tensor-core path: the one-body halves around the
                                   Taylor series and the split of the series' input  */
-  AFQMC_NSTAGES = 10
+  AFQMC_STAGE_ADJOINT_GEMM = 10, /* tensor-core path: the exchange adjoint GEMM alone
+                                   (one interval per launch)                      */
+  AFQMC_NSTAGES = 11
 } afqmc_stage;
 
 /* enable != 0 starts recording (allocates CUDA events on the host side as

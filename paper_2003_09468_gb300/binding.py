@@ -275,7 +275,8 @@ class KPointAFQMC:
         _check(self.lib.afqmc_kp_memory_bytes(self.handle, ctypes.byref(b)), "afqmc_kp_memory_bytes")
         return b.value
 
-    STAGES = ("green", "force_bias", "vhs", "taylor", "weight", "qr", "energy", "exchange", "backward", "onebody")
+    STAGES = ("green", "force_bias", "vhs", "taylor", "weight", "qr", "energy", "exchange", "backward", "onebody",
+              "adjoint_gemm")
 
     def profile(self, enable: bool = True):
         _check(self.lib.afqmc_kp_profile(self.handle, 1 if enable else 0), "afqmc_kp_profile")

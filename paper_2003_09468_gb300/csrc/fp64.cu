@@ -14,6 +14,7 @@
 
 #include <utility>
 
+#include "ff.cuh"
 #include "handle.hpp"
 
 namespace fp64 {
@@ -109,6 +110,94 @@ __global__ void __launch_bounds__(256) zgemm_kernel(ZGemm g) {
   }
 }
 
+// The same GEMM in double-float arithmetic on the FP32 pipe (ff.cuh): FP64 operands are
+// split into hi + lo fp32 pairs as the tiles are staged, products and sums run through the
+// error-free transformations (about 48 significant bits), and the result is rounded back to
+// FP64.  Tile 64 x 64, 4 x 4 outputs per thread.
+constexpr int FBM = 64, FBN = 64, FBK = 8;
+
+__device__ __forceinline__ float4 ff_load(const zc* M, long ld, int r, int c, int op, int rows, int cols) {
+  // element (r, c) of op(M) as a double-float complex, zero outside rows x cols
+  if (r >= rows || c >= cols) return ffa::czero();
+  zc v = op == 0 ? M[(long)r * ld + c] : M[(long)c * ld + r];
+  if (op == 2) v = zconj(v);
+  return ffa::cfrom(v);
+}
+
+__global__ void __launch_bounds__(256) zgemm_ff_kernel(ZGemm g) {
+  __shared__ float4 As[FBK][FBM];
+  __shared__ float4 Bs[FBK][FBN];
+  const int t = threadIdx.x;
+  const int ty = t >> 4, tx = t & 15;
+  const int row0 = blockIdx.y * FBM, col0 = blockIdx.x * FBN;
+  const long nbatch = (long)g.nb[0] * g.nb[1] * g.nb[2];
+  for (long z = blockIdx.z; z < nbatch; z += gridDim.z) {
+    const int b2 = (int)(z % g.nb[2]);
+    const int b1 = (int)((z / g.nb[2]) % g.nb[1]);
+    const int b0 = (int)(z / ((long)g.nb[2] * g.nb[1]));
+    const zc* A = g.A + b0 * g.sA[0] + b1 * g.sA[1] + b2 * g.sA[2];
+    const zc* B = g.B + b0 * g.sB[0] + b1 * g.sB[1] + b2 * g.sB[2];
+    zc* C = g.C + b0 * g.sC[0] + b1 * g.sC[1] + b2 * g.sC[2];
+    ffa::cacc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = ffa::cacc_from(ffa::czero());
+    for (int p0 = 0; p0 < g.k; p0 += FBK) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = t + u * 256;
+        // coalesced along the operand's contiguous index
+        int i, p;
+        if (g.opA == 0) { i = e >> 3; p = e & 7; } else { p = e >> 6; i = e & 63; }
+        As[p][i] = ff_load(A, g.lda, row0 + i, p0 + p, g.opA, g.m, g.k);
+        int j, q;
+        if (g.opB == 0) { q = e >> 6; j = e & 63; } else { j = e >> 3; q = e & 7; }
+        // op(B)[q][j]: stored element (q, j) for N, (j, q) for T / C
+        float4 bv = ffa::czero();
+        if (col0 + j < g.n && p0 + q < g.k) {
+          zc v = g.opB == 0 ? B[(long)(p0 + q) * g.ldb + col0 + j] : B[(long)(col0 + j) * g.ldb + p0 + q];
+          if (g.opB == 2) v = zconj(v);
+          bv = ffa::cfrom(v);
+        }
+        Bs[q][j] = bv;
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int p = 0; p < FBK; ++p) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[p][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[p][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ffa::cacc_fma(acc[i][j], a[i], b[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = row0 + ty * 4 + i, gj = col0 + tx * 4 + j;
+        if (gi < g.m && gj < g.n) {
+          const float4 v = ffa::cacc_get(acc[i][j]);
+          const zc s = zmake(ffa::to_double(ffa::re(v)), ffa::to_double(ffa::im(v)));
+          zc r = zmul(g.alpha, s);
+          zc* c = C + (long)gi * g.ldc + gj;
+          if (g.beta.x != 0.0 || g.beta.y != 0.0) r = zfma(g.beta, *c, r);
+          *c = r;
+          if (g.Acc) {
+            zc* a = g.Acc + b0 * g.sAcc[0] + b1 * g.sAcc[1] + b2 * g.sAcc[2] + (long)gi * g.ldacc + gj;
+            *a = zadd(*a, zmul(g.alpha, s));
+          }
+        }
+      }
+  }
+}
+
 static ZGemm gemm_init(int m, int n, int k, int opA, int opB) {
   ZGemm g;
   memset(&g, 0, sizeof(g));
@@ -123,6 +212,14 @@ static cudaError_t gemm_launch(afqmc_kp* h, const ZGemm& g, cudaStream_t st) {
   long nb = (long)g.nb[0] * g.nb[1] * g.nb[2];
   dim3 grid((g.n + GBN - 1) / GBN, (g.m + GBM - 1) / GBM, (unsigned)(nb < 65535 ? nb : 65535));
   zgemm_kernel<<<grid, 256, 0, st>>>(g);
+  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+
+static cudaError_t gemm_launch_ff(afqmc_kp* h, const ZGemm& g, cudaStream_t st) {
+  long nb = (long)g.nb[0] * g.nb[1] * g.nb[2];
+  dim3 grid((g.n + FBN - 1) / FBN, (g.m + FBM - 1) / FBM, (unsigned)(nb < 65535 ? nb : 65535));
+  zgemm_ff_kernel<<<grid, 256, 0, st>>>(g);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }
@@ -401,7 +498,7 @@ __global__ void __launch_bounds__(256) lu_kernel(zc* S, zc* Sinv, zc* logdet, in
 }
 
 // Gh[w][s] = (phi S^-1)^T = S^-T phi^T  (N x NM)
-static cudaError_t green_impl(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+static cudaError_t green_impl(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st, bool ff = false) {
   cudaError_t e = overlap(h, phi, st);
   if (e != cudaSuccess) return e;
   // pivot scratch lives in the P buffer (used otherwise only by the backward pass)
@@ -414,12 +511,19 @@ static cudaError_t green_impl(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cud
   g.B = phi; g.ldb = N; g.sB[0] = (long)NM * N;
   g.C = h->Gh; g.ldc = NM; g.sC[0] = (long)N * NM;
   g.nb[0] = 2 * h->W;
-  return gemm_launch(h, g, st);
+  return ff ? gemm_launch_ff(h, g, st) : gemm_launch(h, g, st);
 }
 
 cudaError_t green(afqmc_kp* h, const zc* phi, cudaStream_t st) {
   prof_begin(h, AFQMC_STAGE_GREEN, st);
   cudaError_t e = green_impl(h, phi, h->ld_old, h->sing_old, st);
+  prof_end(h, st);
+  return e;
+}
+
+cudaError_t green_ff(afqmc_kp* h, const zc* phi, cudaStream_t st) {
+  prof_begin(h, AFQMC_STAGE_GREEN, st);
+  cudaError_t e = green_impl(h, phi, h->ld_old, h->sing_old, st, true);
   prof_end(h, st);
   return e;
 }
@@ -1064,8 +1168,9 @@ cudaError_t grad_h1(afqmc_kp* h, const zc* grad_e, zc* gh1, cudaStream_t st) {
 // dE/dphi from Gam = conj(grad_e)-weighted dE/dGh: with Gh = S^-T phi^T and S = A^dag phi,
 // dGh = S^-T dphi^T (I - A* Gh), so grad_phi = [S^-1 (Gam - (Gam Gh^T) A^dag)]^H in the
 // conjugate convention of the binding.
-cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st) {
+cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st, bool ff) {
   cudaError_t e;
+  auto launch = [&](const ZGemm& g) { return ff ? gemm_launch_ff(h, g, st) : gemm_launch(h, g, st); };
   const int nk = h->nk, M = h->M, n = h->n, N = h->N, NM = h->NM, W = h->W;
   {  // P = Gam Gh^T  (N x N)
     ZGemm g = gemm_init(N, N, NM, 0, 1);
@@ -1073,7 +1178,7 @@ cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st) {
     g.B = h->Gh; g.ldb = NM; g.sB[0] = (long)N * NM;
     g.C = h->P; g.ldc = N; g.sC[0] = (long)N * N;
     g.nb[0] = 2 * W;
-    if ((e = gemm_launch(h, g, st)) != cudaSuccess) return e;
+    if ((e = launch(g)) != cudaSuccess) return e;
   }
   {  // Gam[:, k-block] -= P[:, k-block of n] A[k]^dagger
     ZGemm g = gemm_init(N, M, n, 0, 2);
@@ -1083,7 +1188,7 @@ cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st) {
     g.nb[0] = 2 * W; g.nb[1] = nk;
     g.alpha = zmake(-1.0, 0.0);
     g.beta = zmake(1.0, 0.0);
-    if ((e = gemm_launch(h, g, st)) != cudaSuccess) return e;
+    if ((e = launch(g)) != cudaSuccess) return e;
   }
   {  // grad_phi = Gam^H Sinv^H  (NM x N)
     ZGemm g = gemm_init(NM, N, N, 2, 2);
@@ -1091,7 +1196,7 @@ cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st) {
     g.B = h->Sinv; g.ldb = N; g.sB[0] = (long)N * N;
     g.C = grad_phi; g.ldc = N; g.sC[0] = (long)NM * N;
     g.nb[0] = 2 * W;
-    if ((e = gemm_launch(h, g, st)) != cudaSuccess) return e;
+    if ((e = launch(g)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -1110,7 +1215,7 @@ static cudaError_t backward_impl(afqmc_kp* h, const zc* grad_e, zc* grad_phi, zc
       h->LH, h->Gh, grad_e, h->Gam, h->kminus, h->minus, nk, h->G, M, n);
   AFQMC_LAUNCHED(h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return project_gamma(h, grad_phi, st);
+  return project_gamma(h, grad_phi, st, false);
 }
 
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,

@@ -113,7 +113,9 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
                                   zc* grad_h1, cudaStream_t st);
 // pieces shared with the mixed path
 cudaError_t grad_h1(afqmc_kp* h, const zc* grad_e, zc* grad_h1, cudaStream_t st);   // from Gh
-cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st);               // Gam, Gh, Sinv
+// the projection's GEMMs in FP64, or (ff) in double-float on the FP32 pipe
+cudaError_t project_gamma(afqmc_kp* h, zc* grad_phi, cudaStream_t st, bool ff);      // Gam, Gh, Sinv
+cudaError_t green_ff(afqmc_kp* h, const zc* phi, cudaStream_t st);  // green() with a double-float Gh GEMM
 cudaError_t overlap_lu(afqmc_kp* h, const zc* phi, zc* ld, int* sing, int want_inv, cudaStream_t st);
 cudaError_t overlap_only(afqmc_kp* h, const zc* phi, cudaStream_t st);
 cudaError_t lu_only(afqmc_kp* h, zc* ld, int* sing, int want_inv, cudaStream_t st);

@@ -1859,15 +1859,15 @@ static cudaError_t adjoint_exchange(afqmc_kp* h, cudaStream_t st) {
 
 // The adjoint: Gam = conj(grad_e)-weighted dE/dGh with the exchange part from the
 // tensor-core GEMM over the full precontracted tensor and the Coulomb and one-body parts in
-// fp32, then the FP64 projection onto dE/dphi (through the FP64 Green's function and S^-1)
-// and dE/dh.
+// fp32, then the projection onto dE/dphi through S^-1 and the Green's function (FP64 LU,
+// double-float products) and dE/dh.
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
                                   cudaStream_t st) {
   MixedState* m = h->mixed;
   if (grad_phi) {
     MSTAGE(AFQMC_STAGE_GREEN, green(h, phi, h->ld_old, h->sing_old, st));
     MSTAGE(AFQMC_STAGE_FORCE_BIAS, cholesky_trace(h, st));
-    MSTAGE(AFQMC_STAGE_BACKWARD, adjoint_exchange(h, st));
+    MSTAGE(AFQMC_STAGE_ADJOINT_GEMM, adjoint_exchange(h, st));
     prof_begin(h, AFQMC_STAGE_BACKWARD, st);
     gamma_assemble_kernel<<<dim3(h->nk, h->nk, cdiv(h->W, GA_W)), 128, sizeof(float2) * GA_W * h->G, st>>>(
         h->LH, h->X, h->AhH, grad_e, m->gam32, h->Gam, h->kminus, h->minus, h->nk, h->G, h->M, h->n, m->Mp, h->W);
@@ -1875,10 +1875,11 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
     prof_end(h, st);
     MTRY(cudaGetLastError());
   }
-  // FP64 Green's function and inverse of the same walkers for the projection
-  MTRY(fp64::green(h, phi, st));
+  // Green's function and inverse of the same walkers for the projection: FP64 overlap and
+  // LU, the large products in double-float
+  MTRY(fp64::green_ff(h, phi, st));
   if (grad_h1) MSTAGE(AFQMC_STAGE_BACKWARD, fp64::grad_h1(h, grad_e, grad_h1, st));
-  if (grad_phi) MSTAGE(AFQMC_STAGE_BACKWARD, fp64::project_gamma(h, grad_phi, st));
+  if (grad_phi) MSTAGE(AFQMC_STAGE_BACKWARD, fp64::project_gamma(h, grad_phi, st, true));
   return cudaSuccess;
 }
 
