@@ -273,6 +273,117 @@ def run_reference(args, spec, wl_name):
 # GPU arm
 # ---------------------------------------------------------------------------
 GROUP_WORKLOAD = "batched-uneven-8"
+DENSE_WORKLOAD = "dense-1x1x2"
+
+
+def dense_oracle_seconds(nwalk, step):
+    """Seconds per walker-step (propagate + E_L) of the standard-representation oracle on the
+    dense workload, over nwalk walkers of one step."""
+    from oracle import standard as so
+    ds = gen.DENSE_1x1x2
+    osys = so.StandardSystem(gen.dense_cholesky(ds), gen.dense_one_body(ds), gen.dense_trial(ds), ds.dt)
+    phis, xo = gen.dense_walkers(ds, nwalk), gen.dense_fields(ds, step, nwalk)
+    t0 = time.perf_counter()
+    for i in range(nwalk):
+        pn, _, _, _ = so.propagate_walker(osys, phis[i], xo[i], 1.0)
+        so.local_energy(osys, pn)
+    return (time.perf_counter() - t0) / nwalk
+
+
+def run_dense_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    times = [dense_oracle_seconds(4, i) for i in range(args.warmup + args.steps)][args.warmup:]
+    t = sum(times) / len(times)
+    v = 1.0 / t
+    sample = f"4 walkers x 1 step per timed step of {DENSE_WORKLOAD}, FP64 NumPy standard representation"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": DENSE_WORKLOAD},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def run_dense(args):
+    """The standard (dense) representation of a two-cell Gamma-point supercell (M = 52, N = 8,
+    416 real vectors, 64 walkers) against the same cells in the k-point representation
+    (1x1x2 grid, M = 26, n = 4, 208 vectors per Q), the comparison of Sec. 3.1 on one GPU."""
+    import torch
+    from paper_2003_09468_gb300 import DenseAFQMC, KPointAFQMC
+
+    def handle_fields(x):
+        # real symmetric vectors: the + fields drive the handle's vectors; plane 1 has no effect
+        out = np.zeros((x.shape[0], 2, 1, x.shape[2]))
+        out[:, 0, 0, :] = x[:, 0]
+        return out
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ds, ks = gen.DENSE_1x1x2, gen.KPOINT_1x1x2
+    nsteps = args.warmup + args.steps
+    stream = torch.cuda.current_stream()
+
+    def timed_steps(sys_, phi0, xs):
+        phi = phi0.clone()
+        w = torch.ones(phi.shape[0], dtype=torch.float64, device=dev)
+        el = torch.empty((phi.shape[0], 3), dtype=torch.complex128, device=dev)
+        for i in range(args.warmup):
+            sys_.step(phi, xs[i], w, el, do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
+        torch.cuda.synchronize()
+        sys_.profile(True)
+        sys_.stage_times()
+        launches = 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.warmup, nsteps):
+            sys_.step(phi, xs[i], w, el, do_qr=((i + 1) % QR_PERIOD == 0))
+            launches += sys_.launch_count()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = sys_.stage_times()
+        sys_.profile(False)
+        return e0.elapsed_time(e1) / args.steps, launches, st, bool(torch.isfinite(el).all())
+
+    dsys = DenseAFQMC(gen.dense_cholesky(ds), gen.dense_one_body(ds), gen.dense_trial(ds), ds.nwalkers, ds.dt,
+                      precision="mixed", hermitian=True)
+    dphi = torch.from_numpy(gen.dense_walkers(ds)).to(dev)
+    dxs = [torch.from_numpy(handle_fields(gen.dense_fields(ds, i))).to(dev) for i in range(nsteps)]
+    clocks = Clocks(0)
+    clocks.start()
+    ms_d, launches_d, st_d, fin_d = timed_steps(dsys, dphi, dxs)
+    clk = clocks.stop()
+    dsys.close()
+    ksys = KPointAFQMC(ks.grid, gen.cholesky(ks), gen.one_body(ks), gen.trial(ks), ks.nwalkers, ks.dt,
+                       precision="mixed")
+    kphi = torch.from_numpy(gen.walkers(ks)).to(dev)
+    kxs = [torch.from_numpy(gen.fields(ks, i)).to(dev) for i in range(nsteps)]
+    ms_k, _, st_k, fin_k = timed_steps(ksys, kphi, kxs)
+    ksys.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        t = dense_oracle_seconds(4, 0)
+        cpu = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"4 walkers x 1 step (propagate + E_L) of {DENSE_WORKLOAD}, FP64 NumPy standard "
+                         f"representation, {t:.3f} s per walker-step"}
+    out = {
+        "metric": METRIC, "value": ds.nwalkers / (ms_d * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_d, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16x2-split/f32-acc + f64", "data": "synthetic",
+        "config": {"workload": DENSE_WORKLOAD, "representation": "standard (dense), Gamma-point supercell",
+                   "M": ds.M, "nocc": ds.nocc, "nchol": ds.nchol, "walkers_per_gpu": ds.nwalkers, "taylor_order": 6,
+                   "qr_period": QR_PERIOD, "precision": "mixed", "parallelism": "replicas x1"},
+        "kpoint_same_cells": {"grid": list(ks.grid), "M": ks.M, "nocc": ks.nocc, "nchol": ks.nchol,
+                              "value": ks.nwalkers / (ms_k * 1e-3), "ms_per_step": ms_k,
+                              "stages_ms": {k: round(v[0] / args.steps, 3) for k, v in st_k.items() if v[1]},
+                              "finite": fin_k},
+        "kpoint_over_dense": ms_d / ms_k,
+        "stages_ms": {k: round(v[0] / args.steps, 3) for k, v in st_d.items() if v[1]},
+        "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches_d, "clocks": clk,
+        "finite": fin_d,
+    }
+    print(json.dumps(out))
 
 
 def run_group(args):
@@ -410,13 +521,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "mixed", "fp64"], default="auto")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + [GROUP_WORKLOAD], default="diamond-3x3x3")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + [GROUP_WORKLOAD, DENSE_WORKLOAD], default="diamond-3x3x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-block", action="store_true", help="skip the graph-captured paper block")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the local-energy adjoint")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
     args = ap.parse_args()
+    if args.workload == DENSE_WORKLOAD:
+        if args.impl == "reference":
+            return run_dense_reference(args)
+        return run_dense(args)
     if args.workload == GROUP_WORKLOAD:
         if args.impl == "reference":
             # the oracle on one walker-step of the smallest member, as for the other workloads

@@ -189,3 +189,93 @@ def upstream(spec: SystemSpec, nw: int | None = None, seed_offset: int = 0) -> n
     """Complex weights g[w, 3] for the three energy parts (upstream gradient)."""
     nw = spec.nwalkers if nw is None else nw
     return _cnormal(_rng(spec.seed + seed_offset, TAG_V1, 10_000), (nw, 3))
+
+
+# ---------------------------------------------------------------------------
+# Standard (dense) representation: one cell at the Gamma point, M orbitals,
+# N occupied per spin, G Cholesky vectors L[g][p][r].
+# ---------------------------------------------------------------------------
+TAG_DENSE = 20
+
+
+@dataclass(frozen=True)
+class DenseSpec:
+    """Sizes and seed of one synthetic standard-representation system.  real=True draws real
+    symmetric Cholesky vectors (real orbitals, as for a Gamma-point supercell); otherwise the
+    vectors come in adjoint pairs (L, L^dag), a set closed under the adjoint, as the vectors
+    of a complex Hamiltonian's electron repulsion integrals are."""
+
+    M: int
+    nocc: int
+    nchol: int
+    nwalkers: int
+    dt: float = 0.005
+    seed: int = 0
+    real: bool = True
+    random_trial: bool = False
+
+    @property
+    def N(self) -> int:
+        return self.nocc
+
+
+# A two-cell Gamma-point supercell of the 1x1x2 k-point system with M = 26 per cell:
+# M = 52, N = 8 per spin, 8M real vectors.
+DENSE_1x1x2 = DenseSpec(M=52, nocc=8, nchol=416, nwalkers=64, real=True)
+# the same cells in the k-point representation
+KPOINT_1x1x2 = SystemSpec(grid=(1, 1, 2), M=26, nocc=4, nchol=208, nwalkers=64)
+
+
+def dense_cholesky(spec: DenseSpec) -> np.ndarray:
+    """L[g, p, r] (nchol, M, M), entries of size exp(-g / 2M) / sqrt(M)."""
+    G, M = spec.nchol, spec.M
+    scale = np.exp(-np.arange(G) / (2.0 * M)) / np.sqrt(M)
+    r = _rng(spec.seed, TAG_DENSE, 0)
+    if spec.real:
+        R = r.standard_normal((G, M, M))
+        return (0.5 * (R + R.transpose(0, 2, 1)) * scale[:, None, None]).astype(np.complex128)
+    if G % 2:
+        raise ValueError("adjoint pairs need an even number of vectors")
+    R = _cnormal(r, (G // 2, M, M)) * scale[0::2, None, None]   # one size per pair
+    out = np.empty((G, M, M), dtype=np.complex128)
+    out[0::2] = R
+    out[1::2] = R.conj().transpose(0, 2, 1)
+    return out
+
+
+def dense_one_body(spec: DenseSpec) -> np.ndarray:
+    """h[p, q] (M, M): diagonal 0..4 plus a small Hermitian (real symmetric if real) part."""
+    r = _rng(spec.seed, TAG_DENSE, 1)
+    R = 0.1 * (r.standard_normal((spec.M, spec.M)) if spec.real else _cnormal(r, (spec.M, spec.M)))
+    np.fill_diagonal(R, 0.0)
+    return (np.diag(np.linspace(0.0, 4.0, spec.M)) + 0.5 * (R + R.conj().T)).astype(np.complex128)
+
+
+def dense_trial(spec: DenseSpec) -> np.ndarray:
+    """A[p, a] (M, nocc): the first nocc orbitals, or nocc columns of a random unitary."""
+    if not spec.random_trial:
+        return np.eye(spec.M, spec.nocc, dtype=np.complex128)
+    Z = _cnormal(_rng(spec.seed, TAG_DENSE, 2), (spec.M, spec.M))
+    Qm, _ = np.linalg.qr(Z)
+    return np.ascontiguousarray(Qm[:, :spec.nocc])
+
+
+def dense_walkers(spec: DenseSpec, nw: int | None = None, first: int = 0) -> np.ndarray:
+    """phi[w, s, M, N], orthonormal columns."""
+    nw = spec.nwalkers if nw is None else nw
+    out = np.empty((nw, 2, spec.M, spec.N), dtype=np.complex128)
+    for i in range(nw):
+        for s in range(2):
+            Qm, _ = np.linalg.qr(_cnormal(_rng(spec.seed, TAG_DENSE, 3, first + i, s), (spec.M, spec.N)))
+            out[i, s] = Qm
+    return out
+
+
+def dense_fields(spec: DenseSpec, step: int, nw: int | None = None, first: int = 0) -> np.ndarray:
+    """x[w, +/-, g] real N(0, 1) fields of one step."""
+    nw = spec.nwalkers if nw is None else nw
+    out = np.empty((nw, 2, spec.nchol))
+    for i in range(nw):
+        out[i] = _rng(spec.seed, TAG_DENSE, 4, step, first + i).standard_normal((2, spec.nchol))
+    return out
+

@@ -104,6 +104,42 @@ typedef struct afqmc_kp* afqmc_kp_t;
 afqmc_status afqmc_kp_create(const afqmc_kp_desc* desc, const void* L, const void* h1,
                              const void* trial, void* stream, afqmc_kp_t* out);
 
+/* Sizes and parameters of one standard-representation system; copied by afqmc_dense_create. */
+typedef struct {
+  int M;               /* orbitals, 1..128                                          */
+  int nocc;            /* occupied orbitals per spin, 1..M                          */
+  int nchol;           /* Cholesky vectors G, >= 1 (2G <= 8192 unless hermitian)    */
+  int nwalkers;        /* walkers per call, >= 1                                    */
+  double dt;           /* imaginary time step, > 0                                  */
+  int taylor_order;    /* terms of the exp(V) series beyond the identity, 1..16     */
+  afqmc_precision prec;
+  int hermitian;       /* 1: every L_g is Hermitian (e.g. real symmetric, real
+                          orbitals at the Gamma point); 0: general complex vectors  */
+  size_t workspace_cap_bytes; /* 0 = no cap                                         */
+} afqmc_dense_desc;
+
+/*
+ * afqmc_dense_create -- a system in the standard (dense) representation of Sec. 2.2:
+ * M orbitals, Cholesky vectors L[g][p][r] with v_{pqrs} = sum_g L_{pr,g} conj(L_{sq,g}),
+ * one-body h[p][q] and trial A[p][a].  The potentials v_{g+/-} built from
+ * (L_g +/- L_g^dag)/2 (Sec. 2.2) are Hermitian combinations A_g = (L_g + L_g^dag)/2 and
+ * B_g = i (L_g - L_g^dag)/2 of the vectors, so the system is created as a handle with a
+ * single k-point (kgrid 1x1x1) and the Hermitian vectors [A; B] (G' = 2G), or A alone
+ * (G' = G) when hermitian = 1.  The exact equivalence needs the integrals to be
+ * symmetric under the exchange of the two electrons (v_pqrs = v_qpsr), as Coulomb
+ * integrals are.  Every entry point then applies to the returned handle, with
+ * NM = M, N = nocc and fields x[W][2][1][G']: x[w][0][0][g] drives v_{g+} and, for
+ * general vectors, x[w][0][0][G + g] drives v_{g-}; x[w][1] has no effect.  The force
+ * bias comes back in the same layout (its second plane is zero).
+ *   L      HOST or DEVICE c128 [G][M][M]
+ *   h1     HOST or DEVICE c128 [M][M], Hermitian
+ *   trial  HOST or DEVICE c128 [M][nocc]
+ * Errors and ownership as for afqmc_kp_create (the library keeps its own copies; the
+ * Hermitian set is built on the device in a temporary buffer freed before return).
+ */
+afqmc_status afqmc_dense_create(const afqmc_dense_desc* desc, const void* L, const void* h1,
+                                const void* trial, void* stream, afqmc_kp_t* out);
+
 /* Frees every device buffer of the handle (synchronises the device first). */
 afqmc_status afqmc_kp_destroy(afqmc_kp_t h);
 

@@ -3,7 +3,7 @@
 The compute lives in libafqmc_kp.so (hand-written CUDA for sm_103a behind the C
 ABI in include/afqmc_kp.h); this package only marshals arguments.
 """
-from .binding import (AfqmcError, KPointAFQMC, KPointGroup, LocalEnergy, LIB_PATH, SIGNATURES,  # noqa: F401
-                      load_library)
+from .binding import (AfqmcError, DenseAFQMC, KPointAFQMC, KPointGroup, LocalEnergy, LIB_PATH,  # noqa: F401
+                      SIGNATURES, load_library)
 
-__all__ = ["AfqmcError", "KPointAFQMC", "KPointGroup", "LocalEnergy", "LIB_PATH", "SIGNATURES", "load_library"]
+__all__ = ["AfqmcError", "DenseAFQMC", "KPointAFQMC", "KPointGroup", "LocalEnergy", "LIB_PATH", "SIGNATURES", "load_library"]

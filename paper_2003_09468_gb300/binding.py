@@ -26,6 +26,7 @@ _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 SIGNATURES = {
     "afqmc_kp_create": [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
     "afqmc_kp_destroy": [_VP],
+    "afqmc_dense_create": [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
     "afqmc_kp_set_one_body": [_VP, _VP, _VP],
     "afqmc_kp_force_bias": [_VP, _VP, _VP, _VP],
     "afqmc_kp_propagate": [_VP, _VP, _VP, _VP, _VP, _I, _VP],
@@ -56,6 +57,11 @@ SIGNATURES = {
 class Desc(ctypes.Structure):
     _fields_ = [("kgrid", ctypes.c_int * 3), ("M", _I), ("nocc", _I), ("nchol", _I), ("nwalkers", _I),
                 ("dt", _D), ("taylor_order", _I), ("prec", _I), ("workspace_cap_bytes", ctypes.c_size_t)]
+
+
+class DenseDesc(ctypes.Structure):
+    _fields_ = [("M", _I), ("nocc", _I), ("nchol", _I), ("nwalkers", _I), ("dt", _D), ("taylor_order", _I),
+                ("prec", _I), ("hermitian", _I), ("workspace_cap_bytes", ctypes.c_size_t)]
 
 
 class AfqmcError(RuntimeError):
@@ -297,6 +303,44 @@ class KPointAFQMC:
 def _ptr_array(ptrs):
     """Host array of device pointers (kept alive by the caller for the call)."""
     return (_VP * len(ptrs))(*ptrs)
+
+
+class DenseAFQMC(KPointAFQMC):
+    """A standard-representation system (afqmc_dense_create): M orbitals, vectors L[G][M][M].
+    It is a single-k-point handle with G' Hermitian vectors; fields and force biases use the
+    layout [W][2][1][G'] (plane 0: the + fields, then for general vectors the - fields)."""
+
+    def __init__(self, L, h1, trial, nwalkers: int, dt: float, taylor_order: int = 6, precision: str = "fp64",
+                 hermitian: bool = False, workspace_cap_bytes: int = 0, stream=None):
+        lib = load_library()
+        self.lib = lib
+        L = _as_c128(L)
+        h1 = _as_c128(h1)
+        trial = _as_c128(trial)
+        G, M, _ = L.shape
+        n = trial.shape[1]
+        self.grid = (1, 1, 1)
+        self.hermitian = bool(hermitian)
+        self.nchol_dense = G
+        self.nk, self.M, self.n, self.W = 1, M, n, int(nwalkers)
+        self.G = G if self.hermitian else 2 * G
+        self.NM, self.N = M, n
+        self.dt = float(dt)
+        self.precision = precision
+        d = DenseDesc()
+        d.M, d.nocc, d.nchol, d.nwalkers = M, n, G, self.W
+        d.dt = self.dt
+        d.taylor_order = int(taylor_order)
+        d.prec = PRECISIONS[precision]
+        d.hermitian = 1 if self.hermitian else 0
+        d.workspace_cap_bytes = int(workspace_cap_bytes)
+        keep = [t if t.is_cuda else t.contiguous() for t in (L, h1, trial)]
+        handle = ctypes.c_void_p()
+        _check(lib.afqmc_dense_create(ctypes.byref(d), keep[0].data_ptr(), keep[1].data_ptr(), keep[2].data_ptr(),
+                                      _stream(stream), ctypes.byref(handle)), "afqmc_dense_create")
+        self.handle = handle
+        h1d = h1.reshape(1, M, M)
+        self.h1 = h1d.cuda() if not h1d.is_cuda else h1d
 
 
 class KPointGroup:

@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "dense.hpp"
 #include "handle.hpp"
 #include "mixed.hpp"
 #include "rng.hpp"
@@ -19,6 +20,7 @@ afqmc_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return AFQMC_OK;
   snprintf(g_msg, sizeof(g_msg), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return AFQMC_ERR_OOM;
+  if (e == cudaErrorNotSupported) return AFQMC_ERR_UNSUPPORTED;
   return AFQMC_ERR_CUDA;
 }
 
@@ -303,6 +305,43 @@ afqmc_status afqmc_kp_create(const afqmc_kp_desc* desc, const void* L, const voi
     delete h;
     return AFQMC_ERR_OOM;
   }
+}
+
+afqmc_status afqmc_dense_create(const afqmc_dense_desc* d, const void* L, const void* h1, const void* trial,
+                                void* stream, afqmc_kp_t* out) {
+  if (!d || !L || !h1 || !trial || !out || (d->hermitian != 0 && d->hermitian != 1) || d->nchol < 1)
+    return AFQMC_ERR_INVALID;
+  const long Gp = (long)d->nchol * (d->hermitian ? 1 : 2);
+  afqmc_kp_desc kd;
+  memset(&kd, 0, sizeof(kd));
+  kd.kgrid[0] = kd.kgrid[1] = kd.kgrid[2] = 1;
+  kd.M = d->M;
+  kd.nocc = d->nocc;
+  kd.nchol = (int)(Gp < 1 << 30 ? Gp : 1 << 30);
+  kd.nwalkers = d->nwalkers;
+  kd.dt = d->dt;
+  kd.taylor_order = d->taylor_order;
+  kd.prec = d->prec;
+  kd.workspace_cap_bytes = d->workspace_cap_bytes;
+  if (!valid_desc(&kd)) return AFQMC_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  const size_t per = (size_t)d->M * d->M;
+  zc* src = nullptr;
+  zc* vec = nullptr;
+  cudaError_t e = cudaMalloc(&src, sizeof(zc) * per * d->nchol);
+  if (e == cudaSuccess) e = cudaMalloc(&vec, sizeof(zc) * per * Gp);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(src, L, sizeof(zc) * per * d->nchol, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = dense::hermitian_vectors(src, vec, d->nchol, d->M, d->hermitian, st);
+  afqmc_status s = e == cudaSuccess ? afqmc_kp_create(&kd, vec, h1, trial, stream, out) : from_cuda(e);
+  cudaError_t f = cudaStreamSynchronize(st);   // the handle has copied the vectors
+  cudaFree(src);
+  cudaFree(vec);
+  if (s == AFQMC_OK && f != cudaSuccess) {
+    afqmc_kp_destroy(*out);
+    *out = nullptr;
+    return from_cuda(f);
+  }
+  return s;
 }
 
 afqmc_status afqmc_kp_destroy(afqmc_kp_t h) {

@@ -1228,11 +1228,14 @@ cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, 
 
 static cudaError_t set_smem(const void* fn, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes > 227 * 1024) return cudaErrorNotSupported;   // larger than one CTA may hold
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Opt in to the dynamic shared memory each kernel needs at this system size.
+// Opt in to the dynamic shared memory each kernel needs at this system size.  A tensor-core
+// (mixed) handle runs none of these kernels (its own take their place), so it needs none.
 static cudaError_t configure_smem(afqmc_kp* h) {
+  if (h->d.prec == AFQMC_MIXED) return cudaSuccess;
   cudaError_t e = set_smem((const void*)vhs_kernel, sizeof(zc) * VWC * h->G);
   if (e == cudaSuccess)
     e = set_smem((const void*)gamma_exchange_kernel, sizeof(zc) * (h->n * h->M + (size_t)h->G * h->n * h->n));
