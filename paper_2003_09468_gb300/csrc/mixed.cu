@@ -172,6 +172,22 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
   return tcg::make_map(m, base, s);
 }
 
+// The same for a B operand of a kPairB policy: the four planes (stride ps elements, order
+// re_hi, re_lo, im_hi, im_lo in memory) are addressed as the two dimensions (re/im, hi/lo),
+// so the staged box holds them as re_hi, im_hi, re_lo, im_lo; d0, d1 and the batch dimension
+// keep their element strides e0 (rows) and eb.
+static cudaError_t map5_pair(CUtensorMap* m, void* base, uint64_t d0, uint64_t d1, uint64_t batch, uint64_t e0,
+                             uint64_t ps, uint64_t eb, uint32_t rows) {
+  tcg::MapSpec s;
+  s.dims[0] = d0; s.dims[1] = d1; s.dims[2] = 2; s.dims[3] = 2; s.dims[4] = batch;
+  s.strides[0] = e0 * sizeof(__half);
+  s.strides[1] = 2 * ps * sizeof(__half);   // re -> im
+  s.strides[2] = ps * sizeof(__half);       // hi -> lo
+  s.strides[3] = eb * sizeof(__half);
+  s.box[0] = 32; s.box[1] = rows; s.box[2] = 2; s.box[3] = 2; s.box[4] = 1;
+  return tcg::make_map(m, base, s);
+}
+
 // ---------------------------------------------------------------------------
 // GEMM policies
 // ---------------------------------------------------------------------------
@@ -180,6 +196,7 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
 // layout.  B = A (A^dag A)^-1 and phi_perp = phi - B S (see green()).
 struct GreenP {
   static constexpr bool kConjA = false;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES;
   int tiles, kchunks;
   int mt_n, nt_n, N, NM, n, M, Mp, nk, WS;
@@ -193,7 +210,7 @@ struct GreenP {
     b = t / (nt_n * mt_n);
   }
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
-    tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, b, 0}};
+    tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, 0, b}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -220,6 +237,7 @@ struct GreenP {
 // blocks are summed in FP64 by xsum_kernel.
 struct ForceBiasP {
   static constexpr bool kConjA = false;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
   int tiles, kchunks;
   int mt_n, nt_n, W, G, nk;
@@ -235,7 +253,7 @@ struct ForceBiasP {
   // rows = Cholesky index g of LH[Q][k] (A), columns = walkers (B = spin-summed Gh)
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
     const int Q = b / nk, k = b % nk, c0 = kc * 32;
-    tcg::Coords c = {{c0, mt * 128, 0, k, Q}, {c0, nt * BN, 0, kminus[k * nk + Q], k}};
+    tcg::Coords c = {{c0, mt * 128, 0, k, Q}, {c0, nt * BN, 0, 0, k * nk + kminus[k * nk + Q]}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -268,6 +286,7 @@ __global__ void xsum_kernel(const double2* Xk, zc* X, int nk, size_t per) {
 // V[w][(k,p)][(k-Q,r)] = sum_g y[w,Q,g] L[Q,k,g,p,r]  -> split planes with a fixed scale
 struct VhsP {
   static constexpr bool kConjA = false;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES;
   int tiles, kchunks;
   int mt_n, nt_n, W, M, nk, NM, NMp;
@@ -283,7 +302,7 @@ struct VhsP {
   // rows (p, r) of L[Q][k] (A), columns = walkers (B = y[Q])
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
     const int Q = b / nk, k = b % nk;
-    tcg::Coords c = {{kc * 32, mt * 128, 0, k, Q}, {kc * 32, nt * BN, 0, Q, 0}};
+    tcg::Coords c = {{kc * 32, mt * 128, 0, k, Q}, {kc * 32, nt * BN, 0, 0, Q}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -341,6 +360,7 @@ struct VhsP {
 //   last step:   acc = phi' (FP64) + V u, the identity part exact.
 struct TaylorP {
   static constexpr bool kConjA = false;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES;
   int tiles, kchunks;
   int mt_n, nt_n, R, NM, NMp;
@@ -356,7 +376,7 @@ struct TaylorP {
     b = t / (nt_n * mt_n);
   }
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
-    tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, b, 0}};
+    tcg::Coords c = {{kc * 32, mt * 128, 0, b, 0}, {kc * 32, nt * BN, 0, 0, b}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -448,6 +468,7 @@ struct TaylorP {
 // L2/HBM while the drain warps already accumulate the next tile.
 struct ExchangeP {
   static constexpr bool kConjA = false;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
   int tiles, kchunks;
   int mt_n, nt_n, WS, nk, nMp;
@@ -465,7 +486,7 @@ struct ExchangeP {
   }
   __device__ tcg::Coords coords(int t, int mt, int nt, int kc) const {
     const int4 q = tri[t];  // (Q, k, kx, weight)
-    tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, t, 0}};
+    tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, 0, t}};
     return c;
   }
   __device__ void store_tile(int t, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -511,6 +532,7 @@ struct ExchangeP {
 struct AdjointP {
   static constexpr bool kConjA = false;
   static constexpr bool kChunkScale = true;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
   int tiles, kchunks;  // kchunks = nk * kcb
   int kcb, mt_n, nt_n, WS, nk, nMp;
@@ -534,7 +556,7 @@ struct AdjointP {
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
     int tf, km, kx, kk;
     split_k(b, kc, tf, km, kx, kk);
-    tcg::Coords c = {{kk * 32, mt * 128, 0, km, kx}, {kk * 32, nt * BN, 0, tf, 0}};
+    tcg::Coords c = {{kk * 32, mt * 128, 0, km, kx}, {kk * 32, nt * BN, 0, 0, tf}};
     return c;
   }
   __device__ float chunk_scale(int b, int kc) const {
@@ -558,6 +580,7 @@ struct AdjointP {
 // Gram[ws] = phi_ws^dag phi_ws from the transposed split planes (rows = columns of phi).
 struct GramP {
   static constexpr bool kConjA = true;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES;
   int tiles, kchunks;
   int mt_n, nt_n, N;
@@ -570,7 +593,7 @@ struct GramP {
   }
   __device__ tcg::Coords coords(int ws, int mt, int nt, int kc) const {
     const int w = ws >> 1, sp = ws & 1;
-    tcg::Coords c = {{kc * 32, sp * N + mt * 128, 0, w, 0}, {kc * 32, sp * N + nt * BN, 0, w, 0}};
+    tcg::Coords c = {{kc * 32, sp * N + mt * 128, 0, w, 0}, {kc * 32, sp * N + nt * BN, 0, 0, w}};
     return c;
   }
   __device__ void store_tile(int ws, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -589,6 +612,7 @@ struct GramP {
 // phi[ws] <- phi[ws] R^-1 : rows r = (k,p), columns j; B = (R^-1)^T split planes.
 struct ApplyRP {
   static constexpr bool kConjA = false;
+  static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES;
   int tiles, kchunks;
   int mt_n, nt_n, NM, N;
@@ -601,7 +625,7 @@ struct ApplyRP {
     b = t / (nt_n * mt_n);
   }
   __device__ tcg::Coords coords(int ws, int mt, int nt, int kc) const {
-    tcg::Coords c = {{kc * 32, mt * 128, 0, ws, 0}, {kc * 32, nt * BN, 0, ws, 0}};
+    tcg::Coords c = {{kc * 32, mt * 128, 0, ws, 0}, {kc * 32, nt * BN, 0, 0, ws}};
     return c;
   }
   __device__ void store_tile(int ws, int mt, int nt, const float2* tile, int tid, int, int) const {
@@ -1470,33 +1494,34 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   // tensor maps
   MTRY(map5(&m->m_sinvt, m->sinvt_sp, {(uint64_t)Np, (uint64_t)N, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)N * Np, (uint64_t)4 * N * Np, (uint64_t)WS * 4 * N * Np}, 128));
-  MTRY(map5(&m->m_phi, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
-            {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, BN));
-  MTRY(map5(&m->m_gsum, m->gsum_sp, {(uint64_t)nMp, (uint64_t)W, 4, (uint64_t)nk, (uint64_t)nk},
-            {(uint64_t)nMp, (uint64_t)nk * nk * W * nMp, (uint64_t)W * nMp, (uint64_t)nk * W * nMp}, BN));
+  MTRY(map5_pair(&m->m_phi, m->phi_sp, (uint64_t)Np, (uint64_t)NM, (uint64_t)WS, (uint64_t)Np, (uint64_t)NM * Np,
+                 (uint64_t)4 * NM * Np, BN));
+  // blocks (k1, k2) of gsum addressed by the one index k1 Nk + k2 (stride W nMp)
+  MTRY(map5_pair(&m->m_gsum, m->gsum_sp, (uint64_t)nMp, (uint64_t)W, (uint64_t)nk * nk, (uint64_t)nMp,
+                 (uint64_t)nk * nk * W * nMp, (uint64_t)W * nMp, BN));
   MTRY(map5(&m->m_lh, m->lh_sp, {(uint64_t)nMp, (uint64_t)G, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)nMp, (uint64_t)nk * nk * G * nMp, (uint64_t)G * nMp, (uint64_t)nk * G * nMp}, 128));
-  MTRY(map5(&m->m_y, m->y_sp, {(uint64_t)Gp, (uint64_t)W, 4, (uint64_t)nk, 1},
-            {(uint64_t)Gp, (uint64_t)nk * W * Gp, (uint64_t)W * Gp, (uint64_t)nk * W * Gp * 4}, BN));
+  MTRY(map5_pair(&m->m_y, m->y_sp, (uint64_t)Gp, (uint64_t)W, (uint64_t)nk, (uint64_t)Gp, (uint64_t)nk * W * Gp,
+                 (uint64_t)W * Gp, BN));
   MTRY(map5(&m->m_lt, m->lt_sp, {(uint64_t)Gp, (uint64_t)M * M, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)Gp, (uint64_t)nk * nk * M * M * Gp, (uint64_t)M * M * Gp, (uint64_t)nk * M * M * Gp}, 128));
   for (int i = 0; i < 2; ++i)
     MTRY(map5(&m->m_t[i], m->t_sp[i], {(uint64_t)NMp, (uint64_t)2 * N, 4, (uint64_t)W, 1},
               {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, 128));
-  MTRY(map5(&m->m_v, m->v_sp, {(uint64_t)NMp, (uint64_t)NM, 4, (uint64_t)W, 1},
-            {(uint64_t)NMp, (uint64_t)NM * NMp, (uint64_t)4 * NM * NMp, (uint64_t)W * 4 * NM * NMp}, BN));
+  MTRY(map5_pair(&m->m_v, m->v_sp, (uint64_t)NMp, (uint64_t)NM, (uint64_t)W, (uint64_t)NMp, (uint64_t)NM * NMp,
+                 (uint64_t)4 * NM * NMp, BN));
   MTRY(map5(&m->m_g, m->g_sp, {(uint64_t)nMp, (uint64_t)WS, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
-  MTRY(map5(&m->m_z, m->z_sp, {(uint64_t)nMp, (uint64_t)nMp, 4, (uint64_t)T, 1},
-            {(uint64_t)nMp, (uint64_t)T * nMp * nMp, (uint64_t)nMp * nMp, (uint64_t)T * nMp * nMp * 4}, BN));
-  MTRY(map5(&m->m_zf, m->zf_sp, {(uint64_t)nMp, (uint64_t)nMp, 4, (uint64_t)Tf, 1},
-            {(uint64_t)nMp, (uint64_t)Tf * nMp * nMp, (uint64_t)nMp * nMp, (uint64_t)Tf * nMp * nMp * 4}, BN));
+  MTRY(map5_pair(&m->m_z, m->z_sp, (uint64_t)nMp, (uint64_t)nMp, (uint64_t)T, (uint64_t)nMp,
+                 (uint64_t)T * nMp * nMp, (uint64_t)nMp * nMp, BN));
+  MTRY(map5_pair(&m->m_zf, m->zf_sp, (uint64_t)nMp, (uint64_t)nMp, (uint64_t)Tf, (uint64_t)nMp,
+                 (uint64_t)Tf * nMp * nMp, (uint64_t)nMp * nMp, BN));
   MTRY(map5(&m->m_phi_a, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, 128));
-  MTRY(map5(&m->m_sinvt_b, m->sinvt_sp, {(uint64_t)Np, (uint64_t)N, 4, (uint64_t)WS, 1},
-            {(uint64_t)Np, (uint64_t)N * Np, (uint64_t)4 * N * Np, (uint64_t)WS * 4 * N * Np}, BN));
-  MTRY(map5(&m->m_t0_b, m->t_sp[0], {(uint64_t)NMp, (uint64_t)2 * N, 4, (uint64_t)W, 1},
-            {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, BN));
+  MTRY(map5_pair(&m->m_sinvt_b, m->sinvt_sp, (uint64_t)Np, (uint64_t)N, (uint64_t)WS, (uint64_t)Np, (uint64_t)N * Np,
+                 (uint64_t)4 * N * Np, BN));
+  MTRY(map5_pair(&m->m_t0_b, m->t_sp[0], (uint64_t)NMp, (uint64_t)2 * N, (uint64_t)W, (uint64_t)NMp,
+                 (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, BN));
   MTRY(set_smem_attr((const void*)gamma_assemble_kernel, sizeof(float2) * GA_W * G));
   MTRY(set_smem_attr((const void*)onebody_in_kernel, onebody_smem(h)));
   MTRY(set_smem_attr((const void*)onebody_out_kernel, onebody_smem(h)));

@@ -63,6 +63,20 @@ template <class P>
 struct ChunkScaled<P, decltype((void)P::kChunkScale)> {
   static constexpr bool value = P::kChunkScale;
 };
+//   static constexpr bool kPairB = true;
+//       B is staged with its planes in the order (re_hi, im_hi, re_lo, im_lo) (a tensor map
+//       whose plane dimensions are (re/im, hi/lo)), so that [B_re; B_im] is one 128-row
+//       operand: one N = 128 MMA then gives [A_x B_re | A_x B_im], twelve MMAs per chunk
+//       instead of twenty-four, and each A plane is read half as often
+template <class P, class = void>
+struct PairB {
+  static constexpr bool value = false;
+};
+template <class P>
+struct PairB<P, decltype((void)P::kPairB)> {
+  static constexpr bool value = P::kPairB;
+};
+
 template <class P>
 __device__ __forceinline__ float chunk_factor(const P& p, int b, int kc) {
   if constexpr (ChunkScaled<P>::value)
@@ -204,27 +218,52 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
           const uint32_t sb = sa + Lay::A_BYTES;
           const uint32_t d = tmem + set * 4 * BNP;
-          uint64_t A[4][2], B[4][2];  // [plane][k16 half]
+          uint64_t A[4][2];  // [plane][k16 half]; A planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
 #pragma unroll
           for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              A[pl][kk] = tc::desc_kmajor_sw64(sa + pl * BM * 64 + kk * 32);
-              B[pl][kk] = tc::desc_kmajor_sw64(sb + pl * BNP * 64 + kk * 32);
-            }
-          // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo.  Accumulators (column offsets):
-          // P_rr = Ar Br (0), P_ii = Ai Bi (64), P_ri = Ar Bi (128), P_ir = Ai Br (192).
-          const int ap[4] = {0, 2, 0, 2}, bp[4] = {0, 2, 2, 0};
+            for (int kk = 0; kk < 2; ++kk) A[pl][kk] = tc::desc_kmajor_sw64(sa + pl * BM * 64 + kk * 32);
+          if constexpr (PairB<P>::value) {
+            // B rows 0..127 = [Br_hi; Bi_hi], rows 128..255 = [Br_lo; Bi_lo].  Accumulators:
+            // Ar [Br | Bi] -> P_rr (0), P_ri (64); Ai [Br | Bi] -> P_ir (128), P_ii (192).
+            constexpr uint32_t id2 = tc::idesc_f16(BM, 2 * BNP, false);
+            uint64_t Bh[2], Bl[2];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t dq = d + q * BNP;
-            const int ah = ap[q], bh = bp[q];
-            tc::mma_f16(dq, A[ah + 1][0], B[bh][0], id, 0);
-            tc::mma_f16(dq, A[ah][0], B[bh + 1][0], id, 1);
-            tc::mma_f16(dq, A[ah + 1][1], B[bh][1], id, 1);
-            tc::mma_f16(dq, A[ah][1], B[bh + 1][1], id, 1);
-            tc::mma_f16(dq, A[ah][0], B[bh][0], id, 1);
-            tc::mma_f16(dq, A[ah][1], B[bh][1], id, 1);
+            for (int kk = 0; kk < 2; ++kk) {
+              Bh[kk] = tc::desc_kmajor_sw64(sb + kk * 32);
+              Bl[kk] = tc::desc_kmajor_sw64(sb + 2 * BNP * 64 + kk * 32);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const uint32_t dq = d + q * 2 * BNP;
+              const int ah = 2 * q;
+              tc::mma_f16(dq, A[ah + 1][0], Bh[0], id2, 0);
+              tc::mma_f16(dq, A[ah][0], Bl[0], id2, 1);
+              tc::mma_f16(dq, A[ah + 1][1], Bh[1], id2, 1);
+              tc::mma_f16(dq, A[ah][1], Bl[1], id2, 1);
+              tc::mma_f16(dq, A[ah][0], Bh[0], id2, 1);
+              tc::mma_f16(dq, A[ah][1], Bh[1], id2, 1);
+            }
+          } else {
+            uint64_t B[4][2];
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk) B[pl][kk] = tc::desc_kmajor_sw64(sb + pl * BNP * 64 + kk * 32);
+            // Accumulators (column offsets):
+            // P_rr = Ar Br (0), P_ii = Ai Bi (64), P_ri = Ar Bi (128), P_ir = Ai Br (192).
+            const int ap[4] = {0, 2, 0, 2}, bp[4] = {0, 2, 2, 0};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t dq = d + q * BNP;
+              const int ah = ap[q], bh = bp[q];
+              tc::mma_f16(dq, A[ah + 1][0], B[bh][0], id, 0);
+              tc::mma_f16(dq, A[ah][0], B[bh + 1][0], id, 1);
+              tc::mma_f16(dq, A[ah + 1][1], B[bh][1], id, 1);
+              tc::mma_f16(dq, A[ah][1], B[bh + 1][1], id, 1);
+              tc::mma_f16(dq, A[ah][0], B[bh][0], id, 1);
+              tc::mma_f16(dq, A[ah][1], B[bh][1], id, 1);
+            }
           }
           tc::mma_commit(&accf[set]);
           tc::mma_commit(&empty[s]);
@@ -268,12 +307,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc::fence_after_sync();
         const uint32_t d = tmem + lane_off + set * 4 * BNP;
         const float cf = chunk_factor(p, b, kc);
+        // column blocks of P_rr, P_ii, P_ri, P_ir in the set
+        constexpr int o_ii = PairB<P>::value ? 3 : 1, o_ri = PairB<P>::value ? 1 : 2, o_ir = PairB<P>::value ? 2 : 3;
         // 8 columns of two accumulators per load round: few registers beyond the sums
 #pragma unroll
         for (int gq = 0; gq < BNP / 8; ++gq) {
           float x[8], y[8];
-          tc::tmem_ld8(d + 0 * BNP + gq * 8, x);   // P_rr
-          tc::tmem_ld8(d + 1 * BNP + gq * 8, y);   // P_ii
+          tc::tmem_ld8(d + 0 * BNP + gq * 8, x);      // P_rr
+          tc::tmem_ld8(d + o_ii * BNP + gq * 8, y);   // P_ii
           tc::tmem_ld_wait();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
@@ -283,8 +324,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             else
               sre[gq * 8 + c] += v;
           }
-          tc::tmem_ld8(d + 2 * BNP + gq * 8, x);   // P_ri
-          tc::tmem_ld8(d + 3 * BNP + gq * 8, y);   // P_ir
+          tc::tmem_ld8(d + o_ri * BNP + gq * 8, x);   // P_ri
+          tc::tmem_ld8(d + o_ir * BNP + gq * 8, y);   // P_ir
           tc::tmem_ld_wait();
           // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
 #pragma unroll
