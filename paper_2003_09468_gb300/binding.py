@@ -109,6 +109,10 @@ def _ptr(t: torch.Tensor, dtype, shape, name) -> int:
         raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    if t.is_complex() and (t.is_conj() or t.is_neg()):
+        # a lazy conjugate or negative view shares the unconjugated storage: its data pointer
+        # would hand the library the wrong values
+        raise ValueError(f"{name} is a lazy conjugate/negative view: pass t.resolve_conj().resolve_neg()")
     return t.data_ptr()
 
 
@@ -435,6 +439,7 @@ class LocalEnergy(torch.autograd.Function):
     def backward(ctx, grad_e):
         (phi,) = ctx.saved_tensors
         sys = ctx.sys
-        gphi, gh1 = sys.local_energy_backward(phi, grad_e.contiguous(), want_phi=ctx.needs_input_grad[0],
+        grad_e = grad_e.resolve_conj().resolve_neg().contiguous()
+        gphi, gh1 = sys.local_energy_backward(phi, grad_e, want_phi=ctx.needs_input_grad[0],
                                               want_h1=ctx.needs_input_grad[1])
         return gphi, gh1, None
