@@ -106,6 +106,45 @@ def vhs_bytes(spec) -> float:
     return 8.0 * spec.nk * spec.nk * spec.nchol * spec.M * spec.M + 8.0 * spec.nwalkers * spec.NM * spec.NM
 
 
+FF_OPS_PER_CMAC = 48.0   # FP32 instructions per complex double-float multiply-add (unnormalised accumulate)
+
+
+def step_roofline_model(spec, qr_period: int, tensor_tfs: float, hbm_gbs: float, sm_mhz: float, sms: int = 152):
+    """Ideal time of each stage of one mixed-path step, each kernel at its own bound
+    (algorithmic flops at the tensor peak, algorithmic bytes at the HBM copy rate, double-float
+    operations at the FP32 issue rate of sms x 128 lanes x clock), summed over the stage's
+    kernels; QR amortised over qr_period steps.  Returns {stage: (bound, ideal_ms)}."""
+    W, nk, M, n, G = spec.nwalkers, spec.nk, spec.M, spec.nocc, spec.nchol
+    WS, NM, N, nM = 2 * W, spec.NM, spec.N, spec.nocc * spec.M
+    Mp = -(-M // 32) * 32
+    nMp = n * Mp
+    T = tensor_tfs * 1e12
+    B = hbm_gbs * 1e9
+    F = sms * 128 * sm_mhz * 1e6
+    ms = lambda x: 1e3 * x
+    out = {}
+    # Green's function of the propagated walkers: double-float overlap and projection, the
+    # double-float inverse, the tensor-core GEMM S^-T phi_perp^T (+ its operands and outputs)
+    ov = max(2.0 * WS * nk * M * n * N * FF_OPS_PER_CMAC / F, 16.0 * WS * NM * N / B)
+    gj = WS * float(N) ** 3 * FF_OPS_PER_CMAC / F
+    gg = max(8.0 * WS * N * NM * N / T, (8.0 * WS * NM * N + 16.0 * nk * nk * WS * nMp) / B)
+    out["green"] = ("ff + tensor", ms(ov + gj + gg))
+    # Cholesky trace X of the new Green's function (spin-summed rows) and the force bias
+    out["force_bias"] = ("hbm", ms(max(8.0 * W * nk * nk * G * nM / T, 8.0 * nk * nk * G * nMp / B)))
+    out["vhs"] = ("hbm", ms(max(8.0 * W * nk * nk * G * M * M / T, vhs_bytes(spec) / B)))
+    out["taylor"] = ("tensor", ms(6 * taylor_term_flops(spec) / T))
+    # the one-body halves: phi read twice and written once in FP64, the fp32 iterate and the
+    # corrections written and read
+    out["onebody"] = ("hbm", ms(80.0 * WS * NM * N / B))
+    # exchange: the precontracted tensor streams once per step
+    t = canonical_triples(spec)
+    out["exchange"] = ("hbm", ms(max(exchange_precontracted_flops(spec) / T, 8.0 * t * nMp * nMp / B)))
+    # Cholesky-QR2 every qr_period steps: two Gram and two apply GEMMs
+    qr = 2 * (8.0 * WS * N * N * NM * 2) / T
+    out["qr"] = ("tensor", ms(qr / qr_period))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # measured DRAM traffic of a kernel, from its committed ncu summary
 # ---------------------------------------------------------------------------
@@ -787,6 +826,23 @@ def main():
             f"HBM copy, {peaks_kind}; stage = operand split + one GEMM launch")
     # dominant kernel: the largest total time in the timed region
     dom = max(rooflines, key=lambda k: stages[k][0]) if rooflines else None
+    # whole step: every stage at its own bound against the live stage times
+    step_roofline = None
+    if precision == "mixed":
+        model = step_roofline_model(spec, QR_PERIOD, tensor_peak, peaks.get("hbm_gbs", 6800.0),
+                                    (clk or {}).get("sm_max_mhz") or 2070.0)
+        per = {}
+        for k, (bound, ideal) in model.items():
+            live = stages[k][0] / steps_t if stages.get(k) and stages[k][1] else None
+            per[k] = {"bound": bound, "ideal_ms": round(ideal, 4), "live_ms": round(live, 4) if live else None,
+                      "frac": round(ideal / live, 3) if live else None}
+        ideal_total = sum(v[1] for v in model.values())
+        step_roofline = {"ideal_ms": ideal_total, "measured_ms": ms / args.steps,
+                         "frac": ideal_total / (ms / args.steps), "stages": per,
+                         "model": "each stage's kernels at their own bound: algorithmic flops at the sustained "
+                                  "tensor peak, algorithmic bytes at the HBM copy rate, double-float work at "
+                                  f"{FF_OPS_PER_CMAC:.0f} FP32 instructions per complex multiply-add at the FP32 "
+                                  "issue rate; E1/E_C, weights and reductions omitted (small)"}
     roofline = rooflines.get(dom)
 
     # the adjoint (dE/dphi and dE/dh for every walker; configs of the adjoint study use the
@@ -925,6 +981,7 @@ def main():
                    "l2": "inputs larger than L2 (Cholesky tensor alone exceeds 129 MB)"},
         "roofline": roofline,
         "rooflines": rooflines,
+        "step_roofline": step_roofline,
         "fp64_path": fp64_cmp,
         "cpu_baseline": cpu_baseline,
         "parity": parity,

@@ -22,6 +22,8 @@ SPECS = {
     "3x1x2-ragged": gen.SystemSpec(grid=(3, 1, 2), M=7, nocc=3, nchol=11, nwalkers=3, random_trial=True, seed=3),
     # single k-point, single walker (standard representation special case)
     "1x1x1": gen.SystemSpec(grid=(1, 1, 1), M=5, nocc=2, nchol=4, nwalkers=1, random_trial=True, seed=5),
+    # the largest orbital count per k-point and the largest nocc M the handle accepts
+    "1x1x1-M128": gen.SystemSpec(grid=(1, 1, 1), M=128, nocc=8, nchol=16, nwalkers=2, random_trial=True, seed=6),
     # 3x3x3 grid with small bands (Q != -Q everywhere but Q = 0)
     "3x3x3-small": gen.SystemSpec(grid=(3, 3, 3), M=4, nocc=1, nchol=9, nwalkers=2, random_trial=True, seed=11),
 }

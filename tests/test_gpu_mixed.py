@@ -42,6 +42,8 @@ SPECS = {
     "2x2x2-rtrial": gen.SystemSpec(grid=(2, 2, 2), M=8, nocc=2, nchol=48, nwalkers=5, random_trial=True, seed=7),
     "3x1x2-ragged": gen.SystemSpec(grid=(3, 1, 2), M=7, nocc=3, nchol=11, nwalkers=3, random_trial=True, seed=3),
     "1x1x1": gen.SystemSpec(grid=(1, 1, 1), M=5, nocc=2, nchol=4, nwalkers=1, random_trial=True, seed=5),
+    # the largest orbital count per k-point and the largest nocc M the handle accepts
+    "1x1x1-M128": gen.SystemSpec(grid=(1, 1, 1), M=128, nocc=8, nchol=16, nwalkers=2, random_trial=True, seed=6),
     "3x3x3-small": gen.SystemSpec(grid=(3, 3, 3), M=4, nocc=1, nchol=9, nwalkers=2, random_trial=True, seed=11),
     # more than 128 walker-spins: two row tiles in every walker-batched GEMM
     "2x1x1-many-walkers": gen.SystemSpec(grid=(2, 1, 1), M=6, nocc=2, nchol=10, nwalkers=70, seed=2),

@@ -62,3 +62,33 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.afqmc_kp_propagate(None, None, None, None, None, 0, None) == 1
     assert lib.afqmc_kp_local_energy_backward(None, None, None, None, None, None) == 1
     assert lib.afqmc_kp_destroy(None) == 1
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    """Generator, comb, block, groups and dense create: NULL pointers and counts out of range
+    are refused before any device work."""
+    from paper_2003_09468_gb300.binding import DenseDesc
+    vp = ctypes.c_void_p
+    assert lib.afqmc_kp_fields(None, 1, None, None, None) == 1
+    assert lib.afqmc_kp_comb(None, None, None, 1, None, None, None) == 1
+    assert lib.afqmc_kp_block(None, None, None, None, None, None, None, 4, 2, 1, 0, 1, 1, None, None, None) == 1
+    assert lib.afqmc_philox4x32_10(None, 1, None, 5, None) == 1
+    assert lib.afqmc_philox4x32_10(None, 1, None, 0, None) == 0          # n = 0: nothing to do
+    out = vp()
+    assert lib.afqmc_kp_group_create(None, 1, ctypes.byref(out)) == 1
+    arr = (vp * 2)(None, None)
+    assert lib.afqmc_kp_group_create(ctypes.cast(arr, ctypes.POINTER(vp)), 2, ctypes.byref(out)) == 1
+    assert lib.afqmc_kp_group_create(ctypes.cast(arr, ctypes.POINTER(vp)), 0, ctypes.byref(out)) == 1
+    assert lib.afqmc_kp_group_step(None, None, None, None, None, None, 0, 0, None) == 1
+    assert lib.afqmc_kp_group_block(None, None, None, None, None, None, None, 1, 1, 1, 0, 0, 1, None, None) == 1
+    assert lib.afqmc_kp_group_destroy(None) == 1
+    assert lib.afqmc_kp_group_launch_count(None, None) == 1
+    d = DenseDesc()
+    d.M, d.nocc, d.nchol, d.nwalkers, d.dt, d.taylor_order, d.prec, d.hermitian = 8, 2, 4, 2, 0.01, 6, 0, 2
+    buf = (ctypes.c_double * 2)()
+    assert lib.afqmc_dense_create(ctypes.byref(d), buf, buf, buf, None, ctypes.byref(out)) == 1   # hermitian 0/1
+    d.hermitian, d.M = 0, 129
+    assert lib.afqmc_dense_create(ctypes.byref(d), buf, buf, buf, None, ctypes.byref(out)) == 1   # M > 128
+    d.M, d.nchol = 8, 0
+    assert lib.afqmc_dense_create(ctypes.byref(d), buf, buf, buf, None, ctypes.byref(out)) == 1   # no vectors
+    assert lib.afqmc_dense_create(None, buf, buf, buf, None, ctypes.byref(out)) == 1
