@@ -470,6 +470,7 @@ def run_group(args):
     systems = [KPointAFQMC(s.grid, gen.cholesky(s), gen.one_body(s), gen.trial(s), s.nwalkers, s.dt,
                            precision="mixed") for s in specs]
     grp = KPointGroup(systems)
+    tunings = [s_.gemm_tuning() for s_ in systems]
     nw = sum(s.nwalkers for s in specs)
     nsteps = args.warmup + args.steps
     xs = [[torch.from_numpy(gen.fields(s, i, s.nwalkers, first=rank * s.nwalkers)).to(dev) for s in specs]
@@ -572,6 +573,7 @@ def run_group(args):
             "speedup_graph_over_sequential": (ms_seq / args.steps) / (ms_graph / (2 * pairs)),
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches[0],
             "clocks": clk, "finite": finite,
+            "autotune": {"ring_depth_per_member": [{k: v["ring_depth"] for k, v in t.items()} for t in tunings]},
         }
         print(json.dumps(out))
     if world > 1:
@@ -633,6 +635,8 @@ def main():
     if sys_ is None:
         precision = "fp64"
         sys_ = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
+    # TMA ring depth per GEMM, picked at create by the library's autotuner (timed per launch)
+    autotune = sys_.gemm_tuning() if precision == "mixed" else None
 
     # walkers and fields: independent replicas per rank (disjoint walker indices)
     first = rank * spec.nwalkers
@@ -982,6 +986,7 @@ def main():
         "roofline": roofline,
         "rooflines": rooflines,
         "step_roofline": step_roofline,
+        "autotune": autotune,
         "fp64_path": fp64_cmp,
         "cpu_baseline": cpu_baseline,
         "parity": parity,

@@ -258,9 +258,11 @@ afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const
  * afqmc_kp_last_error -- synchronise `stream`, read and clear the handle's
  * sticky device flags.  Returns AFQMC_ERR_SINGULAR if any walker had a singular
  * overlap since the last call (their count goes to *n_singular if non-NULL),
- * AFQMC_ERR_TIMEOUT if a bounded device wait gave up, AFQMC_ERR_INVALID if a comb
- * met a total weight that was not positive and finite, AFQMC_ERR_CUDA on an
- * asynchronous CUDA fault, else AFQMC_OK (in that order of precedence).
+ * AFQMC_ERR_TIMEOUT if a bounded device wait gave up, AFQMC_ERR_UNSUPPORTED if a
+ * tensor-core vHS entry left the range of its fixed-scale fp16 format (|V| >= 58;
+ * the walkers of that step are not valid), AFQMC_ERR_INVALID if a comb met a total
+ * weight that was not positive and finite, AFQMC_ERR_CUDA on an asynchronous CUDA
+ * fault, else AFQMC_OK (precedence: CUDA, timeout, vHS range, singular, comb).
  */
 afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular);
 
@@ -465,6 +467,34 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
 
 /* Kernel launches of the last group call, all members together. */
 afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches);
+
+/*
+ * The tensor-core GEMMs of a mixed handle, and their autotuned TMA ring depth.  At create
+ * the library times the step GEMMs (Green's function, force bias, vHS, a Taylor term,
+ * exchange, exchange adjoint) with two- and three-stage rings on the handle's own operands
+ * (three launches each, CUDA events) and keeps the faster for the handle's lifetime; the
+ * depth changes how far the loads run ahead, not the arithmetic, so results do not depend on
+ * it.  The QR GEMMs keep their defaults.
+ */
+typedef enum {
+  AFQMC_GEMM_GREEN = 0,
+  AFQMC_GEMM_FORCE_BIAS = 1,
+  AFQMC_GEMM_VHS = 2,
+  AFQMC_GEMM_TAYLOR = 3,
+  AFQMC_GEMM_EXCHANGE = 4,
+  AFQMC_GEMM_ADJOINT = 5,
+  AFQMC_GEMM_GRAM = 6,
+  AFQMC_GEMM_APPLY_R = 7,
+  AFQMC_NGEMMS = 8
+} afqmc_gemm;
+
+/*
+ * afqmc_kp_gemm_tuning -- the ring depth of every GEMM (depth[AFQMC_NGEMMS]) and the
+ * per-launch milliseconds measured at create with two and three stages (ms2, ms3; 0 where a
+ * GEMM was not timed).  HOST arrays.  *count = AFQMC_NGEMMS for a mixed handle, 0 for an
+ * FP64 handle (no tensor-core GEMMs; the arrays are left untouched).
+ */
+afqmc_status afqmc_kp_gemm_tuning(afqmc_kp_t h, int* depth, double* ms2, double* ms3, int* count);
 
 /* Static, NUL-terminated description of a status code. */
 const char* afqmc_status_string(afqmc_status s);

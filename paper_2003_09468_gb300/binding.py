@@ -47,6 +47,7 @@ SIGNATURES = {
     "afqmc_kp_group_step": [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP],
     "afqmc_kp_group_block": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, ctypes.c_ulonglong, _VP, _VP],
     "afqmc_kp_group_launch_count": [_VP, ctypes.POINTER(_I)],
+    "afqmc_kp_gemm_tuning": [_VP, _VP, _VP, _VP, ctypes.POINTER(_I)],
     "afqmc_philox4x32_10": [_VP, ctypes.c_ulonglong, _VP, ctypes.c_size_t, _VP],
     "afqmc_kp_fields": [_VP, ctypes.c_ulonglong, _VP, _VP, _VP],
     "afqmc_kp_comb": [_VP, _VP, _VP, ctypes.c_ulonglong, _VP, _VP, _VP],
@@ -302,6 +303,18 @@ class KPointAFQMC:
         n = ctypes.c_int(0)
         _check(self.lib.afqmc_kp_launch_count(self.handle, ctypes.byref(n)), "afqmc_kp_launch_count")
         return n.value
+
+    GEMMS = ("green", "force_bias", "vhs", "taylor", "exchange", "adjoint", "gram", "apply_r")
+
+    def gemm_tuning(self):
+        """{gemm: {"ring_depth", "ms_2_stages", "ms_3_stages"}} chosen at create (empty for FP64)."""
+        n = len(self.GEMMS)
+        depth, ms2, ms3 = (ctypes.c_int * n)(), (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        cnt = ctypes.c_int(0)
+        _check(self.lib.afqmc_kp_gemm_tuning(self.handle, depth, ms2, ms3, ctypes.byref(cnt)),
+               "afqmc_kp_gemm_tuning")
+        return {self.GEMMS[i]: {"ring_depth": depth[i], "ms_2_stages": ms2[i], "ms_3_stages": ms3[i]}
+                for i in range(cnt.value)}
 
 
 def _ptr_array(ptrs):

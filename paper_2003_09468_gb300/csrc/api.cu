@@ -458,8 +458,12 @@ afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular) {
   if (cudaMemset(h->flags, 0, sizeof(f)) != cudaSuccess) return AFQMC_ERR_CUDA;
   if (n_singular) *n_singular = f[0];
   if (f[1]) return AFQMC_ERR_TIMEOUT;
+  if (f[2]) {   // the tensor-core vHS left the range of its fixed-scale fp16 format
+    snprintf(g_msg, sizeof(g_msg), "vHS entry beyond the split format's range (|V| >= 58)");
+    return AFQMC_ERR_UNSUPPORTED;
+  }
   if (f[0]) return AFQMC_ERR_SINGULAR;
-  if (f[2]) return AFQMC_ERR_INVALID;
+  if (f[3]) return AFQMC_ERR_INVALID;
   return AFQMC_OK;
 }
 
@@ -604,6 +608,18 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
 afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches) {
   if (!g || !launches) return AFQMC_ERR_INVALID;
   *launches = g->launches;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_gemm_tuning(afqmc_kp_t h, int* depth, double* ms2, double* ms3, int* count) {
+  if (!h || !count) return AFQMC_ERR_INVALID;
+  if (!h->mixed) {
+    *count = 0;
+    return AFQMC_OK;
+  }
+  if (!depth || !ms2 || !ms3) return AFQMC_ERR_INVALID;
+  mixed::gemm_tuning(h, depth, ms2, ms3);
+  *count = AFQMC_NGEMMS;
   return AFQMC_OK;
 }
 

@@ -68,6 +68,10 @@ struct MixedState {
   float4* s_ff = nullptr;                                // [WS][N][N] double-float overlap matrices
   double* logr = nullptr;                                // [WS] log det R of the last Cholesky-QR2
   double2* expart = nullptr;                             // [EX_CHUNKS][WS] exchange partial sums
+  // TMA ring depth of every GEMM (AFQMC_GEMM_* order), chosen at create by timing (autotune),
+  // and the per-launch times measured for two and three stages (0 where not tuned)
+  int ring[AFQMC_NGEMMS] = {0};
+  float tune_ms[AFQMC_NGEMMS][2] = {};
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z, m_zf;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
@@ -1373,9 +1377,146 @@ __global__ void __launch_bounds__(128) gamma_assemble_kernel(const zc* LH, const
     if (e_ != cudaSuccess) return e_;   \
   } while (0)
 
+// Each policy's index in the handle's ring-depth table (AFQMC_GEMM_* of the header).
+template <class P> struct GemmIdOf;
+template <> struct GemmIdOf<GreenP> { static constexpr int value = AFQMC_GEMM_GREEN; };
+template <> struct GemmIdOf<ForceBiasP> { static constexpr int value = AFQMC_GEMM_FORCE_BIAS; };
+template <> struct GemmIdOf<VhsP> { static constexpr int value = AFQMC_GEMM_VHS; };
+template <> struct GemmIdOf<TaylorP> { static constexpr int value = AFQMC_GEMM_TAYLOR; };
+template <> struct GemmIdOf<ExchangeP> { static constexpr int value = AFQMC_GEMM_EXCHANGE; };
+template <> struct GemmIdOf<AdjointP> { static constexpr int value = AFQMC_GEMM_ADJOINT; };
+template <> struct GemmIdOf<GramP> { static constexpr int value = AFQMC_GEMM_GRAM; };
+template <> struct GemmIdOf<ApplyRP> { static constexpr int value = AFQMC_GEMM_APPLY_R; };
+
+// Launch with the handle's ring depth for this GEMM (the policy's default until tuned).  The
+// depth changes only how far the TMA runs ahead: every tile's arithmetic is the same.
 template <class P>
-static cudaError_t run_gemm(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
-  return tcg::launch_precise<P::kStages>(a, b, p, err, st);
+static cudaError_t run_gemm(afqmc_kp* h, const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err,
+                            cudaStream_t st) {
+  const int r = h->mixed->ring[GemmIdOf<P>::value];
+  const int depth = r ? r : P::kStages;
+  return depth == 2 ? tcg::launch_precise<2>(a, b, p, err, st) : tcg::launch_precise<3>(a, b, p, err, st);
+}
+
+// The parameters of each step GEMM as the step launches it.
+static GreenP green_params(const afqmc_kp* h) {
+  const MixedState* m = h->mixed;
+  GreenP p;
+  p.mt_n = cdiv(h->N, 128);
+  p.nt_n = cdiv(h->NM, BN);
+  p.tiles = m->WS * p.mt_n * p.nt_n;
+  p.kchunks = m->Np / 32;
+  p.N = h->N; p.NM = h->NM; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nk = h->nk; p.WS = m->WS;
+  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.bproj32 = m->bproj32; p.g32 = m->g32;
+  return p;
+}
+static ForceBiasP force_bias_params(const afqmc_kp* h) {
+  const MixedState* m = h->mixed;
+  ForceBiasP p;
+  p.mt_n = cdiv(h->G, 128);
+  p.nt_n = cdiv(h->W, BN);
+  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
+  p.kchunks = m->nMp / 32;
+  p.W = h->W; p.G = h->G; p.nk = h->nk;
+  p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.inv_s_lh = m->inv_s_lh; p.Xk = m->xk;
+  return p;
+}
+static VhsP vhs_params(const afqmc_kp* h) {
+  const MixedState* m = h->mixed;
+  VhsP p;
+  p.mt_n = cdiv(h->M * h->M, 128);
+  p.nt_n = cdiv(h->W, BN);
+  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
+  p.kchunks = m->Gp / 32;
+  p.W = h->W; p.M = h->M; p.nk = h->nk; p.NM = h->NM; p.NMp = m->NMp;
+  p.kminus = h->kminus; p.s_y = m->s_y; p.v_sp = m->v_sp; p.overflow = h->flags + 2;
+  return p;
+}
+// Taylor term j of the Horner series, writing the next iterate into t_sp[nxt]
+static TaylorP taylor_params(const afqmc_kp* h, int j, int nxt) {
+  const MixedState* m = h->mixed;
+  const int R = 2 * h->N;
+  TaylorP p;
+  p.mt_n = cdiv(R, 128);
+  p.nt_n = cdiv(h->NM, BN);
+  p.tiles = h->W * p.mt_n * p.nt_n;
+  p.kchunks = m->NMp / 32;
+  p.R = R; p.NM = h->NM; p.NMp = m->NMp;
+  p.inv_j = 1.f / (float)j;
+  p.last = (j == 1);
+  p.s_t = m->s_t; p.p32 = m->p32; p.corr = reinterpret_cast<float4*>(m->acc); p.t_next = m->t_sp[nxt];
+  return p;
+}
+static ExchangeP exchange_params(const afqmc_kp* h) {
+  const MixedState* m = h->mixed;
+  ExchangeP p;
+  p.mt_n = cdiv(m->WS, 128);
+  p.nt_n = cdiv(m->nMp, BN);
+  p.tiles = m->T * p.mt_n * p.nt_n;
+  p.kchunks = m->nMp / 32;
+  p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
+  p.kminus = h->kminus; p.minus = h->minus; p.tri = m->tri; p.s_g = m->s_g; p.s_z = m->s_z; p.g32 = m->g32;
+  p.xpart = m->xpart;
+  return p;
+}
+static AdjointP adjoint_params(const afqmc_kp* h) {
+  const MixedState* m = h->mixed;
+  AdjointP p;
+  p.kcb = cdiv(m->nMp, 32);
+  p.kchunks = h->nk * p.kcb;
+  p.mt_n = cdiv(m->WS, 128);
+  p.nt_n = cdiv(m->nMp, BN);
+  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
+  p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
+  p.kminus = h->kminus; p.s_g = m->s_g; p.s_zf = m->s_zf; p.gam32 = m->gam32;
+  return p;
+}
+
+// Autotuner: time one GEMM with a two- and a three-stage TMA ring on the handle's own
+// operands (three launches each after a warm-up, CUDA events on the create stream) and keep
+// the faster; the policy's default stays unless the other is faster by more than 2%.
+// The operands hold whatever create left in the workspace: the timing does not depend on
+// the values, and every buffer written here is scratch that the next call overwrites.
+template <class P>
+static cudaError_t tune_gemm(afqmc_kp* h, const CUtensorMap& a, const CUtensorMap& b, const P& p, cudaStream_t st,
+                             cudaEvent_t e0, cudaEvent_t e1) {
+  MixedState* m = h->mixed;
+  const int id = GemmIdOf<P>::value;
+  float t[2] = {0.f, 0.f};
+  for (int v = 0; v < 2; ++v) {
+    m->ring[id] = 2 + v;
+    MTRY(run_gemm(h, a, b, p, h->flags + 1, st));
+    MTRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) MTRY(run_gemm(h, a, b, p, h->flags + 1, st));
+    MTRY(cudaEventRecord(e1, st));
+    MTRY(cudaEventSynchronize(e1));
+    MTRY(cudaEventElapsedTime(&t[v], e0, e1));
+    t[v] /= 3.f;
+  }
+  m->tune_ms[id][0] = t[0];
+  m->tune_ms[id][1] = t[1];
+  const int def = P::kStages, other = 5 - def;
+  m->ring[id] = t[other - 2] < 0.98f * t[def - 2] ? other : def;
+  return cudaSuccess;
+}
+
+static cudaError_t autotune(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_sinvt, m->m_phi, green_params(h), st, e0, e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_lh, m->m_gsum, force_bias_params(h), st, e0, e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_lt, m->m_y, vhs_params(h), st, e0, e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_t[0], m->m_v, taylor_params(h, 2, 1), st, e0, e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_z, exchange_params(h), st, e0, e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_zf, adjoint_params(h), st, e0, e1);
+  // the QR GEMMs write the caller's walkers: they keep their defaults
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st);   // scratch-data flags
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
 }
 
 static cudaError_t set_smem_attr(const void* fn, size_t bytes) { return ensure_dyn_smem(fn, bytes); }
@@ -1525,7 +1666,18 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(set_smem_attr((const void*)gamma_assemble_kernel, sizeof(float2) * GA_W * G));
   MTRY(set_smem_attr((const void*)onebody_in_kernel, onebody_smem(h)));
   MTRY(set_smem_attr((const void*)onebody_out_kernel, onebody_smem(h)));
-  return cudaSuccess;
+  return autotune(h, st);
+}
+
+void gemm_tuning(const afqmc_kp* h, int* depth, double* ms2, double* ms3) {
+  const MixedState* m = h->mixed;
+  const int defaults[AFQMC_NGEMMS] = {GreenP::kStages, ForceBiasP::kStages, VhsP::kStages, TaylorP::kStages,
+                                      ExchangeP::kStages, AdjointP::kStages, GramP::kStages, ApplyRP::kStages};
+  for (int i = 0; i < AFQMC_NGEMMS; ++i) {
+    depth[i] = m->ring[i] ? m->ring[i] : defaults[i];
+    ms2[i] = m->tune_ms[i][0];
+    ms3[i] = m->tune_ms[i][1];
+  }
 }
 
 afqmc_status create(afqmc_kp* h, cudaStream_t st) {
@@ -1586,14 +1738,8 @@ static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStre
                                                                m->phi_sp);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
-  GreenP p;
-  p.mt_n = cdiv(h->N, 128);
-  p.nt_n = cdiv(h->NM, BN);
-  p.tiles = WS * p.mt_n * p.nt_n;
-  p.kchunks = m->Np / 32;
-  p.N = h->N; p.NM = h->NM; p.n = h->n; p.M = h->M; p.Mp = m->Mp; p.nk = h->nk; p.WS = WS;
-  p.s_sinv = m->s_sinv; p.s_phi = m->s_phi; p.bproj32 = m->bproj32; p.g32 = m->g32;
-  MTRY(run_gemm(m->m_sinvt, m->m_phi, p, err, st));
+  const GreenP p = green_params(h);
+  MTRY(run_gemm(h, m->m_sinvt, m->m_phi, p, err, st));
   AFQMC_LAUNCHED(h);
   green_max_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->g32, mx_g, h->nk, h->W, m->nMp);
   AFQMC_LAUNCHED(h);
@@ -1605,14 +1751,8 @@ static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStre
 
 static cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
-  ForceBiasP p;
-  p.mt_n = cdiv(h->G, 128);
-  p.nt_n = cdiv(h->W, BN);
-  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
-  p.kchunks = m->nMp / 32;
-  p.W = h->W; p.G = h->G; p.nk = h->nk;
-  p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.inv_s_lh = m->inv_s_lh; p.Xk = m->xk;
-  MTRY(run_gemm(m->m_lh, m->m_gsum, p, h->flags + 1, st));
+  const ForceBiasP p = force_bias_params(h);
+  MTRY(run_gemm(h, m->m_lh, m->m_gsum, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   const size_t per = (size_t)h->W * h->nk * h->G;
   xsum_kernel<<<(int)std::min<size_t>((per + 255) / 256, 4096), 256, 0, st>>>(m->xk, h->X, h->nk, per);
@@ -1637,14 +1777,8 @@ static cudaError_t vhs(afqmc_kp* h, cudaStream_t st) {
   split_y_kernel<<<dim3(h->nk, h->W), 256, 0, st>>>(h->y, m->s_l, m->y_sp, m->s_y, h->nk, h->W, h->G, m->Gp);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
-  VhsP p;
-  p.mt_n = cdiv(h->M * h->M, 128);
-  p.nt_n = cdiv(h->W, BN);
-  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
-  p.kchunks = m->Gp / 32;
-  p.W = h->W; p.M = h->M; p.nk = h->nk; p.NM = h->NM; p.NMp = m->NMp;
-  p.kminus = h->kminus; p.s_y = m->s_y; p.v_sp = m->v_sp; p.overflow = h->flags + 2;
-  MTRY(run_gemm(m->m_lt, m->m_y, p, h->flags + 1, st));
+  const VhsP p = vhs_params(h);
+  MTRY(run_gemm(h, m->m_lt, m->m_y, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   return cudaSuccess;
 }
@@ -1667,17 +1801,9 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   // Horner: u = phi'; u <- phi' + V u / j for j = order .. 1
   for (int j = h->order, step = 0; j >= 1; --j, ++step) {
     const int cur = step & 1, nxt = (step + 1) & 1;
-    TaylorP p;
-    p.mt_n = cdiv(R, 128);
-    p.nt_n = cdiv(h->NM, BN);
-    p.tiles = h->W * p.mt_n * p.nt_n;
-    p.kchunks = m->NMp / 32;
-    p.R = R; p.NM = h->NM; p.NMp = m->NMp;
-    p.inv_j = 1.f / (float)j;
-    p.last = (j == 1);
-    p.s_t = m->s_t; p.p32 = m->p32; p.corr = corr; p.t_next = m->t_sp[nxt];
+    const TaylorP p = taylor_params(h, j, nxt);
     prof_begin(h, AFQMC_STAGE_TAYLOR, st);   // one interval per term: the GEMM launch alone
-    MTRY(run_gemm(m->m_t[cur], m->m_v, p, h->flags + 1, st));
+    MTRY(run_gemm(h, m->m_t[cur], m->m_v, p, h->flags + 1, st));
     prof_end(h, st);
     AFQMC_LAUNCHED(h);
   }
@@ -1756,7 +1882,7 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, double* logr, cudaStream_t st) 
     g.tiles = WS * g.mt_n * g.nt_n;
     g.kchunks = m->NMp / 32;
     g.N = N; g.s_t = m->s_t; g.gram = reinterpret_cast<float2*>(h->P);
-    MTRY(run_gemm(m->m_t[0], m->m_t0_b, g, h->flags + 1, st));
+    MTRY(run_gemm(h, m->m_t[0], m->m_t0_b, g, h->flags + 1, st));
     AFQMC_LAUNCHED(h);
     MTRY(chol_inv(h, logr, st));
     maxabs_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi, (size_t)NM * N, mx_phi);
@@ -1770,7 +1896,7 @@ static cudaError_t cholqr2(afqmc_kp* h, zc* phi, double* logr, cudaStream_t st) 
     a.tiles = WS * a.mt_n * a.nt_n;
     a.kchunks = m->Np / 32;
     a.NM = NM; a.N = N; a.s_phi = m->s_phi; a.s_r = m->s_sinv; a.phi = phi;
-    MTRY(run_gemm(m->m_phi_a, m->m_sinvt_b, a, h->flags + 1, st));
+    MTRY(run_gemm(h, m->m_phi_a, m->m_sinvt_b, a, h->flags + 1, st));
     AFQMC_LAUNCHED(h);
   }
   return cudaSuccess;
@@ -1794,15 +1920,8 @@ static cudaError_t e1_ec(afqmc_kp* h, zc* eloc, cudaStream_t st) {
 
 static cudaError_t exchange(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
-  ExchangeP p;
-  p.mt_n = cdiv(m->WS, 128);
-  p.nt_n = cdiv(m->nMp, BN);
-  p.tiles = m->T * p.mt_n * p.nt_n;
-  p.kchunks = m->nMp / 32;
-  p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
-  p.kminus = h->kminus; p.minus = h->minus; p.tri = m->tri; p.s_g = m->s_g; p.s_z = m->s_z; p.g32 = m->g32;
-  p.xpart = m->xpart;
-  MTRY(run_gemm(m->m_g, m->m_z, p, h->flags + 1, st));
+  const ExchangeP p = exchange_params(h);
+  MTRY(run_gemm(h, m->m_g, m->m_z, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   return cudaSuccess;
 }
@@ -1871,15 +1990,7 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
 // dEX/dGh for every block (AdjointP GEMM into gam32).
 static cudaError_t adjoint_exchange(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
-  AdjointP p;
-  p.kcb = cdiv(m->nMp, 32);
-  p.kchunks = h->nk * p.kcb;
-  p.mt_n = cdiv(m->WS, 128);
-  p.nt_n = cdiv(m->nMp, BN);
-  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
-  p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
-  p.kminus = h->kminus; p.s_g = m->s_g; p.s_zf = m->s_zf; p.gam32 = m->gam32;
-  return run_gemm(m->m_g, m->m_zf, p, h->flags + 1, st);
+  return run_gemm(h, m->m_g, m->m_zf, adjoint_params(h), h->flags + 1, st);
 }
 
 // The adjoint: Gam = conj(grad_e)-weighted dE/dGh with the exchange part from the

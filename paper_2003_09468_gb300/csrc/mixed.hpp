@@ -15,4 +15,6 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
                  cudaStream_t st);
 cudaError_t local_energy_backward(afqmc_kp* h, const zc* phi, const zc* grad_e, zc* grad_phi, zc* grad_h1,
                                   cudaStream_t st);
+// ring depth of every GEMM and the per-launch ms timed for two and three stages at create
+void gemm_tuning(const afqmc_kp* h, int* depth, double* ms2, double* ms3);
 }  // namespace mixed

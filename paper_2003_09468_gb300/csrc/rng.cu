@@ -76,7 +76,7 @@ __global__ void counter_bump_kernel(unsigned long long* counter) { *counter += 1
 
 // Comb selection, one block: cumulative weights in walker order (one thread, so they are
 // the plain running sums), u from Philox, then j_k = upper_bound(C, (k + u) C / W) per
-// walker.  An invalid total keeps the identity and raises flags[2].
+// walker.  An invalid total keeps the identity and raises flags[3].
 __global__ void comb_select_kernel(double* weight, unsigned long long seed, const unsigned long long* counter, int W,
                                    int* idx, int* flags) {
   extern __shared__ __align__(16) unsigned char cs[];
@@ -91,7 +91,7 @@ __global__ void comb_select_kernel(double* weight, unsigned long long seed, cons
     }
     s_tot = acc;
     s_ok = (acc > 0.0) && isfinite(acc);
-    if (!s_ok) atomicAdd(&flags[2], 1);
+    if (!s_ok) atomicAdd(&flags[3], 1);
     const unsigned long long c = *counter;
     const uint4 r = philox4x32_10(
         make_uint4(0u, 0xffffffffu, static_cast<uint32_t>(c), static_cast<uint32_t>(c >> 32)),

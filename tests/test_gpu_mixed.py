@@ -224,3 +224,21 @@ def test_singular_walker_gets_zero_weight():
     assert wg[1] == 0.0 and np.all(np.isfinite(wg)) and np.all(wg[[0, 2, 3, 4]] > 0)
     assert sys_.last_error() == (0, 0)
     sys_.close()
+
+
+def test_gemm_autotuning(case):
+    """Every step GEMM was timed at create with both ring depths and runs the faster one (the
+    policy default unless the other is more than 2% faster); the QR GEMMs keep their defaults."""
+    spec, sys_, _ = case
+    t = sys_.gemm_tuning()
+    assert set(t) == set(sys_.GEMMS)
+    for name, v in t.items():
+        assert v["ring_depth"] in (2, 3), (name, v)
+        if name in ("gram", "apply_r"):
+            assert v["ms_2_stages"] == 0.0 and v["ms_3_stages"] == 0.0
+            continue
+        assert v["ms_2_stages"] > 0.0 and v["ms_3_stages"] > 0.0, (name, v)
+        fast = 2 if v["ms_2_stages"] < v["ms_3_stages"] else 3
+        if v["ring_depth"] != fast:   # the default kept within the 2% margin
+            assert min(v["ms_2_stages"], v["ms_3_stages"]) >= 0.98 * max(v["ms_2_stages"], v["ms_3_stages"]) - 1e-9
+
