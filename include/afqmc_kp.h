@@ -145,8 +145,10 @@ afqmc_status afqmc_kp_destroy(afqmc_kp_t h);
 
 /*
  * afqmc_kp_set_one_body -- replace h[k] (e.g. h + lambda V1 for a response).
+ * Paper: Sec. 2.3, Eq. kp_h1 (h block diagonal in k); Sec. 2.1, Eq. propagator.
  * Recomputes A[k]^dagger h[k] (energy) and exp(-dt/2 (h + v0)) (propagation).
- *   h1  DEVICE c128 [Nk][M][M].
+ *   h1  DEVICE c128 [Nk][M][M], Hermitian per k (not checked).
+ * Invalidates the stored Green's function.  AFQMC_ERR_INVALID on NULL arguments.
  */
 afqmc_status afqmc_kp_set_one_body(afqmc_kp_t h, const void* h1, void* stream);
 
@@ -363,7 +365,9 @@ afqmc_status afqmc_kp_fields(afqmc_kp_t h, unsigned long long seed, unsigned lon
 
 /*
  * afqmc_philox4x32_10 -- the raw generator behind afqmc_kp_fields and afqmc_kp_comb:
- * out[i] = Philox4x32-10(ctr[i], key = (seed_lo, seed_hi)) for i < n.
+ * out[i] = Philox4x32-10(ctr[i], key = (seed_lo, seed_hi)) for i < n (Salmon, Moraes, Dror
+ * and Shaw, SC 2011: ten rounds of the multiply-and-swap bijection, the key advanced by the
+ * Weyl constants between rounds).
  *   ctr   DEVICE uint32 [n][4] counters (c0, c1, c2, c3)
  *   out   DEVICE uint32 [n][4] words
  * Needs no handle; n = 0 is a no-op; AFQMC_ERR_INVALID on NULL pointers with n > 0.
@@ -372,8 +376,9 @@ afqmc_status afqmc_philox4x32_10(const unsigned int* ctr, unsigned long long see
                                  void* stream);
 
 /*
- * afqmc_kp_comb -- population control by the comb.  The paper leaves population
- * control out; this is the standard comb (one uniform u per call): with cumulative
+ * afqmc_kp_comb -- population control by the comb.  The walker weights are those of
+ * Sec. 2.1 (the hybrid weight update); the paper leaves population control out, and
+ * this is the standard comb (one uniform u per call): with cumulative
  * weights C_j = sum_{i<=j} w_i (in walker order) and total C = C_{W-1}, new walker k
  * is old walker j_k = min{ j : C_j > (k + u) C / W } and all new weights are C / W.
  * u = (a + 1/2) 2^-32 with a the first Philox4x32-10 word of counter
@@ -445,7 +450,8 @@ afqmc_status afqmc_kp_group_create(const afqmc_kp_t* systems, int nsys, afqmc_kp
 afqmc_status afqmc_kp_group_destroy(afqmc_kp_group_t g);
 
 /*
- * afqmc_kp_group_step -- afqmc_kp_step on every member.  phi, x, weight, eloc and
+ * afqmc_kp_group_step -- afqmc_kp_step (Sec. 2.1-2.3, one hybrid step and the local
+ * energy) on every member, batched as Sec. 3.2 advises.  phi, x, weight, eloc and
  * logdet are HOST arrays of nsys DEVICE pointers, entry i laid out as for member
  * i's afqmc_kp_step; eloc (the array, or an entry) and logdet may be NULL.
  * do_qr and flags apply to every member.
@@ -455,9 +461,10 @@ afqmc_status afqmc_kp_group_step(afqmc_kp_group_t g, void* const* phi, const dou
                                  int flags, void* stream);
 
 /*
- * afqmc_kp_group_block -- afqmc_kp_block on every member (HOST arrays of DEVICE
- * pointers as above; weight_hist and logdet may be NULL; counter[i] is member i's
- * step counter).  The comb acts within each member's population.
+ * afqmc_kp_group_block -- afqmc_kp_block (the block of Sec. 3.1) on every member
+ * (HOST arrays of DEVICE pointers as above; weight_hist and logdet may be NULL;
+ * counter[i] is member i's step counter).  The comb acts within each member's
+ * population.
  */
 afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* const* weight,
                                   double* const* x, void* const* eloc_hist, double* const* weight_hist,
