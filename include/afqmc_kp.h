@@ -19,7 +19,9 @@
  *   per momentum transfer Q, W = nwalkers.  k - Q is taken modulo the grid.
  * - Array pointers passed to calls other than afqmc_kp_create are DEVICE pointers
  *   on the current device, owned by the caller, and must stay valid until the
- *   work enqueued on `stream` has finished.  `stream` is a cudaStream_t (NULL
+ *   work enqueued on `stream` has finished.  Complex arrays (c128: interleaved
+ *   (re, im) doubles) must be 16-byte aligned, as cudaMalloc and PyTorch
+ *   allocations are; an unaligned complex array is refused with AFQMC_ERR_INVALID.  `stream` is a cudaStream_t (NULL
  *   means the legacy default stream).  Calls are asynchronous: they enqueue
  *   kernels and return without synchronising, except where stated.
  * - After afqmc_kp_create returns, no call allocates device memory, so every
@@ -368,9 +370,10 @@ afqmc_status afqmc_kp_fields(afqmc_kp_t h, unsigned long long seed, unsigned lon
  * out[i] = Philox4x32-10(ctr[i], key = (seed_lo, seed_hi)) for i < n (Salmon, Moraes, Dror
  * and Shaw, SC 2011: ten rounds of the multiply-and-swap bijection, the key advanced by the
  * Weyl constants between rounds).
- *   ctr   DEVICE uint32 [n][4] counters (c0, c1, c2, c3)
- *   out   DEVICE uint32 [n][4] words
- * Needs no handle; n = 0 is a no-op; AFQMC_ERR_INVALID on NULL pointers with n > 0.
+ *   ctr   DEVICE uint32 [n][4] counters (c0, c1, c2, c3), 16-byte aligned
+ *   out   DEVICE uint32 [n][4] words, 16-byte aligned
+ * Needs no handle; n = 0 is a no-op; AFQMC_ERR_INVALID on NULL or unaligned pointers
+ * with n > 0 (checked on the host, before any launch).
  */
 afqmc_status afqmc_philox4x32_10(const unsigned int* ctr, unsigned long long seed, unsigned int* out, size_t n,
                                  void* stream);

@@ -1,6 +1,7 @@
 // C ABI entry points of the k-point AFQMC library (declared in include/afqmc_kp.h).
 // Argument validation, device memory ownership and dispatch to the FP64 or the
 // tensor-core (mixed) kernels.  No exception crosses this file's boundary.
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -83,6 +84,12 @@ bool valid_desc(const afqmc_kp_desc* d) {
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Complex arrays are read and written as 16-byte (re, im) vectors: NULL or 16-byte aligned.
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool al16(const void* a, const void* b, const void* c = nullptr, const void* d = nullptr) {
+  return al16(a) && al16(b) && al16(c) && al16(d);
+}
 
 // One fused step (afqmc_kp_step after validation); keeps the stored-Green bookkeeping.
 cudaError_t step_impl(afqmc_kp* h, void* phi, const double* x, double* weight, void* eloc, void* logdet, int do_qr,
@@ -367,7 +374,7 @@ afqmc_status afqmc_kp_set_one_body(afqmc_kp_t h, const void* h1, void* stream) {
 }
 
 afqmc_status afqmc_kp_force_bias(afqmc_kp_t h, const void* phi, void* xbar, void* stream) {
-  if (!h || !phi || !xbar) return AFQMC_ERR_INVALID;
+  if (!h || !phi || !xbar || !al16(phi, xbar)) return AFQMC_ERR_INVALID;
   h->launches = 0;
   h->green_valid = false;
   cudaStream_t st = as_stream(stream);
@@ -384,7 +391,7 @@ afqmc_status afqmc_kp_force_bias(afqmc_kp_t h, const void* phi, void* xbar, void
 
 afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double* weight, void* logdet,
                                 int do_qr, void* stream) {
-  if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1)) return AFQMC_ERR_INVALID;
+  if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || !al16(phi, logdet)) return AFQMC_ERR_INVALID;
   h->launches = 0;
   h->green_valid = false;
   cudaStream_t st = as_stream(stream);
@@ -398,14 +405,15 @@ afqmc_status afqmc_kp_propagate(afqmc_kp_t h, void* phi, const double* x, double
 
 afqmc_status afqmc_kp_step(afqmc_kp_t h, void* phi, const double* x, double* weight, void* eloc, void* logdet,
                            int do_qr, int flags, void* stream) {
-  if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
+  if (!h || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN) ||
+      !al16(phi, eloc, logdet))
     return AFQMC_ERR_INVALID;
   h->launches = 0;
   return from_cuda(step_impl(h, phi, x, weight, eloc, logdet, do_qr, flags, as_stream(stream)));
 }
 
 afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void* stream) {
-  if (!h || !phi) return AFQMC_ERR_INVALID;
+  if (!h || !phi || !al16(phi, logdet)) return AFQMC_ERR_INVALID;
   h->launches = 0;
   h->green_valid = false;
   cudaStream_t st = as_stream(stream);
@@ -418,7 +426,7 @@ afqmc_status afqmc_kp_orthonormalise(afqmc_kp_t h, void* phi, void* logdet, void
 }
 
 afqmc_status afqmc_kp_local_energy(afqmc_kp_t h, const void* phi, void* eloc, void* stream) {
-  if (!h || !phi || !eloc) return AFQMC_ERR_INVALID;
+  if (!h || !phi || !eloc || !al16(phi, eloc)) return AFQMC_ERR_INVALID;
   h->launches = 0;
   h->green_valid = false;
   cudaStream_t st = as_stream(stream);
@@ -432,7 +440,7 @@ afqmc_status afqmc_kp_local_energy(afqmc_kp_t h, const void* phi, void* eloc, vo
 
 afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const void* grad_e, void* grad_phi,
                                             void* grad_h1, void* stream) {
-  if (!h || !phi || !grad_e) return AFQMC_ERR_INVALID;
+  if (!h || !phi || !grad_e || !al16(phi, grad_e, grad_phi, grad_h1)) return AFQMC_ERR_INVALID;
   h->launches = 0;
   h->green_valid = false;
   cudaStream_t st = as_stream(stream);
@@ -500,6 +508,8 @@ afqmc_status afqmc_kp_stage_times(afqmc_kp_t h, double* ms, int* count) {
 afqmc_status afqmc_philox4x32_10(const unsigned int* ctr, unsigned long long seed, unsigned int* out, size_t n,
                                  void* stream) {
   if (n > 0 && (!ctr || !out)) return AFQMC_ERR_INVALID;
+  // rows of four words are moved as 16-byte vectors
+  if (n > 0 && ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15u)) return AFQMC_ERR_INVALID;
   return from_cuda(rng::philox(ctr, seed, out, n, as_stream(stream)));
 }
 
@@ -512,7 +522,7 @@ afqmc_status afqmc_kp_fields(afqmc_kp_t h, unsigned long long seed, unsigned lon
 
 afqmc_status afqmc_kp_comb(afqmc_kp_t h, void* phi, double* weight, unsigned long long seed,
                            const unsigned long long* counter, int* idx, void* stream) {
-  if (!h || !phi || !weight || !counter) return AFQMC_ERR_INVALID;
+  if (!h || !phi || !weight || !counter || !al16(phi)) return AFQMC_ERR_INVALID;
   if (rng::comb_smem_bytes(h->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
   h->launches = 0;
   h->green_valid = false;
@@ -524,7 +534,8 @@ afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, 
                             int flags, int comb, unsigned long long seed, unsigned long long* counter, int* idx,
                             void* stream) {
   if (!h || !phi || !weight || !x || !eloc_hist || !counter || !block_args_ok(nsteps, qr_period, energy_period, flags,
-                                                                            comb))
+                                                                            comb) ||
+      !al16(phi, eloc_hist, logdet))
     return AFQMC_ERR_INVALID;
   if (comb && rng::comb_smem_bytes(h->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
   h->launches = 0;
@@ -580,7 +591,8 @@ afqmc_status afqmc_kp_group_step(afqmc_kp_group_t g, void* const* phi, const dou
   if (!g || !phi || !x || !weight || (do_qr != 0 && do_qr != 1) || (flags & ~AFQMC_STEP_REUSE_GREEN))
     return AFQMC_ERR_INVALID;
   for (size_t i = 0; i < g->members.size(); ++i)
-    if (!phi[i] || !x[i] || !weight[i]) return AFQMC_ERR_INVALID;
+    if (!phi[i] || !x[i] || !weight[i] || !al16(phi[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr))
+      return AFQMC_ERR_INVALID;
   return from_cuda(group_run(g, as_stream(stream), [&](size_t i, afqmc_kp* h, cudaStream_t s) {
     return step_impl(h, phi[i], x[i], weight[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr, do_qr,
                      flags, s);
@@ -595,7 +607,9 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
       !block_args_ok(nsteps, qr_period, energy_period, flags, comb))
     return AFQMC_ERR_INVALID;
   for (size_t i = 0; i < g->members.size(); ++i) {
-    if (!phi[i] || !weight[i] || !x[i] || !eloc_hist[i] || !counter[i]) return AFQMC_ERR_INVALID;
+    if (!phi[i] || !weight[i] || !x[i] || !eloc_hist[i] || !counter[i] ||
+        !al16(phi[i], eloc_hist[i], logdet ? logdet[i] : nullptr))
+      return AFQMC_ERR_INVALID;
     if (comb && rng::comb_smem_bytes(g->members[i]->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
   }
   return from_cuda(group_run(g, as_stream(stream), [&](size_t i, afqmc_kp* h, cudaStream_t s) {

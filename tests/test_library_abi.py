@@ -74,6 +74,8 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.afqmc_kp_block(None, None, None, None, None, None, None, 4, 2, 1, 0, 1, 1, None, None, None) == 1
     assert lib.afqmc_philox4x32_10(None, 1, None, 5, None) == 1
     assert lib.afqmc_philox4x32_10(None, 1, None, 0, None) == 0          # n = 0: nothing to do
+    assert lib.afqmc_philox4x32_10(vp(4096 + 4), 1, vp(4096), 1, None) == 1   # unaligned rows refused
+    assert lib.afqmc_philox4x32_10(vp(4096), 1, vp(4096 + 8), 1, None) == 1
     out = vp()
     assert lib.afqmc_kp_group_create(None, 1, ctypes.byref(out)) == 1
     arr = (vp * 2)(None, None)
