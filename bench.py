@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 import gen  # noqa: E402
 
-METRIC = "walker-steps/s (propagate+E_L)"
+METRIC = "walker-steps/s (propagate+E_L) mixed vs FP64 at stated error; % roofline"
 UNIT = "walker-steps/s"
 QR_PERIOD = 5
 PAPER_BLOCK_STEPS = 20      # a block: 20 propagation steps, one energy, one orthogonalisation (Sec. 3.1)
