@@ -94,3 +94,30 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
     d.M, d.nchol = 8, 0
     assert lib.afqmc_dense_create(ctypes.byref(d), buf, buf, buf, None, ctypes.byref(out)) == 1   # no vectors
     assert lib.afqmc_dense_create(None, buf, buf, buf, None, ctypes.byref(out)) == 1
+
+
+def test_binding_tables_follow_the_header_enums():
+    """The binding's stage and GEMM name tables index the header's enums in order."""
+    import paper_2003_09468_gb300 as pkg
+    txt = open(os.path.join(ROOT, "include", "afqmc_kp.h")).read()
+    st = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"\bAFQMC_STAGE_(\w+)\s*=\s*(\d+)", txt)}
+    nst = int(re.search(r"\bAFQMC_NSTAGES\s*=\s*(\d+)", txt).group(1))
+    assert len(pkg.KPointAFQMC.STAGES) == nst == len(st)
+    for name, i in st.items():
+        assert pkg.KPointAFQMC.STAGES[i] == name, (name, i)
+    gm = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"\bAFQMC_GEMM_(\w+)\s*=\s*(\d+)", txt)}
+    ng = int(re.search(r"\bAFQMC_NGEMMS\s*=\s*(\d+)", txt).group(1))
+    assert len(pkg.KPointAFQMC.GEMMS) == ng == len(gm)
+    for name, i in gm.items():
+        assert pkg.KPointAFQMC.GEMMS[i] == name, (name, i)
+
+
+def test_every_exported_symbol_is_declared(lib):
+    """No entry point leaves the library without a declaration (and its documentation) in the header."""
+    import subprocess
+    import paper_2003_09468_gb300 as pkg
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("nm unavailable")
+    exported = {l.split()[-1] for l in out.stdout.splitlines() if l.split() and l.split()[-1].startswith("afqmc_")}
+    assert exported and exported <= declared_symbols(), exported - declared_symbols()
