@@ -374,6 +374,8 @@ def run_dense(args):
     """The standard (dense) representation of a two-cell Gamma-point supercell (M = 52, N = 8,
     416 real vectors, 64 walkers) against the same cells in the k-point representation
     (1x1x2 grid, M = 26, n = 4, 208 vectors per Q), the comparison of Sec. 3.1 on one GPU."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return   # one GPU's comparison: the other ranks of a multi-GPU launch have no work
     import torch
     from paper_2003_09468_gb300 import DenseAFQMC, KPointAFQMC
 
