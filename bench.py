@@ -2,11 +2,16 @@
 """Walker-step throughput of the k-point phaseless AFQMC hot path on GB300.
 
 One step = one hybrid propagation of every walker (Green's function, force
-bias, vHS, 6-term Taylor exp(V) with both one-body halves, weight update,
-Householder QR every 5th step) followed by the local energy (E1 + Coulomb +
-exchange) of every walker, for the 3x3x3 diamond-sized synthetic system
-(M = 26 orbitals per k, 4 occupied per k per spin, 208 Cholesky vectors per Q,
-64 walkers per GPU).  Prints one JSON line.
+bias, vHS, 6-term Taylor exp(V) with both one-body halves, weight update, a
+re-orthonormalisation every 5th step) followed by the local energy (E1 +
+Coulomb + exchange) of every walker, for the 3x3x3 diamond-sized synthetic
+system (M = 26 orbitals per k, 4 occupied per k per spin, 208 Cholesky vectors
+per Q, 64 walkers per GPU, walkers seeded near the trial).  The K timed steps
+are taken in five windows that each restart from the seeded walkers; the
+headline is the median window.  The line is marked invalid (and the exit code
+is 1) if the library's sticky device flags report a fault, a bounded wait that
+gave up or a vHS entry out of range, or if no walker is alive afterwards.
+Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
@@ -37,6 +42,13 @@ UNIT = "walker-steps/s"
 QR_PERIOD = 5
 PAPER_BLOCK_STEPS = 20      # a block: 20 propagation steps, one energy, one orthogonalisation (Sec. 3.1)
 BLOCK_SEED = 0x2003094680000001
+WINDOWS = 5                 # timed windows of `steps` steps each; the headline is their median
+DRIFT_STEPS = 10            # trajectory length of the drift report (QR every QR_PERIOD)
+FP64_STEPS = 3              # timed steps of the FP64 comparison arm
+STATUS_NAMES = {0: "ok", 1: "invalid", 2: "oom", 3: "cuda", 4: "singular", 5: "timeout", 6: "vhs-range"}
+# the task's bars for the mixed path (per call on the same inputs)
+BARS_MIXED = {"E_L_ha_per_cell": 1e-5, "force_bias_rel": 1e-6, "phi_rel": 1e-6, "weight_rel": 1e-5,
+              "logdet_abs": 1e-5}
 WORKLOADS = {
     "diamond-3x3x3": gen.DIAMOND_3x3x3,
     "small-2x2x2": gen.SMALL_2x2x2,
@@ -254,7 +266,8 @@ class Clocks:
 # CPU oracle timing (test infrastructure; used only for cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 class OracleStepper:
-    """The FP64 CPU oracle, built once for a workload; times single walker-steps."""
+    """The FP64 CPU oracle, built once for a workload; times single walker-steps and follows
+    sampled walkers through the same steps the GPU takes."""
 
     def __init__(self, spec):
         from oracle import afqmc_kp as ok
@@ -262,13 +275,16 @@ class OracleStepper:
         self.spec = spec
         self.osys = ok.System(spec.grid, gen.cholesky(spec), gen.one_body(spec), gen.trial(spec), spec.dt)
 
+    def walker(self, walker_index: int = 0):
+        return gen.near_trial_walkers(self.spec, 1, first=walker_index)[0]
+
     def seconds(self, walker_index: int = 0, step: int = 0) -> float:
         return self.run(walker_index, step)[0]
 
     def run(self, walker_index: int = 0, step: int = 0):
         """(seconds, propagated walker, weight for w = 1, (E1, EC, EX)) of one walker-step."""
         spec, ok = self.spec, self.ok
-        phi = gen.walkers(spec, 1, first=walker_index)[0]
+        phi = self.walker(walker_index)
         x = gen.fields(spec, step, 1, first=walker_index)[0]
         t0 = time.perf_counter()
         phi_new, w_new, _, _, _ = ok.propagate_walker(self.osys, phi, x, 1.0)
@@ -278,37 +294,95 @@ class OracleStepper:
     def seeded(self, walker_index: int = 0):
         """(E1, EC, EX) and the force bias of a seeded walker as generated (untimed)."""
         ok = self.ok
-        phi = gen.walkers(self.spec, 1, first=walker_index)[0]
+        phi = self.walker(walker_index)
         Ghs = [ok.green_half(self.osys, phi[s])[0] for s in range(2)]
         return np.array(ok.local_energy(self.osys, phi)), ok.force_bias(self.osys, ok.cholesky_trace(self.osys, Ghs))
 
-    def ec_sensitivity(self, phi, reps: int = 3, eps: float = 2.0 ** -22):
-        """Largest change of E_C per cell over `reps` draws of a random relative perturbation
-        eps of every Green's-function entry (the rounding of a 22-bit operand), FP64 throughout:
-        how far the exact energy of this walker moves under the split format's own rounding."""
+    def trajectory(self, walker_index: int, nsteps: int, qr_period: int, keep=()):
+        """{step: (walker, weight, log det per spin, (E1, EC, EX))} after the steps listed in
+        `keep` (1-based), for the seeded walker with the fields of steps 0 .. nsteps-1 and a QR
+        after every qr_period-th step (untimed)."""
+        ok, spec = self.ok, self.spec
+        phi, w = self.walker(walker_index), 1.0
+        out = {}
+        for s in range(nsteps):
+            x = gen.fields(spec, s, 1, first=walker_index)[0]
+            phi, w, _, _, _ = ok.propagate_walker(self.osys, phi, x, w)
+            if (s + 1) % qr_period == 0:
+                phi = np.stack([ok.orthonormalise(phi[sp]) for sp in range(2)])
+            if s + 1 in keep:
+                ld = np.array([ok.log_det(ok.overlap(self.osys, phi[sp])) for sp in range(2)])
+                out[s + 1] = (phi.copy(), w, ld, np.array(ok.local_energy(self.osys, phi)))
+        return out
+
+    def force_bias_of(self, phi):
         ok = self.ok
-        rng = np.random.default_rng(1)
         Ghs = [ok.green_half(self.osys, phi[s])[0] for s in range(2)]
-
-        def ec(G):
-            X = ok.cholesky_trace(self.osys, G)
-            return 0.5 * np.sum(X * X[self.osys.minus])
-        e0 = ec(Ghs)
-        worst = 0.0
-        for _ in range(reps):
-            pert = [G * (1 + eps * (rng.standard_normal(G.shape) + 1j * rng.standard_normal(G.shape))) for G in Ghs]
-            worst = max(worst, abs(ec(pert) - e0) / self.spec.nk)
-        return worst
-
-    def energy_logdet(self, phi):
-        """(E1, EC, EX) and the per-spin log det of a given walker (untimed)."""
-        ok = self.ok
-        return np.array(ok.local_energy(self.osys, phi)), np.array([ok.log_det(ok.overlap(self.osys, phi[s]))
-                                                                    for s in range(2)])
+        return ok.force_bias(self.osys, ok.cholesky_trace(self.osys, Ghs))
 
 
 def cpu_cores() -> int:
     return os.cpu_count() or 1
+
+
+def workload_config(spec, workload, precision, world):
+    """The `config` object of a k-point workload's line (the same for both arms)."""
+    return {"workload": workload, "grid": list(spec.grid), "M": spec.M, "nocc": spec.nocc,
+            "nchol": spec.nchol, "walkers_per_gpu": spec.nwalkers, "taylor_order": 6,
+            "qr_period": QR_PERIOD, "precision": precision, "parallelism": f"replicas x{world}",
+            "walkers": "near-trial: orthonormalised trial + 0.1 relative complex-normal noise per column",
+            "l2": "inputs larger than L2 (Cholesky tensor alone exceeds 129 MB)"}
+
+
+def parity_report(stepper, gpu_seeded, gpu_track, oracle_step, precision):
+    """Walker 0 of the GPU run against the oracle, at the task's bars.
+
+    seeded   E_L and force bias of the seeded walker (per call, identical inputs);
+    step_1   the walker, weight, log det and E_L after the first fused step, against the
+             oracle's step from the same walker with the same fields;
+    drift    the same after DRIFT_STEPS steps (QR every QR_PERIOD) against the oracle's own
+             trajectory, and the force bias of the GPU's final walker against the oracle
+             evaluated on that walker."""
+    nk = stepper.spec.nk
+    mixed = precision == "mixed"
+    bars = BARS_MIXED if mixed else {k: 1e-10 for k in BARS_MIXED}
+    e_seed, xb_seed = stepper.seeded(0)
+    es_g, xbs_g = gpu_seeded
+    seeded_err = [float(abs(es_g[j] - e_seed[j]) / nk) for j in range(3)]
+    xb_err = float(np.linalg.norm(xbs_g - xb_seed) / np.linalg.norm(xb_seed))
+    e_bar = [bars["E_L_ha_per_cell"] if mixed else bars["E_L_ha_per_cell"] * abs(e_seed[j]) / nk
+             for j in range(3)]
+    seeded = {"E_L_err_ha_per_cell": seeded_err, "E_L_ha_per_cell": [float(e_seed[j].real / nk) for j in range(3)],
+              "force_bias_rel_err": xb_err,
+              "pass": bool(all(seeded_err[j] < e_bar[j] for j in range(3)) and xb_err < bars["force_bias_rel"])}
+
+    def compare(gpu, ref):
+        phi_g, w_g, e_g, ld_g = gpu
+        phi_r, w_r, ld_r, e_r = ref
+        row = {"phi_rel_err": float(np.linalg.norm(phi_g - phi_r) / np.linalg.norm(phi_r)),
+               "weight": w_g, "weight_rel_err": float(abs(w_g - w_r) / abs(w_r)) if w_r else None,
+               "logdet_abs_err": float(np.max(np.abs(ld_g.real - ld_r.real))),
+               "E_L_err_ha_per_cell": [float(abs(e_g[j] - e_r[j]) / nk) for j in range(3)],
+               "E_L_ha_per_cell": [float(e_r[j].real / nk) for j in range(3)]}
+        eb = [bars["E_L_ha_per_cell"] if mixed else bars["E_L_ha_per_cell"] * abs(e_r[j]) / nk for j in range(3)]
+        row["pass"] = bool(w_r > 0 and row["phi_rel_err"] < bars["phi_rel"]
+                           and row["weight_rel_err"] < bars["weight_rel"]
+                           and row["logdet_abs_err"] < bars["logdet_abs"]
+                           and all(row["E_L_err_ha_per_cell"][j] < eb[j] for j in range(3)))
+        return row
+
+    traj = stepper.trajectory(0, DRIFT_STEPS, QR_PERIOD, keep=(1, DRIFT_STEPS))
+    step1 = compare(gpu_track[1], traj[1])
+    drift = compare(gpu_track[DRIFT_STEPS], traj[DRIFT_STEPS])
+    xb_ref = stepper.force_bias_of(gpu_track[DRIFT_STEPS][0])
+    drift["force_bias_rel_err_on_gpu_walker"] = float(np.linalg.norm(gpu_track["xbar_end"] - xb_ref)
+                                                      / np.linalg.norm(xb_ref))
+    drift["pass"] = bool(drift["pass"] and drift["force_bias_rel_err_on_gpu_walker"] < bars["force_bias_rel"])
+    drift["steps"] = DRIFT_STEPS
+    phi_ref, w_ref, e_ref = oracle_step
+    return {"walker": 0, "walkers": "near-trial (seeded)", "bars": bars, "seeded": seeded, "step_1": step1,
+            "drift": drift, "device_flags_of_the_parity_run": STATUS_NAMES.get(gpu_track.get("status", 0), "?"),
+            "pass": bool(seeded["pass"] and step1["pass"] and drift["pass"])}
 
 
 def run_reference(args, spec, wl_name):
@@ -325,10 +399,11 @@ def run_reference(args, spec, wl_name):
     value = 1.0 / mean_s
     cb = {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
           "sample": f"1 walker x 1 step (propagate + E_L) of {wl_name} per timed step, FP64 NumPy"}
+    config = workload_config(spec, wl_name, "mixed" if args.precision in ("auto", "mixed") else "fp64", args.gpus)
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": wl_name, "walkers": 1},
+                      "data": "synthetic", "config": config,
                       "cpu_baseline": cb,
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -346,7 +421,7 @@ def dense_oracle_seconds(nwalk, step):
     from oracle import standard as so
     ds = gen.DENSE_1x1x2
     osys = so.StandardSystem(gen.dense_cholesky(ds), gen.dense_one_body(ds), gen.dense_trial(ds), ds.dt)
-    phis, xo = gen.dense_walkers(ds, nwalk), gen.dense_fields(ds, step, nwalk)
+    phis, xo = gen.dense_near_trial_walkers(ds, nwalk), gen.dense_fields(ds, step, nwalk)
     t0 = time.perf_counter()
     for i in range(nwalk):
         pn, _, _, _ = so.propagate_walker(osys, phis[i], xo[i], 1.0)
@@ -414,7 +489,7 @@ def run_dense(args):
 
     dsys = DenseAFQMC(gen.dense_cholesky(ds), gen.dense_one_body(ds), gen.dense_trial(ds), ds.nwalkers, ds.dt,
                       precision="mixed", hermitian=True)
-    dphi = torch.from_numpy(gen.dense_walkers(ds)).to(dev)
+    dphi = torch.from_numpy(gen.dense_near_trial_walkers(ds)).to(dev)
     dxs = [torch.from_numpy(handle_fields(gen.dense_fields(ds, i))).to(dev) for i in range(nsteps)]
     clocks = Clocks(0)
     clocks.start()
@@ -423,7 +498,7 @@ def run_dense(args):
     dsys.close()
     ksys = KPointAFQMC(ks.grid, gen.cholesky(ks), gen.one_body(ks), gen.trial(ks), ks.nwalkers, ks.dt,
                        precision="mixed")
-    kphi = torch.from_numpy(gen.walkers(ks)).to(dev)
+    kphi = torch.from_numpy(gen.near_trial_walkers(ks)).to(dev)
     kxs = [torch.from_numpy(gen.fields(ks, i)).to(dev) for i in range(nsteps)]
     ms_k, _, st_k, fin_k = timed_steps(ksys, kphi, kxs)
     ksys.close()
@@ -477,7 +552,7 @@ def run_group(args):
     nsteps = args.warmup + args.steps
     xs = [[torch.from_numpy(gen.fields(s, i, s.nwalkers, first=rank * s.nwalkers)).to(dev) for s in specs]
           for i in range(nsteps)]
-    phi0 = [torch.from_numpy(gen.walkers(s, s.nwalkers, first=rank * s.nwalkers)).to(dev) for s in specs]
+    phi0 = [torch.from_numpy(gen.near_trial_walkers(s, s.nwalkers, first=rank * s.nwalkers)).to(dev) for s in specs]
     phis = [p.clone() for p in phi0]
     ws = [torch.ones(s.nwalkers, dtype=torch.float64, device=dev) for s in specs]
     els = [torch.empty((s.nwalkers, 3), dtype=torch.complex128, device=dev) for s in specs]
@@ -640,70 +715,116 @@ def main():
     # TMA ring depth per GEMM, picked at create by the library's autotuner (timed per launch)
     autotune = sys_.gemm_tuning() if precision == "mixed" else None
 
-    # walkers and fields: independent replicas per rank (disjoint walker indices)
+    # walkers and fields: independent replicas per rank (disjoint walker indices); the walkers
+    # start near the trial, as a projection does (Sec. 2.1)
     first = rank * spec.nwalkers
-    phi0 = gen.walkers(spec, spec.nwalkers, first=first)
+    phi0 = gen.near_trial_walkers(spec, spec.nwalkers, first=first)
     nsteps = args.warmup + args.steps
-    xs = [torch.from_numpy(gen.fields(spec, i, spec.nwalkers, first=first)).to(dev) for i in range(nsteps)]
-    phi = torch.from_numpy(phi0).to(dev)
+    nfields = max(nsteps, DRIFT_STEPS)
+    xs = [torch.from_numpy(gen.fields(spec, i, spec.nwalkers, first=first)).to(dev) for i in range(nfields)]
+    phi0_d = torch.from_numpy(phi0).to(dev)
+    phi = phi0_d.clone()
     w = torch.ones(spec.nwalkers, dtype=torch.float64, device=dev)
     eloc = torch.empty((spec.nwalkers, 3), dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream()
 
     launches = [0]
 
-    def step(i, x):
-        # one fused call: propagate, then the local energy of the new walkers; the
-        # Green's function formed at the end of a step serves the next step's force bias
-        sys_.step(phi, x, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=True)
-        launches[0] += sys_.launch_count()
+    def step(i, x, count=False):
+        # one fused call: propagate, then the local energy of the new walkers; the Green's
+        # function formed at the end of a step serves the next step's force bias (the first
+        # step after a restart forms it afresh)
+        sys_.step(phi, x, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
+        if count:
+            launches[0] += sys_.launch_count()
 
-    for i in range(args.warmup):
-        step(i, xs[i])
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+    def restart():
+        phi.copy_(phi0_d)
+        w.fill_(1.0)
+
+    # Timed windows: each restarts from the seeded walkers, takes the W warm-up steps untimed
+    # and then times exactly K steps (the same work in every window); the headline is the
+    # median window.
     clocks = Clocks(local)
+    window_ms = []
+    stages = None
+    gpu_launches = 0
     clocks.start()
-    sys_.profile(True)
-    sys_.stage_times()
-    launches[0] = 0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for i in range(args.warmup, nsteps):
-        step(i, xs[i])
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    for r in range(WINDOWS):
+        restart()
+        for i in range(args.warmup):
+            step(i, xs[i])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        profile = r == WINDOWS - 1          # stage times from the last window
+        if profile:
+            sys_.profile(True)
+            sys_.stage_times()
+        launches[0] = 0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.warmup, nsteps):
+            step(i, xs[i], count=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_r = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms_r], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_r = float(t.item())
+            dist.barrier()
+        window_ms.append(ms_r)
+        if profile:
+            stages = sys_.stage_times()
+            sys_.profile(False)
+            gpu_launches = launches[0]
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    stages = sys_.stage_times()
-    sys_.profile(False)
-    gpu_launches = launches[0]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
     torch.cuda.synchronize()
+    ms = statistics.median(window_ms)
     value = world * spec.nwalkers * args.steps / (ms * 1e-3)
+    windows = {"count": WINDOWS, "ms": [round(v, 4) for v in window_ms],
+               "walker_steps_per_s": [world * spec.nwalkers * args.steps / (v * 1e-3) for v in window_ms],
+               "headline": "median window; each window restarts from the seeded walkers, takes the warm-up "
+                           "steps untimed and times exactly `steps` steps"}
+
+    # validity of the timed steps: the library's sticky device flags (CUDA fault, a bounded
+    # wait that gave up, a vHS entry beyond the split format, singular walkers) and a live
+    # population with a finite mixed energy estimate
+    status, n_sing = sys_.last_error()
     eloc_h = eloc.cpu().numpy()
+    w_h = w.cpu().numpy()
     finite = bool(np.all(np.isfinite(eloc_h)))
-    # the block's mixed energy estimate over every rank's walkers (the one cross-rank
-    # exchange of the method; untimed, after the timed steps)
     from paper_2003_09468_gb300.replicas import block_energy
     e_blk, w_blk = block_energy(eloc, w)
-    block = {"E_mixed_ha_per_cell": e_blk.real / spec.nk, "weight_sum": w_blk, "ranks": world}
+    e_cell = e_blk.real / spec.nk
+    block = {"E_mixed_ha_per_cell": e_cell, "weight_sum": w_blk, "ranks": world,
+             "live_walkers": int(np.sum(w_h > 0)), "walkers": int(w_h.size),
+             "log10_weight_range": [float(np.log10(w_h[w_h > 0].min())), float(np.log10(w_h.max()))]
+             if np.any(w_h > 0) else None}
+    flags = {"status": int(status), "status_name": STATUS_NAMES.get(int(status), "?"), "singular_walkers": int(n_sing)}
+    invalid = []
+    if status in (3, 5, 6):
+        invalid.append(f"device flag: {flags['status_name']}")
+    if not (np.isfinite(w_blk) and w_blk > 0):
+        invalid.append("no live walker after the timed steps")
+    if not np.isfinite(e_cell):
+        invalid.append("mixed energy estimate not finite")
+    if not finite:
+        invalid.append("non-finite local energies")
 
-    # end-to-end through the public API with pinned host buffers
+    # end-to-end through the public API with pinned host buffers: each step's fields copied in
+    # from the host, each step's energies and weights copied back
     e2e = None
     if not args.no_e2e:
         xs_host = [x.cpu().pin_memory() for x in xs]
         e_host = torch.empty((spec.nwalkers, 3), dtype=torch.complex128).pin_memory()
         w_host = torch.empty(spec.nwalkers, dtype=torch.float64).pin_memory()
         xdev = torch.empty_like(xs[0])
-        phi.copy_(torch.from_numpy(phi0).to(dev))
-        w.fill_(1.0)
+        restart()
+        for i in range(args.warmup):
+            step(i, xs[i])
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -732,8 +853,7 @@ def main():
         xb = torch.empty_like(xs[0])
         ehb = torch.empty((1, spec.nwalkers, 3), dtype=torch.complex128, device=dev)
         counter = torch.tensor([1 << 20], dtype=torch.int64, device=dev)
-        phi.copy_(torch.from_numpy(phi0).to(dev))
-        w.fill_(1.0)
+        restart()
 
         def blk():
             sys_.block(phi, w, xb, ehb, counter, BLOCK_SEED + rank, nsteps=nb, qr_period=nb, energy_period=nb,
@@ -747,7 +867,7 @@ def main():
             blk()
         g.replay()
         torch.cuda.synchronize()
-        reps = 3
+        reps = 5
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(stream)
         for _ in range(reps):
@@ -760,11 +880,14 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_blk = float(t.item())
         eb = ehb[0].cpu().numpy()
+        wb = w.cpu().numpy()
+        bst, _ = sys_.last_error()
         paper_block = {"ms_per_block": ms_blk, "walker_steps_per_s": world * spec.nwalkers * nb / (ms_blk * 1e-3),
                        "unit": UNIT, "steps_per_block": nb, "energy_evaluations": 1, "qr": 1, "comb": True,
                        "fields": "Philox4x32-10 + Box-Muller on the device", "cuda_graph": True,
                        "replays_timed": reps, "gpu_launches_per_block": blk_launches,
-                       "finite": bool(np.all(np.isfinite(eb)))}
+                       "finite": bool(np.all(np.isfinite(eb))), "weight_after_comb": float(wb[0]),
+                       "device_flags": STATUS_NAMES.get(int(bst), "?")}
         del g
 
     if rank != 0:
@@ -772,22 +895,28 @@ def main():
             dist.destroy_process_group()
         return
 
-    # the first step of walker 0 from the seeded walkers, for the parity report next to the
-    # oracle's timed walker-step (untimed; the walker batch is restarted)
-    gpu_first = None
+    # GPU walker 0 after one step and after DRIFT_STEPS steps (QR every QR_PERIOD), from the
+    # seeded walkers with the fields of steps 0, 1, ...: the parity report's GPU side (untimed)
+    gpu_track = {}
     gpu_seeded = None
     if not args.no_cpu_baseline and world == 1:
-        phi.copy_(torch.from_numpy(phi0).to(dev))
-        # per-call parity on the seeded inputs: the energy and force bias of the seeded walkers
+        restart()
         e_s = sys_.local_energy(phi)
         xb_s = sys_.force_bias(phi)
         torch.cuda.synchronize()
         gpu_seeded = (e_s[0].cpu().numpy(), xb_s[0].cpu().numpy())
-        w.fill_(1.0)
         ld = torch.empty((spec.nwalkers, 2), dtype=torch.complex128, device=dev)
-        sys_.step(phi, xs[0], w, eloc, logdet=ld, do_qr=False, reuse=False)
+        for i in range(DRIFT_STEPS):
+            sys_.step(phi, xs[i], w, eloc, logdet=ld, do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
+            if i + 1 in (1, DRIFT_STEPS):
+                torch.cuda.synchronize()
+                gpu_track[i + 1] = (phi[0].cpu().numpy(), float(w[0].item()), eloc[0].cpu().numpy(),
+                                    ld[0].cpu().numpy())
+        xb_end = sys_.force_bias(phi)
         torch.cuda.synchronize()
-        gpu_first = (phi[0].cpu().numpy(), float(w[0].item()), eloc[0].cpu().numpy(), ld[0].cpu().numpy())
+        gpu_track["xbar_end"] = xb_end[0].cpu().numpy()
+        tst, _ = sys_.last_error()
+        gpu_track["status"] = int(tst)
 
     # derived rates from the per-stage times: propagation (with the Green's function that the
     # fused step forms for the next step) and the local energy
@@ -796,7 +925,7 @@ def main():
     en_ms = sum(stages[k][0] for k in ("energy", "exchange")) / steps_t
     rates = {"propagate_only": spec.nwalkers * world / (prop_ms * 1e-3) if prop_ms > 0 else None,
              "local_energy_only": spec.nwalkers * world / (en_ms * 1e-3) if en_ms > 0 else None,
-             "unit": UNIT, "source": "per-stage CUDA-event times of the timed steps"}
+             "unit": UNIT, "source": "per-stage CUDA-event times of the last timed window"}
 
     peaks, peaks_kind = load_peaks()
     rooflines = {}
@@ -825,7 +954,7 @@ def main():
         note = f"dense f16/bf16 tensor, sustained (kernel timed inside the step), {peaks_kind}"
         put("taylor", "tensor", taylor_term_flops(spec), tensor_peak, "TFLOP/s",
             note + "; one Taylor-term GEMM per launch, algorithmic flops (the 3-product fp16 split "
-                   "issues 3x as many)")
+                   "issues up to 3x as many)")
         put("exchange", "tensor", exchange_precontracted_flops(spec), tensor_peak, "TFLOP/s",
             note + "; algorithmic flops")
         put("vhs", "hbm", vhs_bytes(spec), peaks.get("hbm_gbs", 6800.0), "GB/s",
@@ -855,7 +984,7 @@ def main():
     # same system), timed with CUDA events after one warm-up call
     adjoint = None
     g_up = torch.from_numpy(gen.upstream(spec)).to(dev)
-    phi.copy_(torch.from_numpy(phi0).to(dev))
+    restart()
 
     def time_backward(s_, reps, profile=False):
         s_.local_energy_backward(phi, g_up)
@@ -900,20 +1029,22 @@ def main():
         del sys_
         torch.cuda.synchronize()
         s64 = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
-        phi.copy_(torch.from_numpy(phi0).to(dev))
-        w.fill_(1.0)
-        step_fn = lambda i, x: s64.step(phi, x, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=True)
+        restart()
+        step_fn = lambda i, x: s64.step(phi, x, w, eloc, do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
         step_fn(0, xs[0])
         torch.cuda.synchronize()
+        n64 = max(FP64_STEPS, 1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step_fn(1, xs[min(1, nsteps - 1)])
+        for i in range(1, 1 + n64):
+            step_fn(i, xs[i % nfields])
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        fp64_cmp = {"value": spec.nwalkers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": 1,
+        ms64 = e0.elapsed_time(e1) / n64
+        fp64_cmp = {"value": spec.nwalkers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": n64,
                     "speedup_mixed_over_fp64": value / (spec.nwalkers / (ms64 * 1e-3))}
         if adjoint is not None:
+            restart()
             ms_adj64, _, _ = time_backward(s64, 1)
             adjoint["fp64_ms_per_call"] = ms_adj64
             adjoint["speedup_mixed_over_fp64"] = ms_adj64 / adjoint["ms_per_call"]
@@ -928,71 +1059,26 @@ def main():
         cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                         "sample": f"1 walker x 1 step (propagate + E_L) of {args.workload}, FP64 NumPy, "
                                   f"{t:.1f} s"}
-        if gpu_first is not None:
-            phi_g, w_g, e_g, ld_g = gpu_first
-            e_own, ld_own = stepper.energy_logdet(phi_g)
-            e_seed, xb_seed = stepper.seeded(0)
-            es_g, xbs_g = gpu_seeded
-            sens = stepper.ec_sensitivity(phi_g)
-            seeded_err = [float(abs(es_g[j] - e_seed[j]) / spec.nk) for j in range(3)]
-            xb_err = float(np.linalg.norm(xbs_g - xb_seed) / np.linalg.norm(xb_seed))
-            parity = {
-                "walker": 0, "step": "first step from the seeded walkers, fields of step 0",
-                # the gate: per call on the seeded inputs (energy and force bias of seeded walker 0)
-                "seeded": {"E_L_err_ha_per_cell": seeded_err,
-                           "E_L_ha_per_cell": [float(abs(e_seed[j]) / spec.nk) for j in range(3)],
-                           "force_bias_rel_err": xb_err,
-                           "bar": {"E_L_ha_per_cell": 1e-5, "force_bias_rel": 1e-6} if precision == "mixed"
-                           else {"all_rel": 1e-10}},
-                # the kernels on the walker the GPU propagated, against the oracle evaluated on that
-                # same walker; its overlap is far worse conditioned than the seeded one, and the
-                # bar is three times the change of the exact E_C under the 22-bit rounding of the
-                # Green's function (FP64 oracle, 3 random draws)
-                "kernel": {"E_L_err_ha_per_cell": [float(abs(e_g[j] - e_own[j]) / spec.nk) for j in range(3)],
-                           "E_L_parts": ["E1", "EC", "EX"],
-                           "E_L_ha_per_cell": [float(abs(e_own[j]) / spec.nk) for j in range(3)],
-                           "EC_change_under_2^-22_Gh_rounding_ha_per_cell": sens,
-                           "logdet_abs_err": float(np.max(np.abs(ld_g.real - ld_own.real)))},
-                # the step: the propagated walker and weight against the oracle's own step
-                "step_vs_oracle": {"phi_rel_err": float(np.linalg.norm(phi_g - phi_ref) / np.linalg.norm(phi_ref)),
-                                   "weight_rel_err": float(abs(w_g - w_ref) / abs(w_ref)),
-                                   "E_L_diff_ha_per_cell": [float(abs(e_g[j] - e_ref[j]) / spec.nk)
-                                                            for j in range(3)],
-                                   "note": "E_L and the weight of these walkers are ill-conditioned: a "
-                                           "random 4.4e-8 relative change of the walker moves E_C and E_X "
-                                           "by ~3e-2 Ha/cell and the log det by ~2e-5 (oracle)"},
-                "tolerance": {"seeded_E_L_ha_per_cell": 1e-5, "seeded_force_bias_rel": 1e-6,
-                              "stepped_E_L_ha_per_cell": "max(1e-5, 3 x the E_C change under 2^-22 rounding of Gh)",
-                              "phi_rel": 1e-6, "logdet_abs": 1e-5}
-                if precision == "mixed" else {"all_rel": 1e-10}}
-            if precision == "mixed":
-                bar = max(1e-5, 3.0 * sens)
-                parity["kernel"]["E_L_bar_ha_per_cell"] = bar
-                parity["kernel"]["pass"] = bool(
-                    all(parity["kernel"]["E_L_err_ha_per_cell"][j] < bar for j in range(3))
-                    and parity["kernel"]["logdet_abs_err"] < 1e-5)
-                parity["seeded"]["pass"] = bool(all(v < 1e-5 for v in seeded_err) and xb_err < 1e-6)
-            else:
-                parity["seeded"]["pass"] = bool(
-                    all(seeded_err[j] <= 1e-10 * abs(e_seed[j]) / spec.nk for j in range(3)) and xb_err < 1e-10)
-            parity["pass"] = bool(parity["seeded"]["pass"] and parity["kernel"].get("pass", True))
+        if gpu_track:
+            parity = parity_report(stepper, gpu_seeded, gpu_track, (phi_ref, w_ref, e_ref), precision)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": args.workload, "grid": list(spec.grid), "M": spec.M, "nocc": spec.nocc,
-                   "nchol": spec.nchol, "walkers_per_gpu": spec.nwalkers, "taylor_order": 6,
-                   "qr_period": QR_PERIOD, "precision": precision, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (Cholesky tensor alone exceeds 129 MB)"},
+        "config": workload_config(spec, args.workload, precision, world),
         "roofline": roofline,
         "rooflines": rooflines,
         "step_roofline": step_roofline,
+        "windows": windows,
         "autotune": autotune,
         "fp64_path": fp64_cmp,
         "cpu_baseline": cpu_baseline,
         "parity": parity,
         "block_energy": block,
+        "device_flags": flags,
+        "valid": not invalid,
+        "invalid_reasons": invalid,
         "rates": rates,
         "paper_block": paper_block,
         "adjoint": adjoint,
@@ -1007,6 +1093,8 @@ def main():
         sys_.close()
     if world > 1:
         dist.destroy_process_group()
+    if invalid:
+        sys.exit(1)
 
 
 if __name__ == "__main__":

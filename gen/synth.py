@@ -17,7 +17,14 @@ Recipe (all complex normals are (a + i b)/sqrt(2) with a, b ~ N(0, 1)):
 * Trial A[k] (M x n per k-point, block diagonal in k, Sec. 2.3): the first n
   columns of the identity, or of a random unitary when ``random_trial``.
 * Walkers phi[w, s] (NM x N per spin, dense in k): complex normal matrix with
-  orthonormal columns.
+  orthonormal columns ("random" walkers, far from the trial: a stress case for
+  conditioning).
+* Near-trial walkers: the orthonormalised columns of A + eps Z / sqrt(NM), with
+  A the trial placed block-diagonally in the dense NM x N layout and Z complex
+  normal, so that every column is moved by about eps of its length (eps = 0.1
+  by default).  A projection starts from the trial (Sec. 2.1), so
+  these are the walkers a simulation actually carries: well-conditioned
+  overlaps, small phases, weights that stay positive over many steps.
 * Auxiliary fields x[w, +/-, Q, g]: real N(0, 1) (Sec. 2.1, Eq. hs).
 * Perturbation V1[k]: Hermitised complex N(0, 0.01).
 
@@ -40,6 +47,7 @@ TAG_TRIAL = 3
 TAG_WALKER = 4
 TAG_FIELD = 5
 TAG_V1 = 6
+TAG_NEAR = 7
 
 
 @dataclass(frozen=True)
@@ -167,6 +175,29 @@ def walkers(spec: SystemSpec, nw: int | None = None, first: int = 0) -> np.ndarr
     return out
 
 
+def trial_dense(spec: SystemSpec) -> np.ndarray:
+    """The trial as one dense NM x N matrix: A[k] at rows (k, p), columns (k, a)."""
+    A = trial(spec)
+    out = np.zeros((spec.NM, spec.N), dtype=np.complex128)
+    for k in range(spec.nk):
+        out[k * spec.M:(k + 1) * spec.M, k * spec.nocc:(k + 1) * spec.nocc] = A[k]
+    return out
+
+
+def near_trial_walkers(spec: SystemSpec, nw: int | None = None, first: int = 0, eps: float = 0.1) -> np.ndarray:
+    """phi[w, s, NM, N] for walkers first .. first+nw-1: orthonormal columns spanning
+    A + eps Z / sqrt(NM) (Z complex normal, its own stream per walker and spin)."""
+    nw = spec.nwalkers if nw is None else nw
+    A = trial_dense(spec)
+    eps = eps / np.sqrt(spec.NM)
+    out = np.empty((nw, 2, spec.NM, spec.N), dtype=np.complex128)
+    for i in range(nw):
+        for s in range(2):
+            Z = _cnormal(_rng(spec.seed, TAG_NEAR, first + i, s), (spec.NM, spec.N))
+            out[i, s], _ = np.linalg.qr(A + eps * Z)
+    return out
+
+
 def fields(spec: SystemSpec, step: int, nw: int | None = None, first: int = 0) -> np.ndarray:
     """x[w, +/-, Q, g] real N(0, 1) auxiliary fields for one time step."""
     nw = spec.nwalkers if nw is None else nw
@@ -268,6 +299,18 @@ def dense_walkers(spec: DenseSpec, nw: int | None = None, first: int = 0) -> np.
         for s in range(2):
             Qm, _ = np.linalg.qr(_cnormal(_rng(spec.seed, TAG_DENSE, 3, first + i, s), (spec.M, spec.N)))
             out[i, s] = Qm
+    return out
+
+
+def dense_near_trial_walkers(spec: DenseSpec, nw: int | None = None, first: int = 0, eps: float = 0.1) -> np.ndarray:
+    """phi[w, s, M, N]: orthonormal columns spanning A + eps Z / sqrt(M), Z complex normal."""
+    nw = spec.nwalkers if nw is None else nw
+    A = dense_trial(spec)
+    out = np.empty((nw, 2, spec.M, spec.N), dtype=np.complex128)
+    for i in range(nw):
+        for s in range(2):
+            Z = _cnormal(_rng(spec.seed, TAG_DENSE, 5, first + i, s), (spec.M, spec.N))
+            out[i, s], _ = np.linalg.qr(A + (eps / np.sqrt(spec.M)) * Z)
     return out
 
 

@@ -270,6 +270,23 @@ afqmc_status afqmc_kp_local_energy_backward(afqmc_kp_t h, const void* phi, const
  */
 afqmc_status afqmc_kp_last_error(afqmc_kp_t h, void* stream, int* n_singular);
 
+/*
+ * afqmc_kp_wait_selftest -- exercise the bounded device-side wait that every
+ * mbarrier wait of the tensor-core kernels uses.  The paper has no counterpart:
+ * this is a check of this library's failure handling.  A one-warp kernel
+ * initialises an mbarrier for one arrival and waits on it with a limit of
+ * limit_cycles SM clock cycles; with arrive = 1 the kernel makes the arrival
+ * itself and the wait returns at once, with arrive = 0 nothing arrives, the wait
+ * gives up after the limit and the kernel records a time-out in the handle's
+ * sticky flags (afqmc_kp_last_error then returns AFQMC_ERR_TIMEOUT).  The kernel
+ * issues no copy or MMA and holds no tensor memory, so the device stays usable.
+ *   arrive        0 or 1.
+ *   limit_cycles  1 .. 2^31 (about one second at the maximum SM clock).
+ * AFQMC_ERR_INVALID on a NULL handle or arguments out of range; AFQMC_ERR_CUDA if
+ * the launch fails.
+ */
+afqmc_status afqmc_kp_wait_selftest(afqmc_kp_t h, int arrive, long long limit_cycles, void* stream);
+
 /* Device bytes owned by the handle (static data plus workspace). */
 afqmc_status afqmc_kp_memory_bytes(afqmc_kp_t h, size_t* bytes);
 

@@ -35,6 +35,7 @@ SIGNATURES = {
     "afqmc_kp_local_energy": [_VP, _VP, _VP, _VP],
     "afqmc_kp_local_energy_backward": [_VP, _VP, _VP, _VP, _VP, _VP],
     "afqmc_kp_last_error": [_VP, _VP, ctypes.POINTER(_I)],
+    "afqmc_kp_wait_selftest": [_VP, _I, ctypes.c_longlong, _VP],
     "afqmc_kp_memory_bytes": [_VP, ctypes.POINTER(ctypes.c_size_t)],
     "afqmc_kp_launch_count": [_VP, ctypes.POINTER(_I)],
     "afqmc_kp_profile": [_VP, _I],
@@ -280,6 +281,12 @@ class KPointAFQMC:
         n = ctypes.c_int(0)
         s = self.lib.afqmc_kp_last_error(self.handle, _stream(stream), ctypes.byref(n))
         return s, n.value
+
+    def wait_selftest(self, arrive: bool, limit_cycles: int, stream=None):
+        """One bounded mbarrier wait on the device (afqmc_kp_wait_selftest); without the
+        arrival it gives up after limit_cycles and records a time-out in the sticky flags."""
+        _check(self.lib.afqmc_kp_wait_selftest(self.handle, 1 if arrive else 0, int(limit_cycles), _stream(stream)),
+               "afqmc_kp_wait_selftest")
 
     def memory_bytes(self) -> int:
         b = ctypes.c_size_t(0)

@@ -775,10 +775,12 @@ cudaError_t qr_with(afqmc_kp* h, zc* phi, zc* scratch, cudaStream_t st) {
 }
 
 // Same kernel, without a handle: nmat matrices of rows x cols, scratch of the same size.
+// Launched through cudaLaunchKernel, whose return value is this launch's own status: an
+// earlier, unrelated error stays pending for the code that caused it.
 cudaError_t qr_launch(zc* phi, zc* scratch, int rows, int cols, int nmat, cudaStream_t st) {
   size_t smem = (size_t)cols * (2 * sizeof(zc) + sizeof(double));
-  qr_kernel<<<nmat, 256, smem, st>>>(phi, scratch, rows, cols);
-  return cudaGetLastError();
+  void* args[] = {&phi, &scratch, &rows, &cols};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(qr_kernel), dim3(nmat), dim3(256), args, smem, st);
 }
 
 static cudaError_t qr(afqmc_kp* h, zc* phi, cudaStream_t st) {

@@ -47,6 +47,9 @@ cudaError_t scratch_address(zc** out) {
 
 extern "C" afqmc_status afqmc_orthonormalise_noalloc(void* phi, int rows, int cols, int nmat, void* stream) {
   if (!phi || rows < 1 || cols < 1 || cols > rows || cols > 1024 || nmat < 1) return AFQMC_ERR_INVALID;
+  // the kernel moves (re, im) pairs as 16-byte vectors: refuse an 8-byte-aligned C array here
+  // instead of letting the device fault on it
+  if (reinterpret_cast<uintptr_t>(phi) & 15u) return AFQMC_ERR_INVALID;
   if ((size_t)rows * (size_t)cols * (size_t)nmat > kScratchElems) return AFQMC_ERR_INVALID;
   zc* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);

@@ -26,3 +26,28 @@ def test_reference_arm_line(workload):
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_parity_report_gates_at_the_task_bars():
+    """The benchmark's parity block, fed the oracle's own values for the GPU side, passes with
+    zero errors; a walker moved by 1e-5 (ten times the phi bar) fails it."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import gen
+    spec = gen.SMALL_2x2x2
+    st = bench.OracleStepper(spec)
+    e0, xb0 = st.seeded(0)
+    traj = st.trajectory(0, bench.DRIFT_STEPS, bench.QR_PERIOD, keep=(1, bench.DRIFT_STEPS))
+    track = {n: (traj[n][0], traj[n][1], traj[n][3], traj[n][2]) for n in (1, bench.DRIFT_STEPS)}
+    track["xbar_end"] = st.force_bias_of(traj[bench.DRIFT_STEPS][0])
+    _, phi1, w1, e1 = st.run(0, 0)
+    rep = bench.parity_report(st, (e0, xb0), track, (phi1, w1, e1), "mixed")
+    assert rep["pass"], rep
+    assert rep["step_1"]["phi_rel_err"] == 0.0 and max(rep["drift"]["E_L_err_ha_per_cell"]) == 0.0
+    assert rep["step_1"]["weight"] > 0 and rep["drift"]["weight"] > 0
+    bad = dict(track)
+    p, w, e, ld = track[bench.DRIFT_STEPS]
+    bad[bench.DRIFT_STEPS] = (p * (1 + 1e-5), w, e, ld)
+    rep = bench.parity_report(st, (e0, xb0), bad, (phi1, w1, e1), "mixed")
+    assert not rep["drift"]["pass"] and not rep["pass"] and rep["step_1"]["pass"]

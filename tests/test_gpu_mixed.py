@@ -1,25 +1,30 @@
 """Tensor-core (mixed) path vs the FP64 CPU oracle, through the C ABI.
 
-Bars (see the design notes for the derivation of the ones the task does not fix):
+Two walker sets per system (both seeded, both from the input recipe):
+  near-trial  orthonormalised trial + small noise, the walkers a projection carries
+              (Sec. 2.1 starts from the trial): the task's bars, absolute;
+  random      orthonormalised complex Gaussians far from the trial (cond(A^dag phi) up
+              to ~50 on the small systems): a conditioning stress case with the bars
+              derived below.
+
+Bars on near-trial walkers (the task's):
   force bias      normwise relative 1e-6
-  E_L             every part within 1e-5 Ha per cell, max_w |E_gpu - E_ref| / Nk, on the
-                  diamond-sized workload the bar is stated for; the small synthetic systems
-                  carry 20-60 Ha per cell, where the bar is the FP32-class relative error
-                  2e-6 of each part (or 1e-5 Ha per cell, whichever is larger)
-  propagated phi  normwise relative 1e-6   (only the V and one-body corrections pass
-                                            through reduced precision)
-  weights         relative 1e-5; log det 1e-5 absolute (real part), the same bar since
-                  the weight is exp(Re d logdet) times the force-bias factor
-  QR              Cholesky-QR2 (tensor-core Gram and apply, FP64 Cholesky): normwise
-                  max(1e-6, 2e-7 cond(phi)) against the Householder Q (the QR with
-                  diag(R) > 0 is unique, so an orthonormal-to-u result differs by ~u cond),
-                  and orthonormal to 1e-6
-  adjoint         dE/dphi normwise within 1e-5 of the sum of the norms of the three parts'
-                  gradients (E1, E_C, E_X taken one at a time), so that cancellation between
-                  the large Coulomb and exchange gradients cannot hide or inflate an error:
-                  the exchange part comes from fp16-split tensor-core GEMMs and the Coulomb
-                  part from fp32 sums (relative error ~1e-6 each), the projection through
-                  S^-1 runs in FP64.  dE/dh uses the FP64 Green's function: 1e-10
+  E_L             every part within 1e-5 Ha per cell, max_w |E_gpu - E_ref| / Nk
+  propagated phi  normwise relative 1e-6
+  weights         relative 1e-5; log det 1e-5 absolute (real part)
+  dE/dphi         normwise relative 1e-5 against the oracle's dE/dphi itself
+  dE/dh           1e-10 (the FP64-class double-float Green's function)
+Bars on random walkers (stress):
+  E_L             the FP32-class relative error 2e-6 of each part, or 1e-5 Ha per cell,
+                  whichever is larger (these walkers carry 20-60 Ha per cell)
+  dE/dphi         1e-5 of the sum of the norms of the three parts' gradients (E1, E_C,
+                  E_X taken one at a time): the Coulomb and exchange gradients of such
+                  walkers nearly cancel, so the total's norm hides the size of the
+                  operands; both ratios are printed
+  force bias, phi, weights as above
+QR (both sets): Cholesky-QR2 against the Householder Q, normwise max(1e-6, 2e-7 cond(phi))
+(the QR with diag(R) > 0 is unique, so an orthonormal-to-u result differs by ~u cond),
+and orthonormal to 1e-6.
 """
 import numpy as np
 import pytest
@@ -61,6 +66,8 @@ def case(request):
     sys_.close()
 
 
+WALKER_SETS = {"near_trial": gen.near_trial_walkers, "random": gen.walkers}
+
 TOL_E_REL = 2e-6
 
 
@@ -68,31 +75,37 @@ def energy_error_per_cell(e, ref, nk):
     return np.abs(e - ref).max(axis=0) / nk
 
 
-def energy_bar_per_cell(ref, nk):
+def energy_bar_per_cell(ref, nk, walkers="random"):
+    if walkers == "near_trial":
+        return np.full(3, TOL_E_PER_CELL)
     return np.maximum(TOL_E_PER_CELL, TOL_E_REL * np.abs(ref).max(axis=0) / nk)
 
 
-def test_local_energy(case):
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_local_energy(case, walkers):
     spec, sys_, osys = case
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     e = host(sys_.local_energy(dev(phis)))
     ref = oracle_energy(osys, phis)
     err = energy_error_per_cell(e, ref, spec.nk)
-    assert np.all(err < energy_bar_per_cell(ref, spec.nk)), (err, energy_bar_per_cell(ref, spec.nk))
+    bar = energy_bar_per_cell(ref, spec.nk, walkers)
+    assert np.all(err < bar), (err, bar)
     assert sys_.last_error() == (0, 0)
 
 
-def test_force_bias(case):
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_force_bias(case, walkers):
     spec, sys_, osys = case
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     xb = host(sys_.force_bias(dev(phis)))
     ref = np.array([oracle_xbar(osys, p) for p in phis])
     assert rel(xb, ref) < TOL_XBAR
 
 
-def test_propagate(case):
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_propagate(case, walkers):
     spec, sys_, osys = case
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     x = gen.fields(spec, 1)
     w0 = np.linspace(0.5, 1.5, spec.nwalkers)
     phi, w = dev(phis), dev(w0)
@@ -100,16 +113,23 @@ def test_propagate(case):
     sys_.propagate(phi, dev(x), w, logdet=ld)
     phi_g, w_g, ld_g = host(phi), host(w), host(ld)
     ref = [ok.propagate_walker(osys, phis[i], x[i], w0[i]) for i in range(spec.nwalkers)]
+    w_ref = np.array([r[1] for r in ref])
     assert rel(phi_g, np.array([r[0] for r in ref])) < TOL_PHI
-    assert rel(w_g, np.array([r[1] for r in ref])) < TOL_W
+    if walkers == "near_trial":
+        # every walker's weight on its own (none is near the phaseless cut cos = 0)
+        assert np.all(w_ref > 0)
+        assert np.all(np.abs(w_g - w_ref) <= TOL_W * w_ref), np.abs(w_g - w_ref) / w_ref
+    else:
+        assert rel(w_g, w_ref) < TOL_W
     assert np.abs(ld_g.real - np.array([r[2] for r in ref]).real).max() < TOL_W
     assert sys_.last_error() == (0, 0)
 
 
-def test_orthonormalise(case):
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_orthonormalise(case, walkers):
     spec, sys_, osys = case
     rng = np.random.default_rng(4)
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     mix = rng.standard_normal((spec.N, spec.N)) + 1j * rng.standard_normal((spec.N, spec.N))
     phis = phis @ (np.eye(spec.N) + 0.3 * mix)
     phi = dev(phis)
@@ -138,61 +158,80 @@ def oracle_grads(osys, phis, g, walkers):
     return full, parts
 
 
-def grad_error(got, full, parts):
-    return np.linalg.norm(got - full) / sum(np.linalg.norm(p) for p in parts)
+def grad_errors(got, full, parts):
+    """(error relative to ||dE/dphi||, error relative to the sum of the parts' norms)."""
+    d = np.linalg.norm(got - full)
+    return d / np.linalg.norm(full), d / sum(np.linalg.norm(p) for p in parts)
 
 
-def test_backward(case):
+def check_grad(got, full, parts, walkers):
+    own, summed = grad_errors(got, full, parts)
+    print(f"dE/dphi error: {own:.3e} of ||dE/dphi||, {summed:.3e} of the sum of the parts' norms")
+    if walkers == "near_trial":
+        assert own < TOL_GRAD, (own, summed)
+    else:
+        assert summed < TOL_GRAD, (own, summed)
+
+
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_backward(case, walkers):
     spec, sys_, osys = case
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     g = gen.upstream(spec)
     gphi, gh1 = sys_.local_energy_backward(dev(phis), dev(g))
-    walkers = range(spec.nwalkers)
-    full, parts = oracle_grads(osys, phis, g, walkers)
-    ref_h1 = sum(ok.local_energy_vjp(osys, phis[w], g[w])[1] for w in walkers)
-    assert grad_error(host(gphi), full, parts) < TOL_GRAD
+    idx = range(spec.nwalkers)
+    full, parts = oracle_grads(osys, phis, g, idx)
+    ref_h1 = sum(ok.local_energy_vjp(osys, phis[w], g[w])[1] for w in idx)
+    check_grad(host(gphi), full, parts, walkers)
     assert rel(host(gh1), ref_h1) < 1e-10
     # the gradient of the total energy (every part weighted alike)
     ones = np.ones_like(g)
     gphi1, _ = sys_.local_energy_backward(dev(phis), dev(ones), want_h1=False)
-    full1, parts1 = oracle_grads(osys, phis, ones, walkers)
-    assert grad_error(host(gphi1), full1, parts1) < TOL_GRAD
+    full1, parts1 = oracle_grads(osys, phis, ones, idx)
+    check_grad(host(gphi1), full1, parts1, walkers)
 
 
-def test_backward_diamond_sampled():
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_backward_diamond_sampled(walkers):
     """The adjoint at the 3x3x3, M=26, n=4, nchol=208, 64-walker size: walker 0 against
     the oracle (the other walkers' upstream gradients are zero)."""
     spec = gen.DIAMOND_3x3x3
     sys_, osys = make(spec, "mixed")
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     g = np.zeros((spec.nwalkers, 3), dtype=np.complex128)
     g[0] = gen.upstream(spec)[0]
     gphi, _ = sys_.local_energy_backward(dev(phis), dev(g), want_h1=False)
     got = host(gphi)
     full, parts = oracle_grads(osys, phis, g, [0])
-    assert grad_error(got[:1], full, parts) < TOL_GRAD
+    check_grad(got[:1], full, parts, walkers)
     assert np.abs(got[1:]).max() == 0.0
     assert sys_.last_error() == (0, 0)
     sys_.close()
 
 
 def test_energy_invariant_under_orbital_rotation(case):
-    """E_L depends on phi only through its column space (Sec. 2.2)."""
+    """E_L depends on phi only through its column space (Sec. 2.2): the GPU energies of phi
+    and phi U agree with each other and with the oracle."""
     spec, sys_, osys = case
     rng = np.random.default_rng(8)
-    phis = gen.walkers(spec)
+    phis = gen.near_trial_walkers(spec)
     U, _ = np.linalg.qr(rng.standard_normal((spec.N, spec.N)) + 1j * rng.standard_normal((spec.N, spec.N)))
     e0 = host(sys_.local_energy(dev(phis)))
     e1 = host(sys_.local_energy(dev(phis @ U)))
-    assert np.all(energy_error_per_cell(e0, e1, spec.nk) < 2 * energy_bar_per_cell(e0, spec.nk))
+    ref = oracle_energy(osys, phis)
+    assert np.all(energy_error_per_cell(e1, ref, spec.nk) < TOL_E_PER_CELL)
+    assert np.all(energy_error_per_cell(e0, e1, spec.nk) < 2 * TOL_E_PER_CELL)
 
 
-def test_diamond_size_sampled():
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
+def test_diamond_size_sampled(walkers):
     """3x3x3 grid, M=26, n=4, nchol=208, 64 walkers: the benchmark workload in the
-    benchmark's launch configuration.  Sampled walkers against the oracle."""
+    benchmark's launch configuration.  Sampled walkers against the oracle at the task's bars
+    (the seeded random walkers meet them too; one step later they no longer can, see the
+    trajectory tests)."""
     spec = gen.DIAMOND_3x3x3
     sys_, osys = make(spec, "mixed")
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     e = host(sys_.local_energy(dev(phis)))
     xb = host(sys_.force_bias(dev(phis)))
     assert np.all(np.isfinite(e)) and np.all(np.isfinite(xb))
@@ -204,9 +243,13 @@ def test_diamond_size_sampled():
     phi, wt = dev(phis), dev(np.ones(spec.nwalkers))
     sys_.propagate(phi, dev(x), wt)
     phi_g, w_g = host(phi), host(wt)
-    pn, wn, _, _, _ = ok.propagate_walker(osys, phis[5], x[5], 1.0)
-    assert rel(phi_g[5], pn) < TOL_PHI
-    assert abs(w_g[5] - wn) < TOL_W * abs(wn)
+    # random walkers: walker 5 (the overlap of a random walker after one step has cond ~ 7000,
+    # and its weight moves by ~2e-5 under a 4e-8 relative change of the walker: walker 0's
+    # weight is not determined to 1e-5 by any 22-bit arithmetic)
+    for w in ((0, 5) if walkers == "near_trial" else (5,)):
+        pn, wn, _, _, _ = ok.propagate_walker(osys, phis[w], x[w], 1.0)
+        assert rel(phi_g[w], pn) < TOL_PHI, w
+        assert abs(w_g[w] - wn) <= TOL_W * abs(wn), (w, abs(w_g[w] - wn) / abs(wn))
     assert sys_.last_error() == (0, 0)
     sys_.close()
 

@@ -1,6 +1,8 @@
 """afqmc_kp_step (propagate + local energy with one Green's function per step) vs the
 oracle over two consecutive steps, the second reusing the stored Green's function
-and ending with a QR.  FP64 path at 1e-10; mixed path at the bars of test_gpu_mixed."""
+and ending with a QR.  FP64 path at 1e-10; mixed path at the bars of test_gpu_mixed:
+the task's absolute bars on near-trial walkers, the FP32-class relative energy bar on
+random walkers (a conditioning stress case)."""
 import numpy as np
 import pytest
 
@@ -18,20 +20,24 @@ SPECS = {
 }
 BARS = {"fp64": dict(phi=1e-10, w=1e-10, e_cell=1e-10, e_rel=1e-10),
         "mixed": dict(phi=1e-6, w=1e-5, e_cell=1e-5, e_rel=2e-6)}
+WALKER_SETS = {"near_trial": gen.near_trial_walkers, "random": gen.walkers}
 
 
+@pytest.mark.parametrize("walkers", list(WALKER_SETS))
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", list(SPECS))
-def test_two_steps_with_reuse_and_qr(name, prec):
+def test_two_steps_with_reuse_and_qr(name, prec, walkers):
     """Each step's energy is checked against the oracle evaluated on the walkers the
     GPU itself propagated (E_L of an ill-conditioned walker moves by ~1e-5 Ha/cell
     for a 5e-8 relative change of phi, so comparing against the oracle's own
     trajectory would measure the conditioning, not the kernels); the propagated
     walkers and weights are checked against the oracle step separately."""
     spec = SPECS[name]
-    bar = BARS[prec]
+    bar = dict(BARS[prec])
+    if walkers == "near_trial":
+        bar["e_rel"] = 0.0          # the absolute bar alone
     sys_, osys = make(spec, prec)
-    phis = gen.walkers(spec)
+    phis = WALKER_SETS[walkers](spec)
     w0 = np.linspace(0.7, 1.3, spec.nwalkers)
     phi, w = dev(phis), dev(w0)
     cur_phi, cur_w = phis.copy(), w0.copy()

@@ -1,0 +1,73 @@
+"""Trajectories of the benchmark workload (3x3x3 grid, M = 26, n = 4, 208 vectors per Q,
+64 walkers, dt = 0.005) on the mixed path against the FP64 oracle's own trajectories.
+
+The walkers start near the trial, as a projection does (Sec. 2.1), and take the fused step
+(propagation, then the local energy of the new walkers, the stored Green's function reused
+for the next force bias), with a QR every fifth step: the benchmark's configuration.  Two
+sampled walkers (the first and the last) are followed by the oracle with the same fields.
+After one step and after ten steps the propagated walker, its weight, its log det and its
+local energy meet the task's bars:
+  phi normwise 1e-6, weight 1e-5 relative, log det 1e-5 absolute,
+  E_L 1e-5 Ha per cell per part (E1, E_C, E_X),
+and the force bias of the GPU's walker after ten steps meets 1e-6 normwise against the
+oracle's force bias of that same walker.
+"""
+import numpy as np
+import pytest
+
+import gen
+from oracle import afqmc_kp as ok
+
+torch = pytest.importorskip("torch")
+from gpu_util import dev, host, make, oracle_xbar, rel  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+QR_PERIOD = 5
+NSTEPS = 10
+TOL_PHI, TOL_W, TOL_LD, TOL_E, TOL_XBAR = 1e-6, 1e-5, 1e-5, 1e-5, 1e-6
+
+
+def test_diamond_trajectory_near_trial():
+    spec = gen.DIAMOND_3x3x3
+    sys_, osys = make(spec, "mixed")
+    phis = gen.near_trial_walkers(spec)
+    sampled = (0, spec.nwalkers - 1)
+    phi, w = dev(phis), dev(np.ones(spec.nwalkers))
+    ld = torch.empty((spec.nwalkers, 2), dtype=torch.complex128, device="cuda")
+    eloc = torch.empty((spec.nwalkers, 3), dtype=torch.complex128, device="cuda")
+    ref = {i: (phis[i].copy(), 1.0) for i in sampled}
+    report = []
+    for s in range(NSTEPS):
+        x = gen.fields(spec, s)
+        do_qr = (s + 1) % QR_PERIOD == 0
+        sys_.step(phi, dev(x), w, eloc, logdet=ld, do_qr=do_qr, reuse=s > 0)
+        for i in sampled:
+            pn, wn, _, _, _ = ok.propagate_walker(osys, ref[i][0], x[i], ref[i][1])
+            if do_qr:
+                pn = np.stack([ok.orthonormalise(pn[sp]) for sp in range(2)])
+            ref[i] = (pn, wn)
+        if s + 1 not in (1, NSTEPS):
+            continue
+        got_phi, got_w, got_ld, got_e = host(phi), host(w), host(ld), host(eloc)
+        for i in sampled:
+            pr, wr = ref[i]
+            e_ref = np.array(ok.local_energy(osys, pr))
+            ld_ref = np.array([ok.log_det(ok.overlap(osys, pr[sp])) for sp in range(2)])
+            row = dict(step=s + 1, walker=i, phi=rel(got_phi[i], pr), w=abs(got_w[i] - wr) / wr,
+                       ld=float(np.abs(got_ld[i].real - ld_ref.real).max()),
+                       e=(np.abs(got_e[i] - e_ref) / spec.nk).tolist())
+            report.append(row)
+            print(row)
+            assert wr > 0
+            assert row["phi"] < TOL_PHI, row
+            assert row["w"] < TOL_W, row
+            assert row["ld"] < TOL_LD, row
+            assert max(row["e"]) < TOL_E, row
+    # the force bias of the GPU's walkers after the last step, against the oracle on them
+    xb = host(sys_.force_bias(phi))
+    for i in sampled:
+        assert rel(xb[i], oracle_xbar(osys, got_phi[i])) < TOL_XBAR, i
+    assert np.all(got_w > 0) and np.all(np.isfinite(got_w))
+    assert sys_.last_error() == (0, 0)
+    sys_.close()

@@ -85,6 +85,10 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.afqmc_kp_group_block(None, None, None, None, None, None, None, 1, 1, 1, 0, 0, 1, None, None) == 1
     assert lib.afqmc_kp_group_destroy(None) == 1
     assert lib.afqmc_kp_group_launch_count(None, None) == 1
+    # the allocation-free QR refuses an 8-byte-aligned array before any device work
+    assert lib.afqmc_orthonormalise_noalloc(vp(4096 + 8), 4, 2, 1, None) == 1
+    # the wait self-test: no handle, or a limit out of range
+    assert lib.afqmc_kp_wait_selftest(None, 0, 1000, None) == 1
     d = DenseDesc()
     d.M, d.nocc, d.nchol, d.nwalkers, d.dt, d.taylor_order, d.prec, d.hermitian = 8, 2, 4, 2, 0.01, 6, 0, 2
     buf = (ctypes.c_double * 2)()

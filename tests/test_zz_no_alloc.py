@@ -51,3 +51,10 @@ def test_noalloc_rejects_oversized_requests():
     assert noalloc(phi, too_many, 1, 1) == 1
     assert noalloc(phi, 4, 8, 1) == 1                 # cols > rows
     assert noalloc(phi, 2048, 1025, 1) == 1           # cols beyond the kernel's limit
+    # an 8-byte-aligned complex array (a C double complex pointer may be one) is refused on the
+    # host: the kernel moves (re, im) pairs as 16-byte vectors
+    base = torch.zeros(40, dtype=torch.float64, device="cuda")
+    from paper_2003_09468_gb300 import load_library
+    lib = load_library()
+    assert lib.afqmc_orthonormalise_noalloc(base.data_ptr() + 8, 4, 2, 1,
+                                            torch.cuda.current_stream().cuda_stream) == 1
