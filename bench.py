@@ -315,6 +315,10 @@ class OracleStepper:
                 out[s + 1] = (phi.copy(), w, ld, np.array(ok.local_energy(self.osys, phi)))
         return out
 
+    def log_det_of(self, phi):
+        ok = self.ok
+        return np.array([ok.log_det(ok.overlap(self.osys, phi[s])) for s in range(2)])
+
     def force_bias_of(self, phi):
         ok = self.ok
         Ghs = [ok.green_half(self.osys, phi[s])[0] for s in range(2)]
@@ -359,9 +363,13 @@ def parity_report(stepper, gpu_seeded, gpu_track, oracle_step, precision):
     def compare(gpu, ref):
         phi_g, w_g, e_g, ld_g = gpu
         phi_r, w_r, ld_r, e_r = ref
+        # the returned log det against the oracle's log det of the walker it belongs to (the
+        # GPU's); against the oracle's trajectory it also carries the trajectories' difference
+        ld_own = stepper.log_det_of(phi_g)
         row = {"phi_rel_err": float(np.linalg.norm(phi_g - phi_r) / np.linalg.norm(phi_r)),
                "weight": w_g, "weight_rel_err": float(abs(w_g - w_r) / abs(w_r)) if w_r else None,
-               "logdet_abs_err": float(np.max(np.abs(ld_g.real - ld_r.real))),
+               "logdet_abs_err": float(np.max(np.abs(ld_g.real - ld_own.real))),
+               "logdet_abs_diff_vs_oracle_trajectory": float(np.max(np.abs(ld_g.real - ld_r.real))),
                "E_L_err_ha_per_cell": [float(abs(e_g[j] - e_r[j]) / nk) for j in range(3)],
                "E_L_ha_per_cell": [float(e_r[j].real / nk) for j in range(3)]}
         eb = [bars["E_L_ha_per_cell"] if mixed else bars["E_L_ha_per_cell"] * abs(e_r[j]) / nk for j in range(3)]

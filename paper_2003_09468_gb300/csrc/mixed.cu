@@ -54,11 +54,13 @@ struct MixedState {
   // static operands
   __half* lh_sp = nullptr;    float* s_lh = nullptr;    // [4][Nk][Nk][G][n][Mp], s_lh[Q][G]
   __half* lt_sp = nullptr;    float* s_l = nullptr;     // [4][Nk][Nk][M*M][Gp], s_l[Q][G]
-  __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][T][n*Mp][n*Mp]
+  // Z of every triple in one array: rows 0 .. T-1 the canonical triples (exchange order),
+  // rows T .. Nk^3-1 the transposes for their partners (the adjoint's operands)
+  __half* z_sp = nullptr;     float* s_z = nullptr;     // [4][Nk^3][n*Mp][n*Mp], s_z[Nk^3]
   int4* tri = nullptr;                                   // [T] (Q, k, kx, weight)
-  // adjoint of the exchange: Z for every triple (the partner of a canonical triple holds
-  // the transpose), in the order t = (Q nk + k) nk + kx, and dEX/dGh per block
-  __half* zf_sp = nullptr;    float* s_zf = nullptr;    // [4][Nk^3][n*Mp][n*Mp]
+  // adjoint of the exchange: the row of z_sp that holds Z of triple t = (Q nk + k) nk + kx,
+  // and dEX/dGh per block
+  int* zrow = nullptr;                                   // [Nk^3]
   float2* gam32 = nullptr;                               // [Nk][Nk][WS][n*Mp]
   float2* dhalf = nullptr;                               // [Nk][M][M] exp(-dt/2 H1') - I
   zc* bproj = nullptr;                                   // [Nk][M][n] A (A^dag A)^-1 per k
@@ -72,7 +74,7 @@ struct MixedState {
   // and the per-launch times measured for two and three stages (0 where not tuned)
   int ring[AFQMC_NGEMMS] = {0};
   float tune_ms[AFQMC_NGEMMS][2] = {};
-  CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z, m_zf;
+  CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z, m_zall;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
 };
@@ -542,7 +544,8 @@ struct AdjointP {
   int kcb, mt_n, nt_n, WS, nk, nMp;
   const int* kminus;
   const float* s_g;
-  const float* s_zf;
+  const int* zrow;     // [Nk^3] row of z_sp holding Z of triple t
+  const float* s_z;    // [Nk^3] per row
   float2* gam32;
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
@@ -555,7 +558,7 @@ struct AdjointP {
     const int k1 = b / nk, k2 = b - k1 * nk;
     kx = kminus[k2 * nk + Q];   // k2 - Q
     km = kminus[k1 * nk + Q];   // k1 - Q
-    tf = (Q * nk + k1) * nk + kx;
+    tf = zrow[(Q * nk + k1) * nk + kx];
   }
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
     int tf, km, kx, kk;
@@ -566,7 +569,7 @@ struct AdjointP {
   __device__ float chunk_scale(int b, int kc) const {
     int tf, km, kx, kk;
     split_k(b, kc, tf, km, kx, kk);
-    return 1.f / s_zf[tf];   // a power of two: exact
+    return 1.f / s_z[tf];   // a power of two: exact
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
     const int cols = min(BN, nMp - nt * BN);
@@ -1262,13 +1265,13 @@ __global__ void static_split_kernel(const zc* L, const zc* LH, const float* s_l,
 
 // Z_t[(a,s)][(b,r)] = sum_g LH[Q,k,g,a,r] LH[-Q,kx,g,b,s] in FP64, split per triple.
 __global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, zc* scratch, __half* z_sp,
-                               float* s_z, int T, int nk, int G, int M, int n, int Mp) {
+                               float* s_z, int T, int rows, int nk, int G, int M, int n, int Mp) {
   const int nM = n * M;
   const size_t per = (size_t)nM * nM;
   zc* buf = scratch + (size_t)blockIdx.x * per;
   __shared__ double red[32];
   const int nMp = n * Mp;
-  const size_t ps = (size_t)T * nMp * nMp;
+  const size_t ps = (size_t)rows * nMp * nMp;   // plane stride: z_sp holds `rows` matrices per plane
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int4 q = tri[t];
     const zc* L1 = LH + ((size_t)q.x * nk + q.y) * G * nM;            // LH[Q][k]
@@ -1297,19 +1300,18 @@ __global__ void z_build_kernel(const zc* LH, const int4* tri, const int* minus, 
   }
 }
 
-// Z of every triple from the canonical ones: zf[tf] = z[i] or its transpose (the partner).
-__global__ void z_full_kernel(const __half* z_sp, const float* s_z, const int2* zmap, __half* zf_sp, float* s_zf,
-                              int T, int Tf, int nMp) {
-  const size_t per = (size_t)nMp * nMp, ps = (size_t)T * per, pf = (size_t)Tf * per;
-  for (int tf = blockIdx.x; tf < Tf; tf += gridDim.x) {
-    const int2 zm = zmap[tf];
-    if (threadIdx.x == 0) s_zf[tf] = s_z[zm.x];
+// The partners' rows of z_sp: row T + j holds the transpose of canonical row pmap[j].
+__global__ void z_partner_kernel(__half* z_sp, float* s_z, const int* pmap, int T, int P, int rows, int nMp) {
+  const size_t per = (size_t)nMp * nMp, ps = (size_t)rows * per;
+  for (int j = blockIdx.x; j < P; j += gridDim.x) {
+    const int i = pmap[j];
+    if (threadIdx.x == 0) s_z[T + j] = s_z[i];
     for (int pl = 0; pl < 4; ++pl) {
-      const __half* src = z_sp + pl * ps + (size_t)zm.x * per;
-      __half* dst = zf_sp + pl * pf + (size_t)tf * per;
+      const __half* src = z_sp + pl * ps + (size_t)i * per;
+      __half* dst = z_sp + pl * ps + (size_t)(T + j) * per;
       for (size_t e = threadIdx.x; e < per; e += blockDim.x) {
         const size_t row = e / nMp, col = e % nMp;
-        dst[e] = zm.y ? src[col * nMp + row] : src[e];
+        dst[e] = src[col * nMp + row];
       }
     }
   }
@@ -1468,7 +1470,7 @@ static AdjointP adjoint_params(const afqmc_kp* h) {
   p.nt_n = cdiv(m->nMp, BN);
   p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
   p.WS = m->WS; p.nk = h->nk; p.nMp = m->nMp;
-  p.kminus = h->kminus; p.s_g = m->s_g; p.s_zf = m->s_zf; p.gam32 = m->gam32;
+  p.kminus = h->kminus; p.s_g = m->s_g; p.zrow = m->zrow; p.s_z = m->s_z; p.gam32 = m->gam32;
   return p;
 }
 
@@ -1510,7 +1512,7 @@ static cudaError_t autotune(afqmc_kp* h, cudaStream_t st) {
   if (e == cudaSuccess) e = tune_gemm(h, m->m_lt, m->m_y, vhs_params(h), st, e0, e1);
   if (e == cudaSuccess) e = tune_gemm(h, m->m_t[0], m->m_v, taylor_params(h, 2, 1), st, e0, e1);
   if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_z, exchange_params(h), st, e0, e1);
-  if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_zf, adjoint_params(h), st, e0, e1);
+  if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_zall, adjoint_params(h), st, e0, e1);
   // the QR GEMMs write the caller's walkers: they keep their defaults
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st);   // scratch-data flags
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1523,6 +1525,23 @@ static cudaError_t set_smem_attr(const void* fn, size_t bytes) { return ensure_d
 
 static size_t onebody_smem(const afqmc_kp* h) {
   return sizeof(float2) * h->M * h->M + sizeof(float2) * h->M * OB_LD;
+}
+
+// Free the handle's FP64 Cholesky vectors (the largest static array: Nk^2 G M^2 complex128)
+// once the split operands exist.  Called with no work of the handle in flight.
+static cudaError_t release_fp64_cholesky(afqmc_kp* h) {
+  if (!h->L) return cudaSuccess;
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    if (h->allocs[i] != static_cast<void*>(h->L)) continue;
+    const size_t b = std::max<size_t>((size_t)h->nk * h->nk * h->G * h->M * h->M * sizeof(zc), 16);
+    cudaError_t e = cudaFree(h->L);
+    if (e != cudaSuccess) return e;
+    h->allocs.erase(h->allocs.begin() + i);
+    h->bytes -= b;
+    h->L = nullptr;
+    return cudaSuccess;
+  }
+  return cudaSuccess;
 }
 
 static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
@@ -1556,7 +1575,64 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   m->T = (int)tri.size();
   const int T = m->T;
   const int ntx = cdiv(nMp, BN);
+  const int Tf = nk * nk * nk;
+  // rows of the Z array: canonical triple i at row i; the partner (-Q, kx, k) of a triple
+  // that is not its own partner at row T + j, j counting those triples in order
+  std::vector<int> zrow_h((size_t)Tf, -1), pmap_h;
+  for (int i = 0; i < T; ++i) {
+    const int4 q = tri[i];
+    zrow_h[((size_t)q.x * nk + q.y) * nk + q.z] = i;
+    if (q.w == 2) {
+      zrow_h[((size_t)h->h_minus[q.x] * nk + q.z) * nk + q.y] = T + (int)pmap_h.size();
+      pmap_h.push_back(i);
+    }
+  }
+  const int P = (int)pmap_h.size();
+  if (T + P != Tf) return cudaErrorInvalidValue;
+  for (int v : zrow_h)
+    if (v < 0) return cudaErrorInvalidValue;   // every triple has a canonical member
 
+  // 1. the split Cholesky operands, then the FP64 vectors are released: a mixed handle never
+  //    reads them again (the half-rotated FP64 copy stays for the Z build and the adjoint)
+  MTRY(dalloc(h, &m->lh_sp, (size_t)4 * nk * nk * G * nMp, true, st));
+  MTRY(dalloc(h, &m->s_lh, (size_t)nk * G, true, st));
+  MTRY(dalloc(h, &m->lt_sp, (size_t)4 * nk * nk * M * M * Gp, true, st));
+  MTRY(dalloc(h, &m->s_l, (size_t)nk * G, true, st));
+  MTRY(dalloc(h, &m->inv_s_lh, (size_t)nk * G, true, st));
+  static_scales_kernel<<<dim3(nk, G), 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, nk, G, M, n);
+  AFQMC_LAUNCHED(h);
+  recip_kernel<<<64, 256, 0, st>>>(m->s_lh, m->inv_s_lh, (size_t)nk * G);
+  AFQMC_LAUNCHED(h);
+  static_split_kernel<<<nk * nk, 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, m->lh_sp, m->lt_sp, nk, G, Gp, M, Mp,
+                                               n);
+  AFQMC_LAUNCHED(h);
+  MTRY(cudaGetLastError());
+  MTRY(cudaStreamSynchronize(st));
+  MTRY(release_fp64_cholesky(h));
+
+  // 2. the precontracted exchange tensor of every triple
+  MTRY(dalloc(h, &m->z_sp, (size_t)4 * Tf * nMp * nMp, true, st));
+  MTRY(dalloc(h, &m->s_z, Tf, true, st));
+  MTRY(dalloc(h, &m->tri, T, false, st));
+  MTRY(dalloc(h, &m->zrow, Tf, false, st));
+  int* pmap = nullptr;
+  MTRY(dalloc(h, &pmap, std::max(P, 1), false, st));
+  const int zctas = std::min(T, ZCTAS);
+  MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
+  MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
+  MTRY(cudaMemcpyAsync(m->zrow, zrow_h.data(), sizeof(int) * Tf, cudaMemcpyHostToDevice, st));
+  if (P) MTRY(cudaMemcpyAsync(pmap, pmap_h.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+  z_build_kernel<<<zctas, 256, 0, st>>>(h->LH, m->tri, h->minus, m->zscratch, m->z_sp, m->s_z, T, Tf, nk, G, M, n,
+                                        Mp);
+  AFQMC_LAUNCHED(h);
+  if (P) {
+    z_partner_kernel<<<std::min(P, 4096), 256, 0, st>>>(m->z_sp, m->s_z, pmap, T, P, Tf, nMp);
+    AFQMC_LAUNCHED(h);
+  }
+  MTRY(cudaGetLastError());
+  MTRY(cudaStreamSynchronize(st));   // the host tables above are temporaries
+
+  // 3. per-step workspace
   MTRY(dalloc(h, &m->phi_sp, (size_t)WS * 4 * NM * Np, true, st));
   MTRY(dalloc(h, &m->s_phi, WS, true, st));
   MTRY(dalloc(h, &m->sinvt_sp, (size_t)WS * 4 * N * Np, true, st));
@@ -1577,57 +1653,18 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->xpart, (size_t)T * ntx * WS, true, st));
   MTRY(dalloc(h, &m->xk, (size_t)nk * W * nk * G, true, st));
   MTRY(dalloc(h, &m->mx, (size_t)2 * WS + 3 * W + W, true, st));
-  MTRY(dalloc(h, &m->lh_sp, (size_t)4 * nk * nk * G * nMp, true, st));
-  MTRY(dalloc(h, &m->s_lh, (size_t)nk * G, true, st));
-  MTRY(dalloc(h, &m->lt_sp, (size_t)4 * nk * nk * M * M * Gp, true, st));
-  MTRY(dalloc(h, &m->s_l, (size_t)nk * G, true, st));
-  MTRY(dalloc(h, &m->z_sp, (size_t)4 * T * nMp * nMp, true, st));
-  MTRY(dalloc(h, &m->s_z, T, true, st));
-  MTRY(dalloc(h, &m->tri, T, false, st));
-  const int Tf = nk * nk * nk;
-  MTRY(dalloc(h, &m->zf_sp, (size_t)4 * Tf * nMp * nMp, true, st));
-  MTRY(dalloc(h, &m->s_zf, Tf, true, st));
   MTRY(dalloc(h, &m->gam32, (size_t)nk * nk * WS * nMp, true, st));
-  int2* zmap = nullptr;
-  MTRY(dalloc(h, &zmap, Tf, false, st));
   MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
   MTRY(dalloc(h, &m->bproj, (size_t)nk * M * n, true, st));
   MTRY(dalloc(h, &m->bproj32, (size_t)nk * M * n, true, st));
-  MTRY(dalloc(h, &m->inv_s_lh, (size_t)nk * G, true, st));
-  const int zctas = std::min(T, ZCTAS);
-  MTRY(dalloc(h, &m->zscratch, std::max((size_t)zctas * nM * nM, (size_t)nk * n * 2 * n), false, st));
   MTRY(dalloc(h, &m->s_ff, (size_t)WS * h->N * h->N, false, st));
   MTRY(dalloc(h, &m->logr, (size_t)WS, true, st));
   MTRY(dalloc(h, &m->expart, (size_t)EX_CHUNKS * WS, true, st));
-  MTRY(cudaMemcpyAsync(m->tri, tri.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
-  // every triple's canonical member, and whether it is the transposed partner
-  std::vector<int2> zmap_h((size_t)Tf, make_int2(-1, 0));
-  for (int i = 0; i < T; ++i) {
-    const int4 q = tri[i];
-    zmap_h[((size_t)q.x * nk + q.y) * nk + q.z] = make_int2(i, 0);
-    if (q.w == 2) zmap_h[((size_t)h->h_minus[q.x] * nk + q.z) * nk + q.y] = make_int2(i, 1);
-  }
-  for (const int2& v : zmap_h)
-    if (v.x < 0) return cudaErrorInvalidValue;   // every triple has a canonical member
-  MTRY(cudaMemcpyAsync(zmap, zmap_h.data(), sizeof(int2) * Tf, cudaMemcpyHostToDevice, st));
-  MTRY(cudaStreamSynchronize(st));   // zmap_h is a host temporary
 
-  // trial projector B = A (A^dag A)^-1 (scratch: the z_build buffer, used after this)
+  // trial projector B = A (A^dag A)^-1 (scratch: the Z build's buffer, free again in stream order)
   trial_projector_kernel<<<nk, 256, 0, st>>>(h->A, m->bproj, m->zscratch, M, n);
   AFQMC_LAUNCHED(h);
   to_f32_kernel<<<64, 256, 0, st>>>(m->bproj, m->bproj32, (size_t)nk * M * n);
-  AFQMC_LAUNCHED(h);
-  // static split operands and the precontracted exchange tensor
-  static_scales_kernel<<<dim3(nk, G), 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, nk, G, M, n);
-  AFQMC_LAUNCHED(h);
-  recip_kernel<<<64, 256, 0, st>>>(m->s_lh, m->inv_s_lh, (size_t)nk * G);
-  AFQMC_LAUNCHED(h);
-  static_split_kernel<<<nk * nk, 256, 0, st>>>(h->L, h->LH, m->s_l, m->s_lh, m->lh_sp, m->lt_sp, nk, G, Gp, M, Mp,
-                                               n);
-  AFQMC_LAUNCHED(h);
-  z_build_kernel<<<zctas, 256, 0, st>>>(h->LH, m->tri, h->minus, m->zscratch, m->z_sp, m->s_z, T, nk, G, M, n, Mp);
-  AFQMC_LAUNCHED(h);
-  z_full_kernel<<<std::min(Tf, 4096), 256, 0, st>>>(m->z_sp, m->s_z, zmap, m->zf_sp, m->s_zf, T, Tf, nMp);
   AFQMC_LAUNCHED(h);
   MTRY(cudaGetLastError());
   MTRY(set_one_body(h, st));
@@ -1653,9 +1690,10 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
                  (uint64_t)4 * NM * NMp, BN));
   MTRY(map5(&m->m_g, m->g_sp, {(uint64_t)nMp, (uint64_t)WS, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
+  // the exchange reads the canonical rows, the adjoint every row
   MTRY(map5_pair(&m->m_z, m->z_sp, (uint64_t)nMp, (uint64_t)nMp, (uint64_t)T, (uint64_t)nMp,
-                 (uint64_t)T * nMp * nMp, (uint64_t)nMp * nMp, BN));
-  MTRY(map5_pair(&m->m_zf, m->zf_sp, (uint64_t)nMp, (uint64_t)nMp, (uint64_t)Tf, (uint64_t)nMp,
+                 (uint64_t)Tf * nMp * nMp, (uint64_t)nMp * nMp, BN));
+  MTRY(map5_pair(&m->m_zall, m->z_sp, (uint64_t)nMp, (uint64_t)nMp, (uint64_t)Tf, (uint64_t)nMp,
                  (uint64_t)Tf * nMp * nMp, (uint64_t)nMp * nMp, BN));
   MTRY(map5(&m->m_phi_a, m->phi_sp, {(uint64_t)Np, (uint64_t)NM, 4, (uint64_t)WS, 1},
             {(uint64_t)Np, (uint64_t)NM * Np, (uint64_t)4 * NM * Np, (uint64_t)WS * 4 * NM * Np}, 128));
@@ -1990,7 +2028,7 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
 // dEX/dGh for every block (AdjointP GEMM into gam32).
 static cudaError_t adjoint_exchange(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
-  return run_gemm(h, m->m_g, m->m_zf, adjoint_params(h), h->flags + 1, st);
+  return run_gemm(h, m->m_g, m->m_zall, adjoint_params(h), h->flags + 1, st);
 }
 
 // The adjoint: Gam = conj(grad_e)-weighted dE/dGh with the exchange part from the
