@@ -271,26 +271,30 @@ def orthonormalise(phi_s):
 # Local energy (Sec. 2.2 Eq. local_energy; Sec. 2.3 Eq. kp_el; Sec. 3.2 steps 1-3)
 # --------------------------------------------------------------------------
 
-def local_energy(sys: System, phi):
-    """(E1, EC, EX) of one walker, complex.
-
-    E1 = sum_s sum_k sum_{a q} (A[k]^dag h[k])[a, q] Gh_s[(k a), (k q)]
-    EC = 1/2 sum_{Q g} X[Q, g] X[-Q, g]
-    EX = -1/2 sum_s sum_{Q k k'} sum_{g a b} T1[g, a, b] T2[g, b, a] with
-         T1[g, a, b] = sum_r LH[Q, k, g, a, r] Gh_s[(k'-Q, b), (k-Q, r)]
-         T2[g, b, a] = sum_s LH[-Q, k'-Q, g, b, s] Gh_s[(k, a), (k', s)]
-    """
-    Ghs = [green_half(sys, phi[s])[0] for s in range(2)]
+def one_body_energy(sys: System, Ghs):
+    """E1 = sum_s sum_k sum_{a q} (A[k]^dag h[k])[a, q] Gh_s[(k a), (k q)]."""
     E1 = 0.0j
     for Gh in Ghs:
         for k in range(sys.nk):
             E1 += np.sum((sys.A[k].conj().T @ sys.h[k]) * Gh[sys.rows(k), sys.cols(k)])
-    X = cholesky_trace(sys, Ghs)
-    EC = 0.5 * np.sum(X * X[sys.minus])
+    return complex(E1)
+
+
+def coulomb_energy(sys: System, X):
+    """EC = 1/2 sum_{Q g} X[Q, g] X[-Q, g]."""
+    return complex(0.5 * np.sum(X * X[sys.minus]))
+
+
+def exchange_energy(sys: System, Ghs, Qs=None):
+    """EX = -1/2 sum_s sum_{Q k k'} sum_{g a b} T1[g, a, b] T2[g, b, a] with
+    T1[g, a, b] = sum_r LH[Q, k, g, a, r] Gh_s[(k'-Q, b), (k-Q, r)] and
+    T2[g, b, a] = sum_s LH[-Q, k'-Q, g, b, s] Gh_s[(k, a), (k', s)]  (Sec. 3.2 steps 2(a)-(c)).
+    With Qs given, only the terms of those momentum transfers (a partial sum of EX)."""
     EX = 0.0j
     km, mq = sys.kminus, sys.minus
+    Qlist = range(sys.nk) if Qs is None else Qs
     for Gh in Ghs:
-        for Q in range(sys.nk):
+        for Q in Qlist:
             for k in range(sys.nk):
                 for kp in range(sys.nk):
                     T1 = np.einsum("gar,br->gab", sys.LH[Q, k],
@@ -298,7 +302,17 @@ def local_energy(sys: System, phi):
                     T2 = np.einsum("gbs,as->gba", sys.LH[mq[Q], km[kp, Q]],
                                    Gh[sys.rows(k), sys.cols(kp)])
                     EX += -0.5 * np.einsum("gab,gba->", T1, T2)
-    return complex(E1), complex(EC), complex(EX)
+    return complex(EX)
+
+
+def local_energy(sys: System, phi):
+    """(E1, EC, EX) of one walker, complex (Sec. 2.2 Eq. local_energy; Sec. 2.3 Eq. kp_el):
+    one_body_energy, coulomb_energy of the Cholesky trace X, exchange_energy."""
+    Ghs = [green_half(sys, phi[s])[0] for s in range(2)]
+    E1 = one_body_energy(sys, Ghs)
+    EC = coulomb_energy(sys, cholesky_trace(sys, Ghs))
+    EX = exchange_energy(sys, Ghs)
+    return E1, EC, EX
 
 
 # --------------------------------------------------------------------------
