@@ -36,6 +36,7 @@ host memory.
 from __future__ import annotations
 
 import itertools
+import os
 from dataclasses import dataclass, field
 from typing import Tuple
 
@@ -132,13 +133,25 @@ def chol_block(spec: SystemSpec, Q: int, k: int) -> np.ndarray:
     return (R * scale[:, None, None]).conj().transpose(0, 2, 1).copy()
 
 
-def cholesky(spec: SystemSpec, dtype=np.complex128) -> np.ndarray:
-    """All blocks L[Q, k, g, p, r] (Nk, Nk, nchol, M, M)."""
+def cholesky(spec: SystemSpec, dtype=np.complex128, threads: int | None = None) -> np.ndarray:
+    """All blocks L[Q, k, g, p, r] (Nk, Nk, nchol, M, M).  Every block comes from its own
+    seeded stream, so the blocks are drawn on `threads` threads (default: every core; NumPy's
+    generators and array arithmetic release the GIL) with the same result as one thread."""
+    from concurrent.futures import ThreadPoolExecutor
     nk = spec.nk
     out = np.empty((nk, nk, spec.nchol, spec.M, spec.M), dtype=dtype)
-    for Q in range(nk):
-        for k in range(nk):
-            out[Q, k] = chol_block(spec, Q, k)
+
+    def fill(i):
+        Q, k = divmod(i, nk)
+        out[Q, k] = chol_block(spec, Q, k)
+
+    nthreads = threads or os.cpu_count() or 1
+    if nthreads <= 1 or nk * nk == 1:
+        for i in range(nk * nk):
+            fill(i)
+    else:
+        with ThreadPoolExecutor(min(nthreads, nk * nk)) as ex:
+            list(ex.map(fill, range(nk * nk)))
     return out
 
 

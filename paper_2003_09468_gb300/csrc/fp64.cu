@@ -229,16 +229,30 @@ static cudaError_t gemm_launch_ff(afqmc_kp* h, const ZGemm& g, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 
 // v0[k][p][q] = -1/2 sum_{Q,g,r} L[Q][k][g][p][r] conj(L[Q][k][g][q][r])
-__global__ void v0_kernel(const zc* L, zc* v0, int nk, int G, int M) {
-  const int k = blockIdx.x, p = blockIdx.y;
-  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+// v0[k] = -1/2 sum_{Q,g} L[Q,k,g] L[Q,k,g]^dagger in two passes: one block per (k, Q) sums
+// its g's into part[k][Q] (the block reads its own slab of L once; the M x M products run
+// from L1), then the Q partials are added in a fixed order.
+__global__ void v0_partial_kernel(const zc* L, zc* part, int nk, int G, int M) {
+  const int k = blockIdx.x, Q = blockIdx.y;
+  const int MM = M * M;
+  const zc* slab = L + ((size_t)Q * nk + k) * G * MM;
+  zc* out = part + ((size_t)k * nk + Q) * MM;
+  for (int o = threadIdx.x; o < MM; o += blockDim.x) {
+    const int p = o / M, q = o % M;
     zc s = zzero();
-    for (int Q = 0; Q < nk; ++Q)
-      for (int g = 0; g < G; ++g) {
-        const zc* blk = L + (((long)Q * nk + k) * G + g) * M * M;
-        for (int r = 0; r < M; ++r) s = zfma(blk[p * M + r], zconj(blk[q * M + r]), s);
-      }
-    v0[((long)k * M + p) * M + q] = zscale(s, -0.5);
+    for (int g = 0; g < G; ++g) {
+      const zc* blk = slab + (size_t)g * MM;
+      for (int r = 0; r < M; ++r) s = zfma(blk[p * M + r], zconj(blk[q * M + r]), s);
+    }
+    out[o] = s;
+  }
+}
+__global__ void v0_reduce_kernel(const zc* part, zc* v0, int nk, int M) {
+  const int k = blockIdx.x, MM = M * M;
+  for (int o = threadIdx.x; o < MM; o += blockDim.x) {
+    zc s = zzero();
+    for (int Q = 0; Q < nk; ++Q) s = zadd(s, part[((size_t)k * nk + Q) * MM + o]);
+    v0[(size_t)k * MM + o] = zscale(s, -0.5);
   }
 }
 
@@ -334,10 +348,21 @@ cudaError_t setup_static(afqmc_kp* h, cudaStream_t st) {
     cudaError_t e = gemm_launch(h, g, st);
     if (e != cudaSuccess) return e;
   }
-  v0_kernel<<<dim3(nk, M), 64, 0, st>>>(h->L, h->v0, nk, G, M);
-  AFQMC_LAUNCHED(h);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  {
+    // the Q partials of v0 live in a temporary buffer (create time: allocation is allowed)
+    zc* part = nullptr;
+    cudaError_t e = cudaMalloc(&part, sizeof(zc) * (size_t)nk * nk * M * M);
+    if (e != cudaSuccess) return e;
+    v0_partial_kernel<<<dim3(nk, nk), 256, 0, st>>>(h->L, part, nk, G, M);
+    AFQMC_LAUNCHED(h);
+    v0_reduce_kernel<<<nk, 256, 0, st>>>(part, h->v0, nk, M);
+    AFQMC_LAUNCHED(h);
+    e = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(part);
+    if (e != cudaSuccess) return e;
+    if (e2 != cudaSuccess) return e2;
+  }
   return set_one_body(h, st);
 }
 
