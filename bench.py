@@ -52,7 +52,10 @@ BARS_MIXED = {"E_L_ha_per_cell": 1e-5, "force_bias_rel": 1e-6, "phi_rel": 1e-6, 
 WORKLOADS = {
     "diamond-3x3x3": gen.DIAMOND_3x3x3,
     "small-2x2x2": gen.SMALL_2x2x2,
+    "diamond-4x4x4": gen.DIAMOND_4x4x4,
 }
+LARGE_NK = 64               # from this k-point count on: sampled oracle legs, no FP64 arm
+EX_SAMPLE_Q = 2             # momentum transfers in the sampled oracle exchange of a large workload
 
 
 def load_peaks():
@@ -269,11 +272,12 @@ class OracleStepper:
     """The FP64 CPU oracle, built once for a workload; times single walker-steps and follows
     sampled walkers through the same steps the GPU takes."""
 
-    def __init__(self, spec):
+    def __init__(self, spec, L=None):
         from oracle import afqmc_kp as ok
         self.ok = ok
         self.spec = spec
-        self.osys = ok.System(spec.grid, gen.cholesky(spec), gen.one_body(spec), gen.trial(spec), spec.dt)
+        L = gen.cholesky(spec) if L is None else L      # the GPU arm passes its own copy of the inputs
+        self.osys = ok.System(spec.grid, L, gen.one_body(spec), gen.trial(spec), spec.dt)
 
     def walker(self, walker_index: int = 0):
         return gen.near_trial_walkers(self.spec, 1, first=walker_index)[0]
@@ -315,6 +319,38 @@ class OracleStepper:
                 out[s + 1] = (phi.copy(), w, ld, np.array(ok.local_energy(self.osys, phi)))
         return out
 
+    def sampled_seconds(self, walker_index: int = 0, step: int = 0, nq: int = EX_SAMPLE_Q):
+        """(seconds scaled to one walker-step, propagated walker, weight, description): the
+        propagation, E1 and E_C of one walker timed in full and the exchange timed over the
+        first nq momentum transfers and scaled by Nk / nq (every Q costs the same)."""
+        spec, ok = self.spec, self.ok
+        phi = self.walker(walker_index)
+        x = gen.fields(spec, step, 1, first=walker_index)[0]
+        t0 = time.perf_counter()
+        phi_new, w_new, _, _, _ = ok.propagate_walker(self.osys, phi, x, 1.0)
+        Ghs = [ok.green_half(self.osys, phi_new[s])[0] for s in range(2)]
+        ok.one_body_energy(self.osys, Ghs)
+        ok.coulomb_energy(self.osys, ok.cholesky_trace(self.osys, Ghs))
+        t1 = time.perf_counter()
+        ok.exchange_energy(self.osys, Ghs, Qs=range(nq))
+        t2 = time.perf_counter()
+        total = (t1 - t0) + (t2 - t1) * spec.nk / nq
+        desc = (f"1 walker x 1 step of the workload: propagation, E1 and E_C timed in full ({t1 - t0:.1f} s), "
+                f"the exchange timed over {nq} of {spec.nk} momentum transfers ({t2 - t1:.1f} s) and scaled "
+                f"by {spec.nk // nq}: {total:.0f} s per walker-step (extrapolated), FP64 NumPy")
+        return total, phi_new, w_new, desc
+
+    def energy_parts(self, phi, pool_workers: int = 0):
+        """(E1, EC, EX) of a walker; with pool_workers > 1 the exchange sum over Q is split over
+        that many spawned processes (each sums the oracle's own exchange over its Q's)."""
+        ok = self.ok
+        Ghs = [ok.green_half(self.osys, phi[s])[0] for s in range(2)]
+        e1 = ok.one_body_energy(self.osys, Ghs)
+        ec = ok.coulomb_energy(self.osys, ok.cholesky_trace(self.osys, Ghs))
+        if pool_workers <= 1:
+            return np.array([e1, ec, ok.exchange_energy(self.osys, Ghs)])
+        return np.array([e1, ec, exchange_in_pool(self.osys, Ghs, pool_workers)])
+
     def log_det_of(self, phi):
         ok = self.ok
         return np.array([ok.log_det(ok.overlap(self.osys, phi[s])) for s in range(2)])
@@ -329,6 +365,48 @@ def cpu_cores() -> int:
     return os.cpu_count() or 1
 
 
+class _ExchangeView:
+    """What the oracle's exchange_energy reads from a System: the momentum tables, the block
+    slices and LH, here holding only the momentum transfers one worker sums and their
+    partners (the rest of the array is never touched, so it is never backed by memory)."""
+
+    def __init__(self, grid, n, M, lh_parts):
+        from oracle import afqmc_kp as ok
+        self.kminus, self.minus = ok.kgrid_tables(grid)
+        self.nk, self.n, self.M = len(self.minus), n, M
+        shape = next(iter(lh_parts.values())).shape
+        self.LH = np.zeros((self.nk,) + shape, dtype=np.complex128)
+        for Q, v in lh_parts.items():
+            self.LH[Q] = v
+
+    def rows(self, k):
+        return slice(k * self.n, (k + 1) * self.n)
+
+    def cols(self, k):
+        return slice(k * self.M, (k + 1) * self.M)
+
+
+def _exchange_worker(args):
+    from oracle import afqmc_kp as ok
+    grid, n, M, lh_parts, Ghs, Qs = args
+    return ok.exchange_energy(_ExchangeView(grid, n, M, lh_parts), Ghs, Qs=Qs)
+
+
+def exchange_in_pool(osys, Ghs, workers):
+    """The oracle's exchange energy with its sum over Q split across `workers` spawned
+    processes (spawn: safe after the GPU has been used); the partial sums are added in Q order."""
+    import multiprocessing as mp
+    chunks = [list(range(osys.nk))[i::workers] for i in range(workers)]
+    chunks = [c for c in chunks if c]
+    jobs = []
+    for c in chunks:
+        need = set(c) | {int(osys.minus[Q]) for Q in c}
+        jobs.append((osys.grid, osys.n, osys.M, {Q: osys.LH[Q] for Q in need}, Ghs, c))
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        parts = pool.map(_exchange_worker, jobs)
+    return complex(sum(parts))
+
+
 def workload_config(spec, workload, precision, world):
     """The `config` object of a k-point workload's line (the same for both arms)."""
     return {"workload": workload, "grid": list(spec.grid), "M": spec.M, "nocc": spec.nocc,
@@ -336,6 +414,40 @@ def workload_config(spec, workload, precision, world):
             "qr_period": QR_PERIOD, "precision": precision, "parallelism": f"replicas x{world}",
             "walkers": "near-trial: orthonormalised trial + 0.1 relative complex-normal noise per column",
             "l2": "inputs larger than L2 (Cholesky tensor alone exceeds 129 MB)"}
+
+
+def parity_report_large(stepper, gpu_seeded, gpu_track, oracle_step, precision):
+    """Walker 0 of a large workload against the oracle at the task's bars: the seeded walker's
+    E_L parts and force bias, and after the first fused step the walker, weight, log det and
+    E_L parts (the oracle's exchange summed in a process pool); no drift trajectory."""
+    nk = stepper.spec.nk
+    bars = BARS_MIXED if precision == "mixed" else {k: 1e-10 for k in BARS_MIXED}
+    workers = cpu_cores()
+    e_seed = stepper.energy_parts(stepper.walker(0), workers)
+    xb_seed = stepper.force_bias_of(stepper.walker(0))
+    es_g, xbs_g = gpu_seeded
+    seeded_err = [float(abs(es_g[j] - e_seed[j]) / nk) for j in range(3)]
+    xb_err = float(np.linalg.norm(xbs_g - xb_seed) / np.linalg.norm(xb_seed))
+    seeded = {"E_L_err_ha_per_cell": seeded_err, "E_L_ha_per_cell": [float(e_seed[j].real / nk) for j in range(3)],
+              "force_bias_rel_err": xb_err,
+              "pass": bool(max(seeded_err) < bars["E_L_ha_per_cell"] and xb_err < bars["force_bias_rel"])}
+    phi_r, w_r = oracle_step
+    phi_g, w_g, e_g, ld_g = gpu_track[1]
+    e_r = stepper.energy_parts(phi_r, workers)
+    ld_own = stepper.log_det_of(phi_g)
+    step1 = {"phi_rel_err": float(np.linalg.norm(phi_g - phi_r) / np.linalg.norm(phi_r)), "weight": w_g,
+             "weight_rel_err": float(abs(w_g - w_r) / abs(w_r)) if w_r else None,
+             "logdet_abs_err": float(np.max(np.abs(ld_g.real - ld_own.real))),
+             "E_L_err_ha_per_cell": [float(abs(e_g[j] - e_r[j]) / nk) for j in range(3)],
+             "E_L_ha_per_cell": [float(e_r[j].real / nk) for j in range(3)]}
+    step1["pass"] = bool(w_r > 0 and step1["phi_rel_err"] < bars["phi_rel"]
+                         and step1["weight_rel_err"] < bars["weight_rel"]
+                         and step1["logdet_abs_err"] < bars["logdet_abs"]
+                         and max(step1["E_L_err_ha_per_cell"]) < bars["E_L_ha_per_cell"])
+    return {"walker": 0, "walkers": "near-trial (seeded)", "bars": bars, "seeded": seeded, "step_1": step1,
+            "drift": None, "oracle_exchange": f"summed over Q in {workers} spawned processes",
+            "device_flags_of_the_parity_run": STATUS_NAMES.get(gpu_track.get("status", 0), "?"),
+            "pass": bool(seeded["pass"] and step1["pass"])}
 
 
 def parity_report(stepper, gpu_seeded, gpu_track, oracle_step, precision):
@@ -678,6 +790,7 @@ def main():
     ap.add_argument("--no-block", action="store_true", help="skip the graph-captured paper block")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the local-energy adjoint")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
+    ap.add_argument("--windows", type=int, default=WINDOWS, help="timed windows of --steps steps (median)")
     args = ap.parse_args()
     if args.workload == DENSE_WORKLOAD:
         if args.impl == "reference":
@@ -730,8 +843,10 @@ def main():
     nsteps = args.warmup + args.steps
     nfields = max(nsteps, DRIFT_STEPS)
     xs = [torch.from_numpy(gen.fields(spec, i, spec.nwalkers, first=first)).to(dev) for i in range(nfields)]
-    phi0_d = torch.from_numpy(phi0).to(dev)
-    phi = phi0_d.clone()
+    # the seeded walkers stay on the host (pinned) for the largest workload, whose handle takes
+    # most of the device
+    phi0_d = torch.from_numpy(phi0).pin_memory() if spec.nk >= LARGE_NK else torch.from_numpy(phi0).to(dev)
+    phi = phi0_d.to(dev, copy=True)
     w = torch.ones(spec.nwalkers, dtype=torch.float64, device=dev)
     eloc = torch.empty((spec.nwalkers, 3), dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream()
@@ -758,7 +873,7 @@ def main():
     stages = None
     gpu_launches = 0
     clocks.start()
-    for r in range(WINDOWS):
+    for r in range(args.windows):
         restart()
         for i in range(args.warmup):
             step(i, xs[i])
@@ -766,7 +881,7 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        profile = r == WINDOWS - 1          # stage times from the last window
+        profile = r == args.windows - 1     # stage times from the last window
         if profile:
             sys_.profile(True)
             sys_.stage_times()
@@ -792,7 +907,7 @@ def main():
     torch.cuda.synchronize()
     ms = statistics.median(window_ms)
     value = world * spec.nwalkers * args.steps / (ms * 1e-3)
-    windows = {"count": WINDOWS, "ms": [round(v, 4) for v in window_ms],
+    windows = {"count": args.windows, "ms": [round(v, 4) for v in window_ms],
                "walker_steps_per_s": [world * spec.nwalkers * args.steps / (v * 1e-3) for v in window_ms],
                "headline": "median window; each window restarts from the seeded walkers, takes the warm-up "
                            "steps untimed and times exactly `steps` steps"}
@@ -875,7 +990,7 @@ def main():
             blk()
         g.replay()
         torch.cuda.synchronize()
-        reps = 5
+        reps = 5 if spec.nk < LARGE_NK else 1
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(stream)
         for _ in range(reps):
@@ -914,7 +1029,7 @@ def main():
         torch.cuda.synchronize()
         gpu_seeded = (e_s[0].cpu().numpy(), xb_s[0].cpu().numpy())
         ld = torch.empty((spec.nwalkers, 2), dtype=torch.complex128, device=dev)
-        for i in range(DRIFT_STEPS):
+        for i in range(1 if spec.nk >= LARGE_NK else DRIFT_STEPS):
             sys_.step(phi, xs[i], w, eloc, logdet=ld, do_qr=((i + 1) % QR_PERIOD == 0), reuse=i > 0)
             if i + 1 in (1, DRIFT_STEPS):
                 torch.cuda.synchronize()
@@ -1033,7 +1148,11 @@ def main():
                                    "exchange adjoint over all Nk^3 triples (outside the step)"}
 
     fp64_cmp = None
-    if precision == "mixed" and args.compare_fp64 and world == 1:
+    large = spec.nk >= LARGE_NK
+    if large:
+        fp64_cmp = {"skipped": "FP64 handle at this size: ~150 GB of device buffers and a direct exchange of "
+                               "~375 TFLOP per step on the 1.2 TFLOP/s FP64 pipe (minutes per step)"}
+    if precision == "mixed" and args.compare_fp64 and world == 1 and not large:
         del sys_
         torch.cuda.synchronize()
         s64 = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
@@ -1062,13 +1181,20 @@ def main():
     cpu_baseline = None
     parity = None
     if not args.no_cpu_baseline and world == 1:
-        stepper = OracleStepper(spec)
-        t, phi_ref, w_ref, e_ref = stepper.run(0, 0)
-        cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                        "sample": f"1 walker x 1 step (propagate + E_L) of {args.workload}, FP64 NumPy, "
-                                  f"{t:.1f} s"}
-        if gpu_track:
-            parity = parity_report(stepper, gpu_seeded, gpu_track, (phi_ref, w_ref, e_ref), precision)
+        stepper = OracleStepper(spec, L)
+        if large:
+            t, phi_ref, w_ref, desc = stepper.sampled_seconds(0, 0)
+            cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                            "extrapolated": True}
+            if gpu_track:
+                parity = parity_report_large(stepper, gpu_seeded, gpu_track, (phi_ref, w_ref), precision)
+        else:
+            t, phi_ref, w_ref, e_ref = stepper.run(0, 0)
+            cpu_baseline = {"value": 1.0 / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                            "sample": f"1 walker x 1 step (propagate + E_L) of {args.workload}, FP64 NumPy, "
+                                      f"{t:.1f} s"}
+            if gpu_track:
+                parity = parity_report(stepper, gpu_seeded, gpu_track, (phi_ref, w_ref, e_ref), precision)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

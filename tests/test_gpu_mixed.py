@@ -55,6 +55,9 @@ SPECS = {
     # N = 128 occupied orbitals: the overlap inverse is too large for shared memory and
     # runs on its global-memory variant
     "2x2x2-N128": gen.SystemSpec(grid=(2, 2, 2), M=20, nocc=16, nchol=10, nwalkers=2, random_trial=True, seed=9),
+    # N = 256 occupied orbitals, the count of the 4x4x4 workload: the global-memory overlap
+    # inverse and the global-memory Cholesky of the QR
+    "2x2x4-N256": gen.SystemSpec(grid=(2, 2, 4), M=20, nocc=16, nchol=6, nwalkers=2, random_trial=True, seed=12),
 }
 
 
