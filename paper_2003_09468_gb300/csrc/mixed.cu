@@ -474,6 +474,7 @@ struct TaylorP {
 // L2/HBM while the drain warps already accumulate the next tile.
 struct ExchangeP {
   static constexpr bool kConjA = false;
+  static constexpr bool kStreamB = true;   // Z streams through L2 once per launch
   static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
   int tiles, kchunks;
@@ -537,6 +538,7 @@ struct ExchangeP {
 // chunks are drained.  gam32 receives the sum without the minus sign.
 struct AdjointP {
   static constexpr bool kConjA = false;
+  static constexpr bool kStreamB = true;   // Z streams through L2 once per launch
   static constexpr bool kChunkScale = true;
   static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;

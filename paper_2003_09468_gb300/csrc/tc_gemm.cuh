@@ -77,6 +77,32 @@ struct PairB<P, decltype((void)P::kPairB)> {
   static constexpr bool value = P::kPairB;
 };
 
+//   static constexpr int kDrainChunks = D;
+//       the accumulators run over D consecutive k chunks before they are drained (default 1):
+//       the drain work per MMA falls by D, each fp32 partial carries D times as many
+//       truncating additions.  Not with kChunkScale (one factor per drained partial).
+template <class P, class = void>
+struct DrainChunks {
+  static constexpr int value = 1;
+};
+template <class P>
+struct DrainChunks<P, decltype((void)P::kDrainChunks)> {
+  static constexpr int value = P::kDrainChunks;
+};
+
+//   static constexpr bool kStreamB = true;
+//       B is read once per launch (a large static tensor streamed through): its TMA loads
+//       carry the L2 evict-first policy, so that the reused A tiles and the epilogue's
+//       operands stay in L2
+template <class P, class = void>
+struct StreamB {
+  static constexpr bool value = false;
+};
+template <class P>
+struct StreamB<P, decltype((void)P::kStreamB)> {
+  static constexpr bool value = P::kStreamB;
+};
+
 template <class P>
 __device__ __forceinline__ float chunk_factor(const P& p, int b, int kc) {
   if constexpr (ChunkScaled<P>::value)
@@ -95,6 +121,10 @@ __device__ __forceinline__ float chunk_factor(const P& p, int b, int kc) {
 //   re += P_rr - P_ii,  im += P_ri + P_ir.
 // Tile 128 x BNP (BNP = 64): 4 x 64 columns per set, 2 sets = all 512 TMEM columns.
 constexpr int BNP = 64;
+
+// Accumulator columns per tcgen05.ld in the drain (8 or 16): fewer round trips against more
+// registers beyond the 128 running sums.
+constexpr int DRAIN_COLS = 8;
 
 // Epilogue staging: the finished 128 x 64 tile as (re, im) fp32 pairs, rows padded to 65
 // entries so that row-per-thread and column-per-thread accesses both avoid bank conflicts.
@@ -157,11 +187,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   // are read from HBM once and served from L2 to the others
   const int t0 = blockIdx.x, tstep = gridDim.x;
   const int KC = p.kchunks;
+  constexpr int DC = DrainChunks<P>::value;
+  static_assert(DC >= 1 && (DC == 1 || !ChunkScaled<P>::value), "one chunk factor per drained partial");
 
   if (warp == 0) {
     if (lane == 0) {
       tc::tma_prefetch(&tmA);
       tc::tma_prefetch(&tmB);
+      const uint64_t stream_pol = StreamB<P>::value ? tc::l2_evict_first_policy() : 0;
       long g = 0;
       bool failed = false;
       for (int t = t0; t < p.tiles && !failed; t += tstep) {
@@ -180,7 +213,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           const Coords c = p.coords(b, mt, nt, kc);
           uint8_t* sa = smem + s * Lay::STAGE_BYTES;
           tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
-          tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
+          if constexpr (StreamB<P>::value)
+            tc::tma_load_5d_hint(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4],
+                                 stream_pol);
+          else
+            tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
         }
       }
       // every issued copy must land before the CTA may exit
@@ -194,7 +231,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t id = tc::idesc_f16(BM, BNP, false);
-      long g = 0;
+      long g = 0;   // k chunks (TMA ring)
+      long a = 0;   // drained partials (accumulator sets), one per D chunks
       bool failed = false;
       for (int t = t0; t < p.tiles && !failed; t += tstep) {
         for (int kc = 0; kc < KC; ++kc, ++g) {
@@ -206,14 +244,17 @@ __global__ void __launch_bounds__(THREADS, 1)
             failed = true;
             break;
           }
-          const int set = (int)(g & 1);
-          const uint32_t use = (uint32_t)(g >> 1);
-          if (!tc::mbar_wait(&acce[set], (use & 1) ^ 1, abort)) {
+          const bool open = (kc % DC) == 0;                      // first chunk of a partial
+          const bool close = (kc % DC) == DC - 1 || kc == KC - 1;  // last chunk of a partial
+          const int set = (int)(a & 1);
+          const uint32_t use = (uint32_t)(a >> 1);
+          if (open && !tc::mbar_wait(&acce[set], (use & 1) ^ 1, abort)) {
             atomicCAS(err, 0, tc::ERR_TIMEOUT_ACC);
             *abort = 1;
             failed = true;
             break;
           }
+          const uint32_t acc0 = open ? 0u : 1u;   // the partial's first MMA overwrites the set
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + s * Lay::STAGE_BYTES);
           const uint32_t sb = sa + Lay::A_BYTES;
@@ -237,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int q = 0; q < 2; ++q) {
               const uint32_t dq = d + q * 2 * BNP;
               const int ah = 2 * q;
-              tc::mma_f16(dq, A[ah + 1][0], Bh[0], id2, 0);
+              tc::mma_f16(dq, A[ah + 1][0], Bh[0], id2, acc0);
               tc::mma_f16(dq, A[ah][0], Bl[0], id2, 1);
               tc::mma_f16(dq, A[ah + 1][1], Bh[1], id2, 1);
               tc::mma_f16(dq, A[ah][1], Bl[1], id2, 1);
@@ -257,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int q = 0; q < 4; ++q) {
               const uint32_t dq = d + q * BNP;
               const int ah = ap[q], bh = bp[q];
-              tc::mma_f16(dq, A[ah + 1][0], B[bh][0], id, 0);
+              tc::mma_f16(dq, A[ah + 1][0], B[bh][0], id, acc0);
               tc::mma_f16(dq, A[ah][0], B[bh + 1][0], id, 1);
               tc::mma_f16(dq, A[ah + 1][1], B[bh][1], id, 1);
               tc::mma_f16(dq, A[ah][1], B[bh + 1][1], id, 1);
@@ -265,12 +306,15 @@ __global__ void __launch_bounds__(THREADS, 1)
               tc::mma_f16(dq, A[ah][1], B[bh][1], id, 1);
             }
           }
-          tc::mma_commit(&accf[set]);
+          if (close) {
+            tc::mma_commit(&accf[set]);
+            ++a;
+          }
           tc::mma_commit(&empty[s]);
         }
       }
-      if (g > 0) {  // our own MMAs must complete before TMEM is freed
-        const long last = g - 1;
+      if (a > 0) {  // our own MMAs must complete before TMEM is freed
+        const long last = a - 1;
         int zero = 0;
         if (!tc::mbar_wait(&accf[last & 1], (uint32_t)((last >> 1) & 1), &zero))
           atomicCAS(err, 0, tc::ERR_TIMEOUT_DRAIN);
@@ -286,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-    long g = 0;
+    long g = 0;   // drained partials, in the MMA warp's order
     bool ok = true;
     int ntile = 0;
     for (int t = t0; t < p.tiles; t += tstep, ++ntile) {
@@ -295,7 +339,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float sre[BNP], sim[BNP];
 #pragma unroll
       for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
-      for (int kc = 0; kc < KC; ++kc, ++g) {
+      for (int kc = 0; kc < KC; kc += DC, ++g) {
         const int set = (int)(g & 1);
         const uint32_t use = (uint32_t)(g >> 1);
         if (ok && !tc::mbar_wait(&accf[set], use & 1, abort)) {
@@ -309,32 +353,32 @@ __global__ void __launch_bounds__(THREADS, 1)
         const float cf = chunk_factor(p, b, kc);
         // column blocks of P_rr, P_ii, P_ri, P_ir in the set
         constexpr int o_ii = PairB<P>::value ? 3 : 1, o_ri = PairB<P>::value ? 1 : 2, o_ir = PairB<P>::value ? 2 : 3;
-        // 8 columns of two accumulators per load round: few registers beyond the sums
+        // DRAIN_COLS columns of two accumulators per load round
 #pragma unroll
-        for (int gq = 0; gq < BNP / 8; ++gq) {
-          float x[8], y[8];
-          tc::tmem_ld8(d + 0 * BNP + gq * 8, x);      // P_rr
-          tc::tmem_ld8(d + o_ii * BNP + gq * 8, y);   // P_ii
+        for (int gq = 0; gq < BNP / DRAIN_COLS; ++gq) {
+          float x[DRAIN_COLS], y[DRAIN_COLS];
+          tc::tmem_ld<DRAIN_COLS>(d + 0 * BNP + gq * DRAIN_COLS, x);      // P_rr
+          tc::tmem_ld<DRAIN_COLS>(d + o_ii * BNP + gq * DRAIN_COLS, y);   // P_ii
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int c = 0; c < DRAIN_COLS; ++c) {
             const float v = P::kConjA ? x[c] + y[c] : x[c] - y[c];
             if constexpr (ChunkScaled<P>::value)
-              sre[gq * 8 + c] = fmaf(cf, v, sre[gq * 8 + c]);
+              sre[gq * DRAIN_COLS + c] = fmaf(cf, v, sre[gq * DRAIN_COLS + c]);
             else
-              sre[gq * 8 + c] += v;
+              sre[gq * DRAIN_COLS + c] += v;
           }
-          tc::tmem_ld8(d + o_ri * BNP + gq * 8, x);   // P_ri
-          tc::tmem_ld8(d + o_ir * BNP + gq * 8, y);   // P_ir
+          tc::tmem_ld<DRAIN_COLS>(d + o_ri * BNP + gq * DRAIN_COLS, x);   // P_ri
+          tc::tmem_ld<DRAIN_COLS>(d + o_ir * BNP + gq * DRAIN_COLS, y);   // P_ir
           tc::tmem_ld_wait();
           // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int c = 0; c < DRAIN_COLS; ++c) {
             const float v = P::kConjA ? x[c] - y[c] : x[c] + y[c];
             if constexpr (ChunkScaled<P>::value)
-              sim[gq * 8 + c] = fmaf(cf, v, sim[gq * 8 + c]);
+              sim[gq * DRAIN_COLS + c] = fmaf(cf, v, sim[gq * DRAIN_COLS + c]);
             else
-              sim[gq * 8 + c] += v;
+              sim[gq * DRAIN_COLS + c] += v;
           }
         }
         tc::fence_before_sync();
