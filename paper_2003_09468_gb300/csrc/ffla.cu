@@ -301,11 +301,16 @@ __global__ void __launch_bounds__(GJ_THREADS)
 // arithmetic per element is unchanged (N^3 double-float multiply-adds in all); the
 // rank-GJB update reads and writes each element once per panel instead of once per pivot,
 // with the panel's multipliers and rows reused from registers.
+// The matrix lives in shared memory when it fits (SMEM, N <= GJB_MAXN), else in place in
+// global memory (the overlap buffer, L2-resident while the CTA works on it): each panel then
+// reads and writes the matrix once, where the unblocked kernel does so once per pivot.
 constexpr int GJB = 8;
 constexpr int GJB_MAXN = 112;   // N^2 + GJB N float4 + per-row arrays within SMEM_LIMIT
+constexpr int GJB_GLOBAL_MAXN = 1024;   // GJB N float4 + per-row arrays within SMEM_LIMIT
 
+template <bool SMEM>
 __global__ void __launch_bounds__(GJ_THREADS)
-    gjb_ff_kernel(const float4* Sff, int N, zc* logdet, int* sing, int* flags, __half* out, int Np, float* s_out) {
+    gjb_ff_kernel(float4* Sff, int N, zc* logdet, int* sing, int* flags, __half* out, int Np, float* s_out) {
   extern __shared__ __align__(16) unsigned char gj_smem[];
   __shared__ int s_p, s_sing, s_swaps;
   __shared__ float4 s_pv, s_ajj;
@@ -313,14 +318,15 @@ __global__ void __launch_bounds__(GJ_THREADS)
   __shared__ float s_redf[GJ_WARPS];
   __shared__ int s_prow[GJB];
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const float4* g = Sff + (size_t)b * N * N;
-  float4* a = reinterpret_cast<float4*>(gj_smem);        // [N][N]
-  float4* tmp = a + (size_t)N * N;                        // [GJB][N] panel rows before the update
+  float4* g = Sff + (size_t)b * N * N;
+  float4* a = SMEM ? reinterpret_cast<float4*>(gj_smem) : g;   // [N][N]
+  float4* tmp = reinterpret_cast<float4*>(gj_smem) + (SMEM ? (size_t)N * N : 0);   // [GJB][N] panel rows
   float4* f = tmp + (size_t)GJB * N;                      // [N] multipliers
   double2* piv = reinterpret_cast<double2*>(f + N);
   int* perm = reinterpret_cast<int*>(piv + N);
   int* iperm = perm + N;
-  for (int e = tid; e < N * N; e += GJ_THREADS) a[e] = g[e];
+  if (SMEM)
+    for (int e = tid; e < N * N; e += GJ_THREADS) a[e] = g[e];
   for (int i = tid; i < N; i += GJ_THREADS) perm[i] = i;
   if (tid == 0) {
     s_sing = 0;
@@ -532,8 +538,16 @@ cudaError_t invert(float4* Sff, int WS, int N, zc* logdet, int* sing, int* flags
   if (out && N <= GJB_MAXN) {
     const size_t bytes = ((size_t)N * N + (size_t)GJB * N) * sizeof(float4) + gj_smem_bytes(N, false);
     if (bytes <= SMEM_LIMIT) {
-      if ((e = set_smem(gjb_ff_kernel, bytes)) != cudaSuccess) return e;
-      gjb_ff_kernel<<<WS, GJ_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
+      if ((e = set_smem(gjb_ff_kernel<true>, bytes)) != cudaSuccess) return e;
+      gjb_ff_kernel<true><<<WS, GJ_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
+      return cudaGetLastError();
+    }
+  }
+  if (out && N <= GJB_GLOBAL_MAXN) {
+    const size_t bytes = (size_t)GJB * N * sizeof(float4) + gj_smem_bytes(N, false);
+    if (bytes <= SMEM_LIMIT) {
+      if ((e = set_smem(gjb_ff_kernel<false>, bytes)) != cudaSuccess) return e;
+      gjb_ff_kernel<false><<<WS, GJ_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
       return cudaGetLastError();
     }
   }
