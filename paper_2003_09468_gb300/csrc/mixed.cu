@@ -49,7 +49,8 @@ struct MixedState {
   double2* acc = nullptr;                                // [W][2N][NM] (scratch: float4 Taylor corrections, phi_perp)
   float2* p32 = nullptr;                                 // [W][2N][NM] phi' in fp32 (Taylor series)
   double2* xpart = nullptr;                              // [T][ntile][WS]
-  double2* xk = nullptr;                                 // [Nk][W][Nk][G] per-k-block Cholesky traces
+  double2* xk = nullptr;                                 // [fb_groups][W][Nk][G] Cholesky traces per group of k blocks
+  int fb_groups = 1;                                     // groups of k blocks in the force-bias GEMM
   unsigned long long* mx = nullptr;                      // max |.| bit patterns: phi[WS], sinv[WS], g[3W], acc[W]
   // static operands
   __half* lh_sp = nullptr;    float* s_lh = nullptr;    // [4][Nk][Nk][G][n][Mp], s_lh[Q][G]
@@ -238,32 +239,35 @@ struct GreenP {
   }
 };
 
-// Partial Cholesky trace of one k block: Xk[k][w][Q][g] = sum_{a,r} LH[Q,k,g,a,r] Gsum_w[(k,a),(k-Q,r)].
-// Splitting the k sum across tiles keeps every fp32 running sum short; the k
-// blocks are summed in FP64 by xsum_kernel.
+// Partial Cholesky trace of one group of k blocks:
+//   Xk[grp][w][Q][g] = sum_{k in grp} sum_{a,r} LH[Q,k,g,a,r] Gsum_w[(k,a),(k-Q,r)],
+// the group's k blocks running one after another along the GEMM's k loop (kcb chunks each).
+// The groups (ng, dividing Nk) are as few as still give the GPU enough tiles; they are summed
+// in FP64 by xsum_kernel.  Both operands carry one scale over all k (per (Q, g) and per
+// walker), so the blocks of a group add in one fp32 running sum.
 struct ForceBiasP {
   static constexpr bool kConjA = false;
   static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
   int tiles, kchunks;
-  int mt_n, nt_n, W, G, nk;
+  int mt_n, nt_n, W, G, nk, ng, kg, kcb;   // ng groups of kg k blocks, kcb chunks per block
   const int* kminus;
   const float* s_gsum;
   const float* inv_s_lh;
-  double2* Xk;  // [Nk(k)][W][Nk(Q)][G]
+  double2* Xk;  // [ng][W][Nk(Q)][G]
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
-    b = t / (nt_n * mt_n);   // b = Q * nk + k
+    b = t / (nt_n * mt_n);   // b = Q * ng + group
   }
   // rows = Cholesky index g of LH[Q][k] (A), columns = walkers (B = spin-summed Gh)
   __device__ tcg::Coords coords(int b, int mt, int nt, int kc) const {
-    const int Q = b / nk, k = b % nk, c0 = kc * 32;
+    const int Q = b / ng, k = (b % ng) * kg + kc / kcb, c0 = (kc % kcb) * 32;
     tcg::Coords c = {{c0, mt * 128, 0, k, Q}, {c0, nt * BN, 0, 0, k * nk + kminus[k * nk + Q]}};
     return c;
   }
   __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int, int) const {
-    const int Q = b / nk, k = b % nk;
+    const int Q = b / ng, grp = b % ng;
     // down the rows: consecutive threads write consecutive g of one walker
     for (int e = tid; e < 128 * BN; e += 128) {
       const int r = e % 128, c = e / 128;
@@ -271,16 +275,16 @@ struct ForceBiasP {
       if (w >= W || g >= G) continue;
       const float f = inv_s_lh[Q * G + g] / s_gsum[w];
       const float2 v = tile[r * tcg::STAGE_LD + c];
-      Xk[(((size_t)k * W + w) * nk + Q) * G + g] = make_double2((double)(v.x * f), (double)(v.y * f));
+      Xk[(((size_t)grp * W + w) * nk + Q) * G + g] = make_double2((double)(v.x * f), (double)(v.y * f));
     }
   }
 };
 
-// X[w][Q][g] = sum_k Xk[k][w][Q][g]  (FP64, fixed order)
-__global__ void xsum_kernel(const double2* Xk, zc* X, int nk, size_t per) {
+// X[w][Q][g] = sum over the groups of Xk[grp][w][Q][g]  (FP64, fixed order)
+__global__ void xsum_kernel(const double2* Xk, zc* X, int ng, size_t per) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < per; e += (size_t)gridDim.x * blockDim.x) {
     double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < nk; ++k) {
+    for (int k = 0; k < ng; ++k) {
       const double2 v = Xk[(size_t)k * per + e];
       s.x += v.x;
       s.y += v.y;
@@ -474,7 +478,7 @@ struct TaylorP {
 // L2/HBM while the drain warps already accumulate the next tile.
 struct ExchangeP {
   static constexpr bool kConjA = false;
-  static constexpr bool kStreamB = true;   // Z streams through L2 once per launch
+  static constexpr bool kStreamB = true;   // Z streams through L2 once per launch when mt_n == 1
   static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
   int tiles, kchunks;
@@ -486,6 +490,8 @@ struct ExchangeP {
   const float* s_z;
   const float2* g32;  // [Nk][Nk][WS][n*Mp]
   double2* xpart;     // [T][nt_n][WS]
+  // with more than one row tile every Z tile is read once per row tile: keep it in L2 then
+  __device__ bool stream_b() const { return mt_n == 1; }
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -538,7 +544,7 @@ struct ExchangeP {
 // chunks are drained.  gam32 receives the sum without the minus sign.
 struct AdjointP {
   static constexpr bool kConjA = false;
-  static constexpr bool kStreamB = true;   // Z streams through L2 once per launch
+  static constexpr bool kStreamB = true;   // Z streams through L2 once per launch when mt_n == 1
   static constexpr bool kChunkScale = true;
   static constexpr bool kPairB = true;
   static constexpr int kStages = STAGES_LIGHT;
@@ -549,6 +555,8 @@ struct AdjointP {
   const int* zrow;     // [Nk^3] row of z_sp holding Z of triple t
   const float* s_z;    // [Nk^3] per row
   float2* gam32;
+  // with more than one row tile every Z tile is read once per row tile: keep it in L2 then
+  __device__ bool stream_b() const { return mt_n == 1; }
   __device__ void tile(int t, int& b, int& mt, int& nt) const {
     nt = t % nt_n;
     mt = (t / nt_n) % mt_n;
@@ -896,14 +904,20 @@ __global__ void onebody_in_kernel(const zc* phi, const float2* dhalf, float4* co
 
 // Second half step: with corr.xy = d = phi'' - phi and corr.zw = phi'' (fp32) after the
 // Taylor series, phi <- phi + d + D phi'' (the sum of fp32 corrections is added to the
-// FP64 walker once).  grid (k, ws, j-chunk of 64)
+// FP64 walker once).  grid (k, ws, j-chunk of 64).  STAGE_D: both parts of corr are staged in
+// shared memory by one coalesced pass (rows j, orbitals contiguous), and the FP64 walker
+// (orbital rows, columns j contiguous) is updated with sixteen consecutive threads on sixteen
+// consecutive columns; without it (M too large for the second staging buffer) the threads
+// run down the orbitals and read d from global memory.
+template <bool STAGE_D>
 __global__ void onebody_out_kernel(const float4* corr, const float2* dhalf, zc* phi, int nk, int M, int N, int NM) {
   const int k = blockIdx.x, ws = blockIdx.y, j0 = blockIdx.z * 64;
   const int w = ws >> 1, sp = ws & 1;
   const int jn = min(64, N - j0);
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* blk = reinterpret_cast<float2*>(smraw);          // [M][OB_LD]
-  float2* Dt = blk + M * OB_LD;                                 // [M][M]
+  float2* blk = reinterpret_cast<float2*>(smraw);          // [M][OB_LD] phi''
+  float2* dd = blk + M * OB_LD;                                 // [M][OB_LD] d (STAGE_D)
+  float2* Dt = dd + (STAGE_D ? M * OB_LD : 0);                  // [M][M]
   for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
     const int p = e / M, q = e % M;
     Dt[q * M + p] = dhalf[(size_t)k * M * M + e];
@@ -911,27 +925,25 @@ __global__ void onebody_out_kernel(const float4* corr, const float2* dhalf, zc* 
   const float4* src = corr + ((size_t)w * 2 * N + sp * N + j0) * NM + k * M;
   for (int e = threadIdx.x; e < M * 64; e += blockDim.x) {
     const int j = e / M, q = e % M;
-    float2 v = make_float2(0.f, 0.f);
-    if (j < jn) {
-      const float4 x = src[(size_t)j * NM + q];
-      v = make_float2(x.z, x.w);
-    }
-    blk[q * OB_LD + j] = v;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < jn) x = src[(size_t)j * NM + q];
+    blk[q * OB_LD + j] = make_float2(x.z, x.w);
+    if (STAGE_D) dd[q * OB_LD + j] = make_float2(x.x, x.y);
   }
   __syncthreads();
   zc* dst = phi + (size_t)ws * NM * N;
   for (int e = threadIdx.x; e < M * 16; e += blockDim.x) {
-    const int p = e % M, jq = e / M;
+    const int jq = STAGE_D ? e % 16 : e / M, p = STAGE_D ? e / 16 : e % M;
     float2 c[4];
     onebody_apply4(Dt, blk, M, p, jq, c);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = jq + 16 * u;
       if (j >= jn) continue;
-      const float2 dd = reinterpret_cast<const float2*>(src)[2 * ((size_t)j * NM + p)];
+      const float2 d = STAGE_D ? dd[p * OB_LD + j] : reinterpret_cast<const float2*>(src)[2 * ((size_t)j * NM + p)];
       zc v = dst[(size_t)(k * M + p) * N + j0 + j];
-      v.x += (double)(dd.x + c[u].x);
-      v.y += (double)(dd.y + c[u].y);
+      v.x += (double)(d.x + c[u].x);
+      v.y += (double)(d.y + c[u].y);
       dst[(size_t)(k * M + p) * N + j0 + j] = v;
     }
   }
@@ -1419,8 +1431,11 @@ static ForceBiasP force_bias_params(const afqmc_kp* h) {
   ForceBiasP p;
   p.mt_n = cdiv(h->G, 128);
   p.nt_n = cdiv(h->W, BN);
-  p.tiles = h->nk * h->nk * p.mt_n * p.nt_n;
-  p.kchunks = m->nMp / 32;
+  p.ng = m->fb_groups;
+  p.kg = h->nk / p.ng;
+  p.kcb = m->nMp / 32;
+  p.tiles = h->nk * p.ng * p.mt_n * p.nt_n;
+  p.kchunks = p.kg * p.kcb;
   p.W = h->W; p.G = h->G; p.nk = h->nk;
   p.kminus = h->kminus; p.s_gsum = m->s_gsum; p.inv_s_lh = m->inv_s_lh; p.Xk = m->xk;
   return p;
@@ -1528,6 +1543,9 @@ static cudaError_t set_smem_attr(const void* fn, size_t bytes) { return ensure_d
 static size_t onebody_smem(const afqmc_kp* h) {
   return sizeof(float2) * h->M * h->M + sizeof(float2) * h->M * OB_LD;
 }
+// the second half step with d staged too, where it fits
+static size_t onebody_out_smem(const afqmc_kp* h) { return onebody_smem(h) + sizeof(float2) * h->M * OB_LD; }
+static bool onebody_out_staged(const afqmc_kp* h) { return onebody_out_smem(h) <= 220 * 1024; }
 
 // Free the handle's FP64 Cholesky vectors (the largest static array: Nk^2 G M^2 complex128)
 // once the split operands exist.  Called with no work of the handle in flight.
@@ -1653,7 +1671,20 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
   MTRY(dalloc(h, &m->acc, (size_t)W * 2 * N * NM, true, st));
   MTRY(dalloc(h, &m->p32, (size_t)W * 2 * N * NM, true, st));
   MTRY(dalloc(h, &m->xpart, (size_t)T * ntx * WS, true, st));
-  MTRY(dalloc(h, &m->xk, (size_t)nk * W * nk * G, true, st));
+  // force-bias GEMM: the fewest groups of k blocks (a divisor of Nk) that give every SM a tile
+  {
+    int dev = 0, sms = 0;
+    MTRY(cudaGetDevice(&dev));
+    MTRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_group = nk * cdiv(G, 128) * cdiv(W, BN);
+    m->fb_groups = nk;
+    for (int d = 1; d <= nk; ++d)
+      if (nk % d == 0 && per_group * d >= sms) {
+        m->fb_groups = d;
+        break;
+      }
+  }
+  MTRY(dalloc(h, &m->xk, (size_t)m->fb_groups * W * nk * G, true, st));
   MTRY(dalloc(h, &m->mx, (size_t)2 * WS + 3 * W + W, true, st));
   MTRY(dalloc(h, &m->gam32, (size_t)nk * nk * WS * nMp, true, st));
   MTRY(dalloc(h, &m->dhalf, (size_t)nk * M * M, true, st));
@@ -1705,7 +1736,10 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
                  (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, BN));
   MTRY(set_smem_attr((const void*)gamma_assemble_kernel, sizeof(float2) * GA_W * G));
   MTRY(set_smem_attr((const void*)onebody_in_kernel, onebody_smem(h)));
-  MTRY(set_smem_attr((const void*)onebody_out_kernel, onebody_smem(h)));
+  if (onebody_out_staged(h))
+    MTRY(set_smem_attr((const void*)onebody_out_kernel<true>, onebody_out_smem(h)));
+  else
+    MTRY(set_smem_attr((const void*)onebody_out_kernel<false>, onebody_smem(h)));
   return autotune(h, st);
 }
 
@@ -1795,7 +1829,7 @@ static cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st) {
   MTRY(run_gemm(h, m->m_lh, m->m_gsum, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   const size_t per = (size_t)h->W * h->nk * h->G;
-  xsum_kernel<<<(int)std::min<size_t>((per + 255) / 256, 4096), 256, 0, st>>>(m->xk, h->X, h->nk, per);
+  xsum_kernel<<<(int)std::min<size_t>((per + 255) / 256, 4096), 256, 0, st>>>(m->xk, h->X, m->fb_groups, per);
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }
@@ -1848,7 +1882,10 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
     AFQMC_LAUNCHED(h);
   }
   prof_begin(h, AFQMC_STAGE_ONEBODY, st);
-  onebody_out_kernel<<<g1, 256, onebody_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
+  if (onebody_out_staged(h))
+    onebody_out_kernel<true><<<g1, 256, onebody_out_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
+  else
+    onebody_out_kernel<false><<<g1, 256, onebody_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
   AFQMC_LAUNCHED(h);
   prof_end(h, st);
   return cudaGetLastError();

@@ -90,10 +90,10 @@ struct DrainChunks<P, decltype((void)P::kDrainChunks)> {
   static constexpr int value = P::kDrainChunks;
 };
 
-//   static constexpr bool kStreamB = true;
-//       B is read once per launch (a large static tensor streamed through): its TMA loads
-//       carry the L2 evict-first policy, so that the reused A tiles and the epilogue's
-//       operands stay in L2
+//   static constexpr bool kStreamB = true;  __device__ bool stream_b() const;
+//       when stream_b() is true, B is read once per launch (a large static tensor streamed
+//       through, one row tile): its TMA loads carry the L2 evict-first policy, so that the
+//       reused A tiles and the epilogue's operands stay in L2
 template <class P, class = void>
 struct StreamB {
   static constexpr bool value = false;
@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       tc::tma_prefetch(&tmA);
       tc::tma_prefetch(&tmB);
-      const uint64_t stream_pol = StreamB<P>::value ? tc::l2_evict_first_policy() : 0;
+      bool stream = false;
+      if constexpr (StreamB<P>::value) stream = p.stream_b();
+      const uint64_t stream_pol = stream ? tc::l2_evict_first_policy() : 0;
       long g = 0;
       bool failed = false;
       for (int t = t0; t < p.tiles && !failed; t += tstep) {
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const Coords c = p.coords(b, mt, nt, kc);
           uint8_t* sa = smem + s * Lay::STAGE_BYTES;
           tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
-          if constexpr (StreamB<P>::value)
+          if (stream)
             tc::tma_load_5d_hint(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4],
                                  stream_pol);
           else
