@@ -319,7 +319,7 @@ def local_energy(sys: System, phi):
 # Adjoint of the local energy (derived from Eq. kp_el; holomorphic in phi)
 # --------------------------------------------------------------------------
 
-def local_energy_grad(sys: System, phi, parts=(1.0, 1.0, 1.0)):
+def local_energy_grad(sys: System, phi, parts=(1.0, 1.0, 1.0), two_body=None):
     """Holomorphic derivatives of c1 E1 + c2 EC + c3 EX.
 
     Returns (dphi[s, NM, N], dh[k, M, M]) with dphi = d E / d phi and
@@ -332,11 +332,13 @@ def local_energy_grad(sys: System, phi, parts=(1.0, 1.0, 1.0)):
     and with S = A^dag phi_s, Theta = phi_s S^-1:
       dE/dphi_s = [S^-1 (Gamma_s - (Gamma_s Theta) A^dag)]^T
       dE/dh[k]  = c1 sum_s conj(A[k]) Gh_s[(k, .), (k, .)]
+    two_body(sys, Gh, X, c2, c3, Gam) adds the Coulomb and exchange blocks (default
+    gamma_two_body; a caller may pass one that sums the same blocks in another order).
     """
     c1, c2, c3 = parts
+    two_body = gamma_two_body if two_body is None else two_body
     Ghs = [green_half(sys, phi[s])[0] for s in range(2)]
     X = cholesky_trace(sys, Ghs)
-    km, mq = sys.kminus, sys.minus
     Ad = sys.A_dense()
     dphi = np.empty_like(phi)
     dh = np.zeros_like(sys.h)
@@ -345,15 +347,7 @@ def local_energy_grad(sys: System, phi, parts=(1.0, 1.0, 1.0)):
         for k in range(sys.nk):
             Gam[sys.rows(k), sys.cols(k)] += c1 * (sys.A[k].conj().T @ sys.h[k])
             dh[k] += c1 * (sys.A[k].conj() @ Gh[sys.rows(k), sys.cols(k)])
-        for Q in range(sys.nk):
-            for k in range(sys.nk):
-                Gam[sys.rows(k), sys.cols(km[k, Q])] += c2 * np.einsum(
-                    "g,gar->ar", X[mq[Q]], sys.LH[Q, k])
-                for kp in range(sys.nk):
-                    T2 = np.einsum("gbs,as->gba", sys.LH[mq[Q], km[kp, Q]],
-                                   Gh[sys.rows(k), sys.cols(kp)])
-                    Gam[sys.rows(km[kp, Q]), sys.cols(km[k, Q])] += -c3 * np.einsum(
-                        "gba,gar->br", T2, sys.LH[Q, k])
+        two_body(sys, Gh, X, c2, c3, Gam)
         S = overlap(sys, phi[s])
         Sinv = np.linalg.inv(S)
         Theta = phi[s] @ Sinv
@@ -361,10 +355,28 @@ def local_energy_grad(sys: System, phi, parts=(1.0, 1.0, 1.0)):
     return dphi, dh
 
 
-def local_energy_vjp(sys: System, phi, g):
+def gamma_two_body(sys: System, Gh, X, c2, c3, Gam, Qs=None):
+    """Add to Gam (N x NM) the Coulomb and exchange parts of dE/dGh of one spin:
+      block (k, k - Q)            += c2 sum_g X[-Q, g] LH[Q, k, g]
+      block (k' - Q, k - Q)[b, r] += -c3 sum_{g a} T2[g, b, a] LH[Q, k, g, a, r]
+    for every momentum transfer Q (or those in Qs: a partial sum), T2 as in exchange_energy."""
+    km, mq = sys.kminus, sys.minus
+    for Q in (range(sys.nk) if Qs is None else Qs):
+        for k in range(sys.nk):
+            Gam[sys.rows(k), sys.cols(km[k, Q])] += c2 * np.einsum(
+                "g,gar->ar", X[mq[Q]], sys.LH[Q, k])
+            for kp in range(sys.nk):
+                T2 = np.einsum("gbs,as->gba", sys.LH[mq[Q], km[kp, Q]],
+                               Gh[sys.rows(k), sys.cols(kp)])
+                Gam[sys.rows(km[kp, Q]), sys.cols(km[k, Q])] += -c3 * np.einsum(
+                    "gba,gar->br", T2, sys.LH[Q, k])
+    return Gam
+
+
+def local_energy_vjp(sys: System, phi, g, two_body=None):
     """PyTorch-convention backward: returns conj(dE/dphi) and conj(dE/dh) weighted by g[3].
 
     With g = dLoss/dconj(E) per part, dLoss/dconj(phi) = sum_part g_part conj(dE_part/dphi).
     """
-    dphi, dh = local_energy_grad(sys, phi, parts=tuple(np.conj(g)))
+    dphi, dh = local_energy_grad(sys, phi, parts=tuple(np.conj(g)), two_body=two_body)
     return dphi.conj(), dh.conj()
