@@ -392,6 +392,31 @@ def _exchange_worker(args):
     return ok.exchange_energy(_ExchangeView(grid, n, M, lh_parts), Ghs, Qs=Qs)
 
 
+def _gamma_worker(args):
+    from oracle import afqmc_kp as ok
+    grid, n, M, lh_parts, Gh, X, c2, c3, Qs = args
+    return ok.gamma_two_body(_ExchangeView(grid, n, M, lh_parts), Gh, X, c2, c3, np.zeros_like(Gh), Qs=Qs)
+
+
+def gamma_in_pool(workers):
+    """A two_body for the oracle's local_energy_grad that splits its sum over Q across `workers`
+    spawned processes (each runs the oracle's own gamma_two_body on its momentum transfers) and
+    adds the partial blocks in Q-chunk order."""
+    import multiprocessing as mp
+
+    def two_body(osys, Gh, X, c2, c3, Gam):
+        chunks = [c for c in (list(range(osys.nk))[i::workers] for i in range(workers)) if c]
+        jobs = []
+        for c in chunks:
+            need = set(c) | {int(osys.minus[Q]) for Q in c}
+            jobs.append((osys.grid, osys.n, osys.M, {Q: osys.LH[Q] for Q in need}, Gh, X, c2, c3, c))
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            for part in pool.map(_gamma_worker, jobs):
+                Gam += part
+        return Gam
+    return two_body
+
+
 def exchange_in_pool(osys, Ghs, workers):
     """The oracle's exchange energy with its sum over Q split across `workers` spawned
     processes (spawn: safe after the GPU has been used); the partial sums are added in Q order."""

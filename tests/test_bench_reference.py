@@ -51,3 +51,24 @@ def test_parity_report_gates_at_the_task_bars():
     bad[bench.DRIFT_STEPS] = (p * (1 + 1e-5), w, e, ld)
     rep = bench.parity_report(st, (e0, xb0), bad, (phi1, w1, e1), "mixed")
     assert not rep["drift"]["pass"] and not rep["pass"] and rep["step_1"]["pass"]
+
+
+def test_pooled_oracle_sums_equal_the_oracle():
+    """The benchmark's process-pool forms of the oracle's exchange energy and of its two-body
+    gradient blocks (the sum over Q split across spawned processes) give the oracle's values."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import gen
+    from oracle import afqmc_kp as ok
+    spec = gen.SystemSpec(grid=(2, 2, 1), M=5, nocc=2, nchol=6, nwalkers=1, random_trial=True, seed=3)
+    osys = ok.System(spec.grid, gen.cholesky(spec), gen.one_body(spec), gen.trial(spec), spec.dt)
+    phi = gen.near_trial_walkers(spec)[0]
+    Ghs = [ok.green_half(osys, phi[s])[0] for s in range(2)]
+    ex = ok.exchange_energy(osys, Ghs)
+    assert abs(bench.exchange_in_pool(osys, Ghs, 3) - ex) < 1e-12 * abs(ex)
+    g = gen.upstream(spec)[0]
+    a = ok.local_energy_vjp(osys, phi, g)
+    b = ok.local_energy_vjp(osys, phi, g, two_body=bench.gamma_in_pool(3))
+    assert np.abs(a[0] - b[0]).max() < 1e-12 * np.abs(a[0]).max()
+    assert np.abs(a[1] - b[1]).max() == 0.0

@@ -7,9 +7,12 @@ exchange tensor of all 262 144 triples, the walker workspace), so this test need
 GPU.  The oracle follows walker 0 at the task's bars:
   the seeded walker's force bias (1e-6 normwise) and E1, E_C, E_X (1e-5 Ha per cell);
   after one fused step, the walker (1e-6), its weight (1e-5 relative), its log det (1e-5,
-  against the oracle's log det of the GPU's walker) and E1, E_C, E_X (1e-5 Ha per cell).
-The oracle's exchange sum of one walker at this size (2 x 64^3 terms) is split over Q across
-spawned processes, each running the oracle's own exchange_energy on its momentum transfers.
+  against the oracle's log det of the GPU's walker) and E1, E_C, E_X (1e-5 Ha per cell);
+  the adjoint of the seeded walker's local energy (dE/dphi within 1e-5 of ||dE/dphi||, dE/dh
+  within 1e-10).
+The oracle's exchange sum of one walker at this size (2 x 64^3 terms) and the exchange blocks of
+its gradient are split over Q across spawned processes, each running the oracle's own
+functions on its momentum transfers.
 """
 import gc
 import os
@@ -50,6 +53,13 @@ def test_diamond_4x4x4_sampled():
     e1 = host(sys_.step(phi, dev(x), w, logdet=ld, do_qr=False, reuse=False))
     phi_g, w_g, ld_g = host(phi[:1]), host(w), host(ld)
     assert np.all(np.isfinite(e0)) and np.all(np.isfinite(e1)) and np.all(w_g > 0)
+    # the adjoint of the seeded walkers' energy, walker 0's upstream weights only
+    g = np.zeros((spec.nwalkers, 3), dtype=np.complex128)
+    g[0] = gen.upstream(spec)[0]
+    phi.copy_(torch.from_numpy(phis))
+    gphi, gh1 = sys_.local_energy_backward(phi, dev(g))
+    gphi0, gh1_h = host(gphi[:1])[0], host(gh1)
+    del gphi
     assert sys_.last_error() == (0, 0)
     sys_.close()
     del phi
@@ -76,3 +86,7 @@ def test_diamond_4x4x4_sampled():
     assert np.abs(ld_g[0].real - ld_own.real).max() < TOL_LD
     err = np.abs(e1[0] - energy(pn)) / spec.nk
     assert np.all(err < TOL_E), err
+    # the adjoint
+    ref_phi, ref_h = ok.local_energy_vjp(osys, phis[0], g[0], two_body=bench.gamma_in_pool(workers))
+    assert rel(gphi0, ref_phi) < 1e-5
+    assert rel(gh1_h, ref_h) < 1e-10
