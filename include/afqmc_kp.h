@@ -451,7 +451,8 @@ afqmc_status afqmc_kp_block(afqmc_kp_t h, void* phi, double* weight, double* x, 
  * precision) advanced by one call.  A group call forks from `stream` onto one
  * stream per member, runs every member's work there and joins back, so one
  * captured CUDA graph holds the whole group as concurrent branches and the small,
- * latency-bound kernels of different systems overlap on the GPU.  Each member
+ * latency-bound kernels of different systems overlap on the GPU.  Groups of mixed
+ * handles also share their GEMM launches (afqmc_kp_group_set_shared).  Each member
  * computes exactly what the same call on the member alone computes (bit for bit).
  * The walker sets of the members are the independent units of the paper's batching
  * (Sec. 3.2: operate on as many walkers at once as possible).
@@ -494,6 +495,23 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
 
 /* Kernel launches of the last group call, all members together. */
 afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches);
+
+/*
+ * afqmc_kp_group_set_shared -- shared GEMM launches for group_step and group_block
+ * (Sec. 3.2: all walkers of all systems in one batched operation).  With shared = 1
+ * every tensor-core GEMM of a step (the Green's function, the force bias, vHS, each
+ * Taylor term, the exchange) is one persistent launch on `stream` over the tiles of
+ * every member, each tile with its own member's operands, sizes and tensor maps; the
+ * small kernels between the GEMMs run on the member streams.  With shared = 0 every
+ * member launches its own GEMMs on its own stream.  Either way each member computes
+ * bit for bit what it computes alone.  A group of 1..8 mixed handles with one Taylor
+ * order starts shared; shared = 1 on any other group is AFQMC_ERR_UNSUPPORTED.
+ * GEMM time-outs of a shared launch are reported by the first member's
+ * afqmc_kp_last_error.
+ */
+afqmc_status afqmc_kp_group_set_shared(afqmc_kp_group_t g, int shared);
+/* Whether the group uses the shared GEMM launches (1) or not (0). */
+afqmc_status afqmc_kp_group_shared(afqmc_kp_group_t g, int* shared);
 
 /*
  * The tensor-core GEMMs of a mixed handle, and their autotuned TMA ring depth.  At create

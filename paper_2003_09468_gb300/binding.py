@@ -48,6 +48,8 @@ SIGNATURES = {
     "afqmc_kp_group_step": [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP],
     "afqmc_kp_group_block": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, ctypes.c_ulonglong, _VP, _VP],
     "afqmc_kp_group_launch_count": [_VP, ctypes.POINTER(_I)],
+    "afqmc_kp_group_set_shared": [_VP, _I],
+    "afqmc_kp_group_shared": [_VP, ctypes.POINTER(_I)],
     "afqmc_kp_gemm_tuning": [_VP, _VP, _VP, _VP, ctypes.POINTER(_I)],
     "afqmc_philox4x32_10": [_VP, ctypes.c_ulonglong, _VP, ctypes.c_size_t, _VP],
     "afqmc_kp_fields": [_VP, ctypes.c_ulonglong, _VP, _VP, _VP],
@@ -368,7 +370,8 @@ class DenseAFQMC(KPointAFQMC):
 
 
 class KPointGroup:
-    """Several KPointAFQMC systems advanced together, one CUDA stream per member."""
+    """Several KPointAFQMC systems advanced together, one CUDA stream per member; groups of up
+    to 8 mixed systems of one Taylor order share every GEMM launch (`shared`)."""
 
     def __init__(self, systems):
         self.lib = load_library()
@@ -429,6 +432,16 @@ class KPointGroup:
         n = ctypes.c_int(0)
         _check(self.lib.afqmc_kp_group_launch_count(self.group, ctypes.byref(n)), "afqmc_kp_group_launch_count")
         return n.value
+
+    @property
+    def shared(self) -> bool:
+        n = ctypes.c_int(0)
+        _check(self.lib.afqmc_kp_group_shared(self.group, ctypes.byref(n)), "afqmc_kp_group_shared")
+        return bool(n.value)
+
+    @shared.setter
+    def shared(self, on: bool):
+        _check(self.lib.afqmc_kp_group_set_shared(self.group, 1 if on else 0), "afqmc_kp_group_set_shared")
 
 
 def philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

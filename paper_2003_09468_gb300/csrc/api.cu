@@ -85,6 +85,12 @@ bool valid_desc(const afqmc_kp_desc* d) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+#define MTRY_API(x)                         \
+  do {                                      \
+    const cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return e_;       \
+  } while (0)
+
 // Complex arrays are read and written as 16-byte (re, im) vectors: NULL or 16-byte aligned.
 bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 bool al16(const void* a, const void* b, const void* c = nullptr, const void* d = nullptr) {
@@ -147,12 +153,16 @@ cudaError_t block_impl(afqmc_kp* h, void* phi, double* weight, double* x, void* 
 // A group of handles stepped together: one stream per member, forked from and joined
 // back to the caller's stream, so that a whole group call captures as one CUDA graph
 // whose branches run concurrently.
+// With `shared` set (mixed members of one Taylor order, at most mixed::GROUP_MAX of them),
+// every tensor-core GEMM of a step is one persistent launch over the tiles of all members on
+// the caller's stream, and only the small kernels between the GEMMs run on member streams.
 struct afqmc_kp_group {
   std::vector<afqmc_kp*> members;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
   int launches = 0;
+  bool shared = false;
 };
 
 namespace {
@@ -167,8 +177,7 @@ void group_free(afqmc_kp_group* g) {
 // Runs fn(i, member, member stream) for every member between a fork and a join on st.
 // Every member that was forked is joined, also after an error.
 template <typename F>
-cudaError_t group_run(afqmc_kp_group* g, cudaStream_t st, F&& fn) {
-  g->launches = 0;
+cudaError_t fork_join(afqmc_kp_group* g, cudaStream_t st, F&& fn) {
   cudaError_t e = cudaEventRecord(g->fork, st);
   if (e != cudaSuccess) return e;
   size_t forked = 0;
@@ -177,10 +186,7 @@ cudaError_t group_run(afqmc_kp_group* g, cudaStream_t st, F&& fn) {
     e = cudaStreamWaitEvent(g->streams[i], g->fork, 0);
     if (e != cudaSuccess) { err = e; break; }
     ++forked;
-    afqmc_kp* h = g->members[i];
-    h->launches = 0;
-    e = fn(i, h, g->streams[i]);
-    g->launches += h->launches;
+    e = fn((int)i, g->members[i], g->streams[i]);
     if (e != cudaSuccess) { err = e; break; }
   }
   for (size_t i = 0; i < forked; ++i) {
@@ -189,6 +195,84 @@ cudaError_t group_run(afqmc_kp_group* g, cudaStream_t st, F&& fn) {
     if (e != cudaSuccess && err == cudaSuccess) err = e;
   }
   return err;
+}
+
+// A group call: the launch counts of the members start at 0 and add up to the group's.
+template <typename F>
+cudaError_t group_run(afqmc_kp_group* g, F&& body) {
+  for (afqmc_kp* h : g->members) h->launches = 0;
+  const cudaError_t e = body();
+  g->launches = 0;
+  for (afqmc_kp* h : g->members) g->launches += h->launches;
+  return e;
+}
+
+bool group_shareable(const afqmc_kp_group* g) {
+  if (g->members.size() > (size_t)mixed::GROUP_MAX) return false;
+  for (const afqmc_kp* h : g->members)
+    if (!h->mixed || h->order != g->members[0]->order) return false;
+  return true;
+}
+
+// One step of every member with the shared GEMM launches (mixed::group_step); keeps each
+// member's stored-Green bookkeeping as step_impl does.
+cudaError_t group_step_shared(afqmc_kp_group* g, void* const* phi, const double* const* x, double* const* weight,
+                              void* const* eloc, void* const* logdet, int do_qr, int flags, cudaStream_t st) {
+  const size_t n = g->members.size();
+  std::vector<zc*> ph(n), el(n), ld(n);
+  std::vector<int> reuse(n);
+  for (size_t i = 0; i < n; ++i) {
+    afqmc_kp* h = g->members[i];
+    ph[i] = static_cast<zc*>(phi[i]);
+    el[i] = eloc ? static_cast<zc*>(eloc[i]) : nullptr;
+    ld[i] = logdet ? static_cast<zc*>(logdet[i]) : nullptr;
+    reuse[i] = (flags & AFQMC_STEP_REUSE_GREEN) && h->green_valid && h->green_phi == phi[i];
+    h->green_valid = false;
+  }
+  const mixed::ForEach each = [&](const mixed::MemberFn& fn) { return fork_join(g, st, fn); };
+  const cudaError_t e = mixed::group_step(g->members.data(), (int)n, ph.data(), x, weight, el.data(), ld.data(),
+                                          do_qr, reuse.data(), each, st);
+  if (e == cudaSuccess)
+    for (size_t i = 0; i < n; ++i) {
+      g->members[i]->green_valid = true;
+      g->members[i]->green_phi = phi[i];
+    }
+  return e;
+}
+
+// afqmc_kp_group_block with the shared GEMM launches: block_impl's sequence, every step
+// through group_step_shared.
+cudaError_t group_block_shared(afqmc_kp_group* g, void* const* phi, double* const* weight, double* const* x,
+                               void* const* eloc_hist, double* const* weight_hist, void* const* logdet, int nsteps,
+                               int qr_period, int energy_period, int flags, int comb, unsigned long long seed,
+                               unsigned long long* const* counter, cudaStream_t st) {
+  const size_t n = g->members.size();
+  std::vector<void*> el(n), ld(n);
+  for (int s = 0; s < nsteps; ++s) {
+    MTRY_API(fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t ms) {
+      return rng::fields(h, seed, counter[i], x[i], ms);
+    }));
+    const int do_qr = ((s + 1) % qr_period == 0) || s == nsteps - 1;
+    const int measure = ((s + 1) % energy_period == 0) || s == nsteps - 1;
+    for (size_t i = 0; i < n; ++i) {
+      el[i] = measure ? static_cast<void*>(static_cast<zc*>(eloc_hist[i]) +
+                                           (size_t)(s / energy_period) * g->members[i]->W * 3)
+                      : nullptr;
+      ld[i] = (s == nsteps - 1 && logdet) ? logdet[i] : nullptr;
+    }
+    MTRY_API(group_step_shared(g, phi, x, weight, el.data(), ld.data(), do_qr,
+                               s == 0 ? flags : AFQMC_STEP_REUSE_GREEN, st));
+    if (weight_hist)
+      MTRY_API(fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t ms) {
+        return cudaMemcpyAsync(weight_hist[i] + (size_t)s * h->W, weight[i], sizeof(double) * h->W,
+                               cudaMemcpyDeviceToDevice, ms);
+      }));
+  }
+  if (!comb) return cudaSuccess;
+  return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t ms) {
+    h->green_valid = false;
+    return rng::comb(h, static_cast<zc*>(phi[i]), weight[i], seed, counter[i], nullptr, ms);
+  });
 }
 
 }  // namespace
@@ -567,6 +651,7 @@ afqmc_status afqmc_kp_group_create(const afqmc_kp_t* systems, int nsys, afqmc_kp
       group_free(g);
       return from_cuda(e);
     }
+    g->shared = group_shareable(g);
   } catch (...) {
     group_free(g);
     return AFQMC_ERR_OOM;
@@ -593,9 +678,13 @@ afqmc_status afqmc_kp_group_step(afqmc_kp_group_t g, void* const* phi, const dou
   for (size_t i = 0; i < g->members.size(); ++i)
     if (!phi[i] || !x[i] || !weight[i] || !al16(phi[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr))
       return AFQMC_ERR_INVALID;
-  return from_cuda(group_run(g, as_stream(stream), [&](size_t i, afqmc_kp* h, cudaStream_t s) {
-    return step_impl(h, phi[i], x[i], weight[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr, do_qr,
-                     flags, s);
+  cudaStream_t st = as_stream(stream);
+  return from_cuda(group_run(g, [&] {
+    if (g->shared) return group_step_shared(g, phi, x, weight, eloc, logdet, do_qr, flags, st);
+    return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t s) {
+      return step_impl(h, phi[i], x[i], weight[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr, do_qr,
+                       flags, s);
+    });
   }));
 }
 
@@ -612,11 +701,30 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
       return AFQMC_ERR_INVALID;
     if (comb && rng::comb_smem_bytes(g->members[i]->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
   }
-  return from_cuda(group_run(g, as_stream(stream), [&](size_t i, afqmc_kp* h, cudaStream_t s) {
-    return block_impl(h, phi[i], weight[i], x[i], eloc_hist[i], weight_hist ? weight_hist[i] : nullptr,
-                      logdet ? logdet[i] : nullptr, nsteps, qr_period, energy_period, flags, comb, seed, counter[i],
-                      nullptr, s);
+  cudaStream_t st = as_stream(stream);
+  return from_cuda(group_run(g, [&] {
+    if (g->shared)
+      return group_block_shared(g, phi, weight, x, eloc_hist, weight_hist, logdet, nsteps, qr_period, energy_period,
+                                flags, comb, seed, counter, st);
+    return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t s) {
+      return block_impl(h, phi[i], weight[i], x[i], eloc_hist[i], weight_hist ? weight_hist[i] : nullptr,
+                        logdet ? logdet[i] : nullptr, nsteps, qr_period, energy_period, flags, comb, seed,
+                        counter[i], nullptr, s);
+    });
   }));
+}
+
+afqmc_status afqmc_kp_group_set_shared(afqmc_kp_group_t g, int shared) {
+  if (!g || (shared != 0 && shared != 1)) return AFQMC_ERR_INVALID;
+  if (shared && !group_shareable(g)) return AFQMC_ERR_UNSUPPORTED;
+  g->shared = shared != 0;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_group_shared(afqmc_kp_group_t g, int* shared) {
+  if (!g || !shared) return AFQMC_ERR_INVALID;
+  *shared = g->shared ? 1 : 0;
+  return AFQMC_OK;
 }
 
 afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches) {

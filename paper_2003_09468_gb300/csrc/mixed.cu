@@ -27,6 +27,8 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <functional>
+#include <utility>
 #include <vector>
 
 #include "mixed.hpp"
@@ -1791,12 +1793,12 @@ static cudaError_t overlap_logdet(afqmc_kp* h, const zc* phi, zc* ld, int* sing,
   return cudaSuccess;
 }
 
-static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+// The Green's function in three parts: the double-float overlap, inverse and log det and
+// the split of phi_perp (green_pre); the tensor-core GEMM; its max and split (green_post).
+static cudaError_t green_pre(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
   MixedState* m = h->mixed;
-  int* err = h->flags + 1;
   const int WS = m->WS;
   unsigned long long* mx_phi = m->mx;
-  unsigned long long* mx_g = m->mx + 2 * WS;
   // phi (A^dag phi)^-1 = B + phi_perp S^-1 with B = A (A^dag A)^-1 and phi_perp = phi - B S:
   // the trial-subspace part is exact, so the split GEMM never forms the large
   // cancelling partial sums of S^-1 (A^dag phi) = I.
@@ -1811,10 +1813,11 @@ static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStre
   split_rows32_kernel<<<dim3(WS, SPLIT_CHUNKS), 256, 0, st>>>(phi_perp, h->NM, h->N, m->Np, mx_phi, m->s_phi,
                                                                m->phi_sp);
   AFQMC_LAUNCHED(h);
-  MTRY(cudaGetLastError());
-  const GreenP p = green_params(h);
-  MTRY(run_gemm(h, m->m_sinvt, m->m_phi, p, err, st));
-  AFQMC_LAUNCHED(h);
+  return cudaGetLastError();
+}
+static cudaError_t green_post(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  unsigned long long* mx_g = m->mx + 2 * m->WS;
   green_max_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->g32, mx_g, h->nk, h->W, m->nMp);
   AFQMC_LAUNCHED(h);
   split_green_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->g32, mx_g, m->g_sp, m->s_g, m->gsum_sp, m->s_gsum,
@@ -1822,12 +1825,25 @@ static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStre
   AFQMC_LAUNCHED(h);
   return cudaGetLastError();
 }
+static cudaError_t green(afqmc_kp* h, const zc* phi, zc* ld, int* sing, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  MTRY(green_pre(h, phi, ld, sing, st));
+  MTRY(run_gemm(h, m->m_sinvt, m->m_phi, green_params(h), h->flags + 1, st));
+  AFQMC_LAUNCHED(h);
+  return green_post(h, st);
+}
 
+static cudaError_t trace_post(afqmc_kp* h, cudaStream_t st);
 static cudaError_t cholesky_trace(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
   const ForceBiasP p = force_bias_params(h);
   MTRY(run_gemm(h, m->m_lh, m->m_gsum, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
+  return trace_post(h, st);
+}
+// X from the group partials of the force-bias GEMM
+static cudaError_t trace_post(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
   const size_t per = (size_t)h->W * h->nk * h->G;
   xsum_kernel<<<(int)std::min<size_t>((per + 255) / 256, 4096), 256, 0, st>>>(m->xk, h->X, m->fb_groups, per);
   AFQMC_LAUNCHED(h);
@@ -1846,18 +1862,24 @@ cudaError_t force_bias(afqmc_kp* h, const zc* phi, zc* xbar, cudaStream_t st) {
   return e;
 }
 
-static cudaError_t vhs(afqmc_kp* h, cudaStream_t st) {
+static cudaError_t vhs_pre(afqmc_kp* h, cudaStream_t st) {
   MixedState* m = h->mixed;
   split_y_kernel<<<dim3(h->nk, h->W), 256, 0, st>>>(h->y, m->s_l, m->y_sp, m->s_y, h->nk, h->W, h->G, m->Gp);
   AFQMC_LAUNCHED(h);
-  MTRY(cudaGetLastError());
+  return cudaGetLastError();
+}
+static cudaError_t vhs(afqmc_kp* h, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  MTRY(vhs_pre(h, st));
   const VhsP p = vhs_params(h);
   MTRY(run_gemm(h, m->m_lt, m->m_y, p, h->flags + 1, st));
   AFQMC_LAUNCHED(h);
   return cudaSuccess;
 }
 
-static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
+// The Taylor series in three parts: the first one-body half step and the split of the
+// series' input (taylor_pre), the Horner GEMMs, the second half step (taylor_post).
+static cudaError_t taylor_pre(afqmc_kp* h, const zc* phi, cudaStream_t st) {
   MixedState* m = h->mixed;
   const int R = 2 * h->N;
   dim3 g1(h->nk, m->WS, cdiv(h->N, 64));
@@ -1871,7 +1893,24 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
   split_rows32_kernel<<<dim3(h->W, SPLIT_CHUNKS), 256, 0, st>>>(m->p32, R, h->NM, m->NMp, mx_acc, m->s_t, m->t_sp[0]);
   AFQMC_LAUNCHED(h);
   prof_end(h, st);
-  MTRY(cudaGetLastError());
+  return cudaGetLastError();
+}
+static cudaError_t taylor_post(afqmc_kp* h, zc* phi, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  dim3 g1(h->nk, m->WS, cdiv(h->N, 64));
+  float4* corr = reinterpret_cast<float4*>(m->acc);
+  prof_begin(h, AFQMC_STAGE_ONEBODY, st);
+  if (onebody_out_staged(h))
+    onebody_out_kernel<true><<<g1, 256, onebody_out_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
+  else
+    onebody_out_kernel<false><<<g1, 256, onebody_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
+  AFQMC_LAUNCHED(h);
+  prof_end(h, st);
+  return cudaGetLastError();
+}
+static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  MTRY(taylor_pre(h, phi, st));
   // Horner: u = phi'; u <- phi' + V u / j for j = order .. 1
   for (int j = h->order, step = 0; j >= 1; --j, ++step) {
     const int cur = step & 1, nxt = (step + 1) & 1;
@@ -1881,14 +1920,7 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
     prof_end(h, st);
     AFQMC_LAUNCHED(h);
   }
-  prof_begin(h, AFQMC_STAGE_ONEBODY, st);
-  if (onebody_out_staged(h))
-    onebody_out_kernel<true><<<g1, 256, onebody_out_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
-  else
-    onebody_out_kernel<false><<<g1, 256, onebody_smem(h), st>>>(corr, m->dhalf, phi, h->nk, h->M, h->N, h->NM);
-  AFQMC_LAUNCHED(h);
-  prof_end(h, st);
-  return cudaGetLastError();
+  return taylor_post(h, phi, st);
 }
 
 cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr, cudaStream_t st) {
@@ -2062,6 +2094,97 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
   std::swap(h->ld_old, h->ld_new);
   std::swap(h->sing_old, h->sing_new);
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// several handles stepped together (a group of uneven systems)
+// ---------------------------------------------------------------------------
+// One launch of policy P over the tiles of every listed handle (tcg::GroupP): mk(h) gives a
+// handle's parameters, maps(h) its (A, B) tensor maps.  Time-outs land in the first handle's
+// flags.  The TMA ring takes the policy's default depth: the depth changes no arithmetic.
+template <class P, class MK, class MAPS>
+static cudaError_t group_gemm(afqmc_kp* const* hs, int n, MK mk, MAPS maps, cudaStream_t st) {
+  constexpr int NMAX = GROUP_MAX;
+  if (n < 1 || n > NMAX) return cudaErrorInvalidValue;
+  tcg::GroupP<P, NMAX> g{};
+  g.n = n;
+  g.start[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    g.m[i] = mk(hs[i]);
+    // the member's tile groups must fit the 20 bits GroupP packs them in
+    if ((long long)g.m[i].tiles >= (1LL << 20) * g.m[i].mt_n * g.m[i].nt_n) return cudaErrorInvalidValue;
+    const auto mp = maps(hs[i]);
+    g.ma[i] = *mp.first;
+    g.mb[i] = *mp.second;
+    g.start[i + 1] = g.start[i] + g.m[i].tiles;
+  }
+  for (int i = n + 1; i <= NMAX; ++i) g.start[i] = g.start[n];
+  g.tiles = g.start[n];
+  g.kchunks = 0;
+  const auto mp0 = maps(hs[0]);
+  AFQMC_LAUNCHED(hs[0]);
+  return tcg::launch_precise<P::kStages>(*mp0.first, *mp0.second, g, hs[0]->flags + 1, st);
+}
+
+cudaError_t group_step(afqmc_kp* const* hs, int n, zc* const* phi, const double* const* x, double* const* w,
+                       zc* const* eloc, zc* const* logdet, int do_qr, const int* reuse, const ForEach& each,
+                       cudaStream_t st) {
+  using MP = std::pair<const CUtensorMap*, const CUtensorMap*>;
+  // force bias of the current walkers (their Green's function first where not reused), y
+  MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
+    if (!reuse[i]) {
+      MTRY(green(h, phi[i], h->ld_old, h->sing_old, s));
+      MTRY(cholesky_trace(h, s));
+    }
+    MTRY(fp64::force_bias(h, x[i], h->xbar, s));
+    return vhs_pre(h, s);
+  }));
+  MTRY(group_gemm<VhsP>(hs, n, [](const afqmc_kp* h) { return vhs_params(h); },
+                        [](const afqmc_kp* h) { return MP(&h->mixed->m_lt, &h->mixed->m_y); }, st));
+  MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) { return taylor_pre(h, phi[i], s); }));
+  const int order = hs[0]->order;
+  for (int j = order, step = 0; j >= 1; --j, ++step) {
+    const int cur = step & 1, nxt = (step + 1) & 1;
+    MTRY(group_gemm<TaylorP>(hs, n, [&](const afqmc_kp* h) { return taylor_params(h, j, nxt); },
+                             [&](const afqmc_kp* h) { return MP(&h->mixed->m_t[cur], &h->mixed->m_v); }, st));
+  }
+  // the propagated walkers' Green's function, the Cholesky trace, the weights
+  MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
+    MTRY(taylor_post(h, phi[i], s));
+    return green_pre(h, phi[i], h->ld_new, h->sing_new, s);
+  }));
+  MTRY(group_gemm<GreenP>(hs, n, [](const afqmc_kp* h) { return green_params(h); },
+                          [](const afqmc_kp* h) { return MP(&h->mixed->m_sinvt, &h->mixed->m_phi); }, st));
+  MTRY(each([&](int, afqmc_kp* h, cudaStream_t s) { return green_post(h, s); }));
+  MTRY(group_gemm<ForceBiasP>(hs, n, [](const afqmc_kp* h) { return force_bias_params(h); },
+                              [](const afqmc_kp* h) { return MP(&h->mixed->m_lh, &h->mixed->m_gsum); }, st));
+  MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
+    MTRY(trace_post(h, s));
+    MTRY(fp64::weight_only(h, x[i], w[i], do_qr ? nullptr : logdet[i], s));
+    return eloc[i] ? e1_ec(h, eloc[i], s) : cudaSuccess;
+  }));
+  // the exchange of the members that want their energy
+  std::vector<afqmc_kp*> ex;
+  for (int i = 0; i < n; ++i)
+    if (eloc[i]) ex.push_back(hs[i]);
+  if (!ex.empty())
+    MTRY(group_gemm<ExchangeP>(ex.data(), (int)ex.size(), [](const afqmc_kp* h) { return exchange_params(h); },
+                               [](const afqmc_kp* h) { return MP(&h->mixed->m_g, &h->mixed->m_z); }, st));
+  return each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
+    if (eloc[i]) MTRY(ex_reduce(h, eloc[i], s));
+    if (do_qr) {
+      MixedState* m = h->mixed;
+      MTRY(cholqr2(h, phi[i], m->logr, s));
+      ld_shift_kernel<<<cdiv(m->WS, 128), 128, 0, s>>>(h->ld_new, m->logr, h->sing_new, m->WS);
+      AFQMC_LAUNCHED(h);
+      MTRY(cudaGetLastError());
+      if (logdet[i])
+        MTRY(cudaMemcpyAsync(logdet[i], h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, s));
+    }
+    std::swap(h->ld_old, h->ld_new);
+    std::swap(h->sing_old, h->sing_new);
+    return cudaSuccess;
+  });
 }
 
 // dEX/dGh for every block (AdjointP GEMM into gam32).

@@ -103,6 +103,39 @@ struct StreamB<P, decltype((void)P::kStreamB)> {
   static constexpr bool value = P::kStreamB;
 };
 
+//   static constexpr bool kGrouped = true;
+//       the tiles of several problems in one launch (GroupP below): the k chunks of a tile
+//       and its operands' tensor maps depend on the tile (kchunks_of(b), map_a(b), map_b(b))
+template <class P, class = void>
+struct Grouped {
+  static constexpr bool value = false;
+};
+template <class P>
+struct Grouped<P, decltype((void)P::kGrouped)> {
+  static constexpr bool value = P::kGrouped;
+};
+template <class P>
+__device__ __forceinline__ int kchunks_of(const P& p, int b) {
+  if constexpr (Grouped<P>::value)
+    return p.kchunks_of(b);
+  else
+    return p.kchunks;
+}
+template <class P>
+__device__ __forceinline__ const CUtensorMap* map_a_of(const P& p, int b, const CUtensorMap* own) {
+  if constexpr (Grouped<P>::value)
+    return p.map_a(b);
+  else
+    return own;
+}
+template <class P>
+__device__ __forceinline__ const CUtensorMap* map_b_of(const P& p, int b, const CUtensorMap* own) {
+  if constexpr (Grouped<P>::value)
+    return p.map_b(b);
+  else
+    return own;
+}
+
 template <class P>
 __device__ __forceinline__ float chunk_factor(const P& p, int b, int kc) {
   if constexpr (ChunkScaled<P>::value)
@@ -144,7 +177,7 @@ struct LayoutP {
 template <int STAGES, class P>
 __global__ void __launch_bounds__(THREADS, 1)
     cgemm_precise_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                         const P p, int* err) {
+                         const __grid_constant__ P p, int* err) {
   // Persistent: CTA i handles tiles i, i + grid, i + 2 grid, ...  The TMA ring and the
   // two TMEM accumulator sets run continuously across tile boundaries.  One drain per 32-wide k
   // chunk: per accumulator the four small cross products of the chunk go first, then
@@ -186,14 +219,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   // consecutive, so the operands they share (one walker's rows, one Cholesky block)
   // are read from HBM once and served from L2 to the others
   const int t0 = blockIdx.x, tstep = gridDim.x;
-  const int KC = p.kchunks;
   constexpr int DC = DrainChunks<P>::value;
   static_assert(DC >= 1 && (DC == 1 || !ChunkScaled<P>::value), "one chunk factor per drained partial");
 
   if (warp == 0) {
     if (lane == 0) {
-      tc::tma_prefetch(&tmA);
-      tc::tma_prefetch(&tmB);
+      if constexpr (!Grouped<P>::value) {
+        tc::tma_prefetch(&tmA);
+        tc::tma_prefetch(&tmB);
+      }
       bool stream = false;
       if constexpr (StreamB<P>::value) stream = p.stream_b();
       const uint64_t stream_pol = stream ? tc::l2_evict_first_policy() : 0;
@@ -202,6 +236,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int t = t0; t < p.tiles && !failed; t += tstep) {
         int b, mt, nt;
         p.tile(t, b, mt, nt);
+        const int KC = kchunks_of(p, b);
+        const CUtensorMap* ma = map_a_of(p, b, &tmA);
+        const CUtensorMap* mb = map_b_of(p, b, &tmB);
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % STAGES);
           const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -214,12 +251,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
           const Coords c = p.coords(b, mt, nt, kc);
           uint8_t* sa = smem + s * Lay::STAGE_BYTES;
-          tc::tma_load_5d(sa, &tmA, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
+          tc::tma_load_5d(sa, ma, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
           if (stream)
-            tc::tma_load_5d_hint(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4],
+            tc::tma_load_5d_hint(sa + Lay::A_BYTES, mb, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4],
                                  stream_pol);
           else
-            tc::tma_load_5d(sa + Lay::A_BYTES, &tmB, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
+            tc::tma_load_5d(sa + Lay::A_BYTES, mb, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
         }
       }
       // every issued copy must land before the CTA may exit
@@ -237,6 +274,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       long a = 0;   // drained partials (accumulator sets), one per D chunks
       bool failed = false;
       for (int t = t0; t < p.tiles && !failed; t += tstep) {
+        int b, mt, nt;
+        p.tile(t, b, mt, nt);
+        const int KC = kchunks_of(p, b);
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % STAGES);
           const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -341,6 +381,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float sre[BNP], sim[BNP];
 #pragma unroll
       for (int c = 0; c < BNP; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
+      const int KC = kchunks_of(p, b);
       for (int kc = 0; kc < KC; kc += DC, ++g) {
         const int set = (int)(g & 1);
         const uint32_t use = (uint32_t)(g >> 1);
@@ -413,6 +454,40 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc::tmem_dealloc(tmem, Lay::TMEM_COLS);
   }
 }
+
+// ---------------------------------------------------------------- tile lists of several problems
+// The tiles of up to NMAX problems of one policy kind (the same GEMM of several systems) in one
+// persistent launch: tile t belongs to the member i with start[i] <= t < start[i + 1], and every
+// member keeps its own parameters, k chunks and tensor maps.  A member tile computes exactly
+// what it computes in its own launch.  The tile index handed to the member's policy is packed
+// with the member number (b = i << 20 | member tile group).
+template <class P, int NMAX = 8>
+struct GroupP {
+  static constexpr bool kConjA = P::kConjA;
+  static constexpr bool kPairB = PairB<P>::value;
+  static constexpr bool kGrouped = true;
+  static constexpr int kStages = P::kStages;
+  static_assert(!ChunkScaled<P>::value && DrainChunks<P>::value == 1, "plain policies only");
+  int tiles, kchunks;   // kchunks unused: per member
+  int n;
+  int start[NMAX + 1];
+  P m[NMAX];
+  CUtensorMap ma[NMAX], mb[NMAX];
+  __device__ void tile(int t, int& b, int& mt, int& nt) const {
+    int i = 0;
+    while (i + 1 < n && t >= start[i + 1]) ++i;
+    int bl;
+    m[i].tile(t - start[i], bl, mt, nt);
+    b = (i << 20) | bl;
+  }
+  __device__ Coords coords(int b, int mt, int nt, int kc) const { return m[b >> 20].coords(b & 0xFFFFF, mt, nt, kc); }
+  __device__ void store_tile(int b, int mt, int nt, const float2* tile, int tid, int ew, int lane) const {
+    m[b >> 20].store_tile(b & 0xFFFFF, mt, nt, tile, tid, ew, lane);
+  }
+  __device__ int kchunks_of(int b) const { return m[b >> 20].kchunks; }
+  __device__ const CUtensorMap* map_a(int b) const { return &ma[b >> 20]; }
+  __device__ const CUtensorMap* map_b(int b) const { return &mb[b >> 20]; }
+};
 
 // ---------------------------------------------------------------- host side
 // 5-D fp16 tensor map with 64-byte swizzle.  dims[0] is the contiguous k
