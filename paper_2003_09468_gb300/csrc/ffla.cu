@@ -422,34 +422,34 @@ __global__ void __launch_bounds__(GJ_THREADS)
       for (int jj = 0; jj < jb; ++jj) tmp[(size_t)jj * N + r] = a[(size_t)(j0 + jj) * N + c];
     }
     __syncthreads();
-    // ---- rank-jb update a[i][c] += sum_l (T - I)[i][j0 + l] tmp[l][c]: a warp takes two rows
-    // and 64 rest columns (lanes on consecutive columns), the multipliers are broadcast
+    // ---- rank-jb update a[i][c] += sum_l (T - I)[i][j0 + l] tmp[l][c]: a thread takes two
+    // rows and two rest columns r and r + H (H = ceil(R / 2)), consecutive threads consecutive
+    // r, so a warp reads tmp in one conflict-free run and (mostly) one row pair's multipliers
     {
-      const int row_pairs = (N + 1) / 2, col_blocks = (R + 63) / 64;
-      for (int u = warp; u < row_pairs * col_blocks; u += GJ_WARPS) {
-        const int i0 = 2 * (u / col_blocks), r0 = 64 * (u % col_blocks);
-        const int rA = r0 + lane, rB = r0 + lane + 32;
-        const bool okA = rA < R, okB = rB < R, ok1 = i0 + 1 < N;
+      const int row_pairs = (N + 1) / 2, H = (R + 1) / 2;
+      for (int u = tid; u < row_pairs * H; u += GJ_THREADS) {
+        const int i0 = 2 * (u / H), rA = u % H, rB = rA + H;
+        const bool okB = rB < R, ok1 = i0 + 1 < N;
         const int cA = (rA < j0) ? rA : rA + jb, cB = (rB < j0) ? rB : rB + jb;
-        ffa::cacc x00 = ffa::cacc_from(okA ? a[(size_t)i0 * N + cA] : ffa::czero());
+        ffa::cacc x00 = ffa::cacc_from(a[(size_t)i0 * N + cA]);
         ffa::cacc x01 = ffa::cacc_from(okB ? a[(size_t)i0 * N + cB] : ffa::czero());
-        ffa::cacc x10 = ffa::cacc_from((ok1 && okA) ? a[(size_t)(i0 + 1) * N + cA] : ffa::czero());
+        ffa::cacc x10 = ffa::cacc_from(ok1 ? a[(size_t)(i0 + 1) * N + cA] : ffa::czero());
         ffa::cacc x11 = ffa::cacc_from((ok1 && okB) ? a[(size_t)(i0 + 1) * N + cB] : ffa::czero());
         for (int l = 0; l < jb; ++l) {
           float4 d0 = a[(size_t)i0 * N + j0 + l];
           float4 d1 = ok1 ? a[(size_t)(i0 + 1) * N + j0 + l] : ffa::czero();
           if (i0 == j0 + l) d0 = ffa::pack(ffa::add(ffa::re(d0), ffa::make(-1.f, 0.f)), ffa::im(d0));
           if (i0 + 1 == j0 + l) d1 = ffa::pack(ffa::add(ffa::re(d1), ffa::make(-1.f, 0.f)), ffa::im(d1));
-          const float4 tA = okA ? tmp[(size_t)l * N + rA] : ffa::czero();
+          const float4 tA = tmp[(size_t)l * N + rA];
           const float4 tB = okB ? tmp[(size_t)l * N + rB] : ffa::czero();
           ffa::cacc_fma(x00, d0, tA);
           ffa::cacc_fma(x01, d0, tB);
           ffa::cacc_fma(x10, d1, tA);
           ffa::cacc_fma(x11, d1, tB);
         }
-        if (okA) a[(size_t)i0 * N + cA] = ffa::cacc_get(x00);
+        a[(size_t)i0 * N + cA] = ffa::cacc_get(x00);
         if (okB) a[(size_t)i0 * N + cB] = ffa::cacc_get(x01);
-        if (ok1 && okA) a[(size_t)(i0 + 1) * N + cA] = ffa::cacc_get(x10);
+        if (ok1) a[(size_t)(i0 + 1) * N + cA] = ffa::cacc_get(x10);
         if (ok1 && okB) a[(size_t)(i0 + 1) * N + cB] = ffa::cacc_get(x11);
       }
     }

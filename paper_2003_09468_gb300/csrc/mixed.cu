@@ -504,35 +504,54 @@ struct ExchangeP {
     tcg::Coords c = {{kc * 32, mt * 128, 0, kminus[q.y * nk + q.x], q.z}, {kc * 32, nt * BN, 0, 0, t}};
     return c;
   }
-  __device__ void store_tile(int t, int mt, int nt, const float2* tile, int tid, int, int) const {
-    const int ws = mt * 128 + tid, r = tid;
-    if (ws >= WS) return;
+  // Each store warp takes 32 rows of the tile, four at a time: eight lanes per row, each
+  // reading four 16-byte pieces of the row's partner run, so that one warp load covers four
+  // whole 128-byte lines.  Every load of the tile is issued before the first product.
+  __device__ void store_tile(int t, int mt, int nt, const float2* tile, int tid, int, int lane) const {
     const int4 q = tri[t];
     const int kxq = kminus[q.z * nk + minus[q.x]];  // kx + Q
-    const float4* g4 = reinterpret_cast<const float4*>(
-        g32 + (((size_t)q.y * nk + kxq) * WS + ws) * nMp + nt * BN);
+    const float2* gb = g32 + ((size_t)q.y * nk + kxq) * WS * nMp + nt * BN;
     // padding columns (s >= M) of Z_t are zero, so every column below n*Mp takes part
     const int pairs = min(BN, nMp - nt * BN) / 2;
-    float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
-    constexpr int U = BN / 2;   // the whole row's loads in flight at once
-    for (int j0 = 0; j0 < pairs; j0 += U) {
-      float4 gv[U];
+    const int ri = lane >> 3, cl = lane & 7, r0 = (tid >> 5) * 32;
+    constexpr int IT = 8, UJ = BN / 16;   // rows per lane, 16-byte pieces per lane and row
+    float4 gv[IT][UJ];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (j0 + u < pairs) gv[u] = g4[j0 + u];
+    for (int it = 0; it < IT; ++it) {
+      const int ws = mt * 128 + r0 + 4 * it + ri;
+      const float4* g4 = reinterpret_cast<const float4*>(gb + (size_t)ws * nMp);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int j = j0 + u;
-        if (j >= pairs) break;
-        const float2 y0 = tile[r * tcg::STAGE_LD + 2 * j], y1 = tile[r * tcg::STAGE_LD + 2 * j + 1];
-        pr0 = fmaf(y0.x, gv[u].x, fmaf(-y0.y, gv[u].y, pr0));
-        pi0 = fmaf(y0.x, gv[u].y, fmaf(y0.y, gv[u].x, pi0));
-        pr1 = fmaf(y1.x, gv[u].z, fmaf(-y1.y, gv[u].w, pr1));
-        pi1 = fmaf(y1.x, gv[u].w, fmaf(y1.y, gv[u].z, pi1));
+      for (int u = 0; u < UJ; ++u) {
+        const int j = cl + 8 * u;
+        gv[it][u] = (ws < WS && j < pairs) ? g4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    const float inv = 1.f / (s_g[ws] * s_z[t]);   // powers of two: exact after the sum
-    xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)((pr0 + pr1) * inv), (double)((pi0 + pi1) * inv));
+    const float inv_z = 1.f / s_z[t];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int r = r0 + 4 * it + ri, ws = mt * 128 + r;
+      float pr0 = 0.f, pi0 = 0.f, pr1 = 0.f, pi1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < UJ; ++u) {
+        const int j = cl + 8 * u;
+        const float2 y0 = tile[r * tcg::STAGE_LD + 2 * j], y1 = tile[r * tcg::STAGE_LD + 2 * j + 1];
+        const float4 g = gv[it][u];
+        pr0 = fmaf(y0.x, g.x, fmaf(-y0.y, g.y, pr0));
+        pi0 = fmaf(y0.x, g.y, fmaf(y0.y, g.x, pi0));
+        pr1 = fmaf(y1.x, g.z, fmaf(-y1.y, g.w, pr1));
+        pi1 = fmaf(y1.x, g.w, fmaf(y1.y, g.z, pi1));
+      }
+      float pr = pr0 + pr1, pi = pi0 + pi1;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
+      }
+      if (cl == 0 && ws < WS) {
+        const float inv = inv_z / s_g[ws];   // powers of two: exact after the sum
+        xpart[((size_t)t * nt_n + nt) * WS + ws] = make_double2((double)(pr * inv), (double)(pi * inv));
+      }
+    }
   }
 };
 
@@ -1587,11 +1606,15 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
         const bool canon = (Q < mQ) || (Q == mQ && k <= kx);
         if (canon) tri.push_back(make_int4(Q, k, kx, self ? 1 : 2));
       }
-  // Order the triples by the Green's-function block (k - Q, kx) that is their GEMM's A
-  // operand: the triples sharing a block then run on neighbouring CTAs at the same time
-  // and read it from HBM once.
+  // Order of the triples.  A triple reads two Green's-function blocks: (k - Q, kx), its
+  // GEMM's A operand, and (k, kx + Q), the partner its epilogue contracts with.  Both lie on
+  // the block diagonal d = k - Q - kx, so the triples are grouped by d first (the blocks a
+  // group touches, 2 Nk of them, stay in L2 while the group runs) and by the A block next
+  // (the triples sharing it run on neighbouring CTAs at the same time).
   std::stable_sort(tri.begin(), tri.end(), [&](const int4& a, const int4& b) {
     const int ka = h->h_kminus[(size_t)a.y * nk + a.x], kb = h->h_kminus[(size_t)b.y * nk + b.x];
+    const int da = h->h_kminus[(size_t)ka * nk + a.z], db = h->h_kminus[(size_t)kb * nk + b.z];
+    if (da != db) return da < db;
     return ka != kb ? ka < kb : a.z < b.z;
   });
   m->T = (int)tri.size();
