@@ -305,17 +305,26 @@ __global__ void __launch_bounds__(GJ_THREADS)
 // global memory (the overlap buffer, L2-resident while the CTA works on it): each panel then
 // reads and writes the matrix once, where the unblocked kernel does so once per pivot.
 constexpr int GJB = 8;
+static_assert(GJB == 8, "the panel's index arithmetic uses shifts by 3");
+constexpr int GJB_THREADS = 512;
+constexpr int GJB_WARPS = GJB_THREADS / 32;
 constexpr int GJB_MAXN = 112;   // N^2 + GJB N float4 + per-row arrays within SMEM_LIMIT
 constexpr int GJB_GLOBAL_MAXN = 1024;   // GJB N float4 + per-row arrays within SMEM_LIMIT
 
+// Pivot candidate key: larger |value| first, then the smaller row (m >= 0 and not NaN, so its
+// bits order as the values do).
+__device__ __forceinline__ unsigned long long pivot_key(float m, int i) {
+  return ((unsigned long long)__float_as_uint(m) << 32) | (unsigned long long)(0xffffffffu - (unsigned)i);
+}
+
 template <bool SMEM>
-__global__ void __launch_bounds__(GJ_THREADS)
+__global__ void __launch_bounds__(GJB_THREADS)
     gjb_ff_kernel(float4* Sff, int N, zc* logdet, int* sing, int* flags, __half* out, int Np, float* s_out) {
   extern __shared__ __align__(16) unsigned char gj_smem[];
-  __shared__ int s_p, s_sing, s_swaps;
-  __shared__ float4 s_pv, s_ajj;
-  __shared__ double s_red[GJ_WARPS];
-  __shared__ float s_redf[GJ_WARPS];
+  __shared__ int s_swaps;
+  __shared__ unsigned long long s_key[2];   // the next pivot's (|value|, row) key, two in turn
+  __shared__ double s_red[GJB_WARPS];
+  __shared__ float s_redf[GJB_WARPS];
   __shared__ int s_prow[GJB];
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4* g = Sff + (size_t)b * N * N;
@@ -326,67 +335,78 @@ __global__ void __launch_bounds__(GJ_THREADS)
   int* perm = reinterpret_cast<int*>(piv + N);
   int* iperm = perm + N;
   if (SMEM)
-    for (int e = tid; e < N * N; e += GJ_THREADS) a[e] = g[e];
-  for (int i = tid; i < N; i += GJ_THREADS) perm[i] = i;
-  if (tid == 0) {
-    s_sing = 0;
-    s_swaps = 0;
-  }
+    for (int e = tid; e < N * N; e += GJB_THREADS) a[e] = g[e];
+  for (int i = tid; i < N; i += GJB_THREADS) perm[i] = i;
+  if (tid == 0) s_swaps = 0;
   __syncthreads();
-  for (int j0 = 0; j0 < N && !s_sing; j0 += GJB) {
+  // Every thread reads the same shared pivot keys after the same barriers, so it takes the
+  // singular exit at the same step as the others.
+  bool singular_l = false;
+  for (int j0 = 0; j0 < N && !singular_l; j0 += GJB) {
     const int jb = min(GJB, N - j0);
     // ---- panel: columns [j0, j0 + jb), every row
+    // The pivot of column j is the row i >= j of largest |re.hi| + |im.hi| (the smallest i
+    // among equals).  The panel's first column was last written by the rank update and is
+    // searched by warp 0; every later column j + 1 is searched while the elimination of
+    // column j writes it (a warp maximum of the (|value|, row) keys, then one shared atomic
+    // maximum per warp), which saves the search's serial pass and a barrier per pivot.
     for (int jj = 0; jj < jb; ++jj) {
       const int j = j0 + jj;
-      if (warp == 0) {
-        float best = -1.f;
-        int bi = j;
-        for (int i = j + lane; i < N; i += 32) {
-          const float4 v = a[(size_t)i * N + j];
-          const float m = fabsf(v.x) + fabsf(v.z);
-          if (m > best) {
-            best = m;
-            bi = i;
+      if (jj == 0) {
+        if (warp == 0) {
+          float best = -1.f;
+          int bi = j;
+          for (int i = j + lane; i < N; i += 32) {
+            const float4 v = a[(size_t)i * N + j];
+            const float m = fabsf(v.x) + fabsf(v.z);
+            if (m > best) {
+              best = m;
+              bi = i;
+            }
           }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const float b2 = __shfl_xor_sync(FULL, best, o);
-          const int i2 = __shfl_xor_sync(FULL, bi, o);
-          if (b2 > best || (b2 == best && i2 < bi)) {
-            best = b2;
-            bi = i2;
+          for (int o = 16; o > 0; o >>= 1) {
+            const float b2 = __shfl_xor_sync(FULL, best, o);
+            const int i2 = __shfl_xor_sync(FULL, bi, o);
+            if (b2 > best || (b2 == best && i2 < bi)) {
+              best = b2;
+              bi = i2;
+            }
           }
+          if (lane == 0) s_key[0] = best >= 0.f ? pivot_key(best, bi) : 0ull;
         }
-        if (lane == 0) {
-          s_p = bi;
-          s_prow[jj] = bi;
-          s_pv = a[(size_t)bi * N + j];
-          s_ajj = a[(size_t)j * N + j];
-          if (!(best > 0.f) || !isfinite(best)) {
-            s_sing = 1;
-          } else if (bi != j) {
-            const int t = perm[j];
-            perm[j] = perm[bi];
-            perm[bi] = t;
-            ++s_swaps;
-          }
-        }
+        __syncthreads();
       }
-      __syncthreads();
-      if (s_sing) break;   // the same shared value for every thread after the barrier
-      const int p = s_p;
-      const float4 pv = s_pv, ajj = s_ajj;
+      const unsigned long long key = s_key[jj & 1];
+      const float best = __uint_as_float((unsigned)(key >> 32));
+      if (!(best > 0.f) || !isfinite(best)) {
+        singular_l = true;
+        break;
+      }
+      const int p = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+      const float4 pv = a[(size_t)p * N + j], ajj = a[(size_t)j * N + j];
       const float4 inv = ffa::crecip(pv);
-      if (tid == 0) piv[j] = make_double2(ffa::to_double(ffa::re(pv)), ffa::to_double(ffa::im(pv)));
-      // swap rows j and p and scale row j, panel columns only
-      for (int cc = tid; cc < jb; cc += GJ_THREADS) {
+      if (tid == 0) {
+        s_prow[jj] = p;
+        if (p != j) {
+          const int t = perm[j];
+          perm[j] = perm[p];
+          perm[p] = t;
+          ++s_swaps;
+        }
+        piv[j] = make_double2(ffa::to_double(ffa::re(pv)), ffa::to_double(ffa::im(pv)));
+        s_key[(jj + 1) & 1] = 0ull;   // read last before the previous step's barriers
+      }
+      // swap rows j and p and scale row j, panel columns other than j (the elimination below
+      // writes column j whole: inv in row j, -f inv elsewhere)
+      for (int cc = tid; cc < jb; cc += GJB_THREADS) {
         const int c = j0 + cc;
+        if (c == j) continue;
         const float4 tj = a[(size_t)j * N + c];
         const float4 tp = (p == j) ? tj : a[(size_t)p * N + c];
-        a[(size_t)j * N + c] = (c == j) ? inv : ffa::cmul(tp, inv);
+        a[(size_t)j * N + c] = ffa::cmul(tp, inv);
         if (p != j) a[(size_t)p * N + c] = tj;
       }
-      for (int i = tid; i < N; i += GJ_THREADS) {
+      for (int i = tid; i < N; i += GJB_THREADS) {
         if (i == j)
           f[i] = ffa::czero();
         else
@@ -395,21 +415,34 @@ __global__ void __launch_bounds__(GJ_THREADS)
       __syncthreads();
       // eliminate column j from every other row, panel columns only: one thread per
       // (row, panel column)
-      for (int e = tid; e < N * jb; e += GJ_THREADS) {
-        const int i = e / jb, c = j0 + e % jb;
+      unsigned long long cand = 0ull;
+      for (int e = tid; e < N * jb; e += GJB_THREADS) {
+        const int i = (jb == GJB) ? (e >> 3) : e / jb, c = j0 + ((jb == GJB) ? (e & 7) : e % jb);
+        if (c == j) {
+          a[(size_t)i * N + c] = (i == j) ? inv : ffa::cneg(ffa::cmul(f[i], inv));
+          continue;
+        }
         if (i == j) continue;
-        const float4 fi = f[i];
-        if (c == j)
-          a[(size_t)i * N + c] = ffa::cneg(ffa::cmul(fi, inv));
-        else
-          a[(size_t)i * N + c] = ffa::cfms(a[(size_t)i * N + c], fi, a[(size_t)j * N + c]);
+        const float4 v = ffa::cfms(a[(size_t)i * N + c], f[i], a[(size_t)j * N + c]);
+        a[(size_t)i * N + c] = v;
+        if (c == j + 1 && i > j) {
+          const float m = fabsf(v.x) + fabsf(v.z);
+          if (!isnan(m)) cand = max(cand, pivot_key(m, i));
+        }
+      }
+      if (jj + 1 < jb) {
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long other = __shfl_xor_sync(FULL, cand, o);
+          cand = other > cand ? other : cand;
+        }
+        if (lane == 0 && cand) atomicMax(&s_key[(jj + 1) & 1], cand);
       }
       __syncthreads();
     }
-    if (s_sing) break;
+    if (singular_l) break;
     // ---- every other column: the panel's row swaps in order, a copy of the panel rows
     const int R = N - jb;   // rest column r -> c = r < j0 ? r : r + jb
-    for (int r = tid; r < R; r += GJ_THREADS) {
+    for (int r = tid; r < R; r += GJB_THREADS) {
       const int c = (r < j0) ? r : r + jb;
       for (int jj = 0; jj < jb; ++jj) {
         const int j = j0 + jj, p = s_prow[jj];
@@ -422,43 +455,36 @@ __global__ void __launch_bounds__(GJ_THREADS)
       for (int jj = 0; jj < jb; ++jj) tmp[(size_t)jj * N + r] = a[(size_t)(j0 + jj) * N + c];
     }
     __syncthreads();
-    // ---- rank-jb update a[i][c] += sum_l (T - I)[i][j0 + l] tmp[l][c]: a thread takes two
-    // rows and two rest columns r and r + H (H = ceil(R / 2)), consecutive threads consecutive
-    // r, so a warp reads tmp in one conflict-free run and (mostly) one row pair's multipliers
+    // ---- rank-jb update a[i][c] += sum_l (T - I)[i][j0 + l] tmp[l][c]: a thread takes one
+    // row and two rest columns r and r + H (H = ceil(R / 2)), consecutive threads consecutive
+    // r, so a warp reads tmp in one conflict-free run and (mostly) one row's multipliers;
+    // N H tasks spread evenly over the threads
     {
-      const int row_pairs = (N + 1) / 2, H = (R + 1) / 2;
-      for (int u = tid; u < row_pairs * H; u += GJ_THREADS) {
-        const int i0 = 2 * (u / H), rA = u % H, rB = rA + H;
-        const bool okB = rB < R, ok1 = i0 + 1 < N;
+      const int H = (R + 1) / 2;
+      for (int u = tid; u < N * H; u += GJB_THREADS) {
+        const int i = u / H, rA = u % H, rB = rA + H;
+        const bool okB = rB < R;
         const int cA = (rA < j0) ? rA : rA + jb, cB = (rB < j0) ? rB : rB + jb;
-        ffa::cacc x00 = ffa::cacc_from(a[(size_t)i0 * N + cA]);
-        ffa::cacc x01 = ffa::cacc_from(okB ? a[(size_t)i0 * N + cB] : ffa::czero());
-        ffa::cacc x10 = ffa::cacc_from(ok1 ? a[(size_t)(i0 + 1) * N + cA] : ffa::czero());
-        ffa::cacc x11 = ffa::cacc_from((ok1 && okB) ? a[(size_t)(i0 + 1) * N + cB] : ffa::czero());
+        ffa::cacc xA = ffa::cacc_from(a[(size_t)i * N + cA]);
+        ffa::cacc xB = ffa::cacc_from(okB ? a[(size_t)i * N + cB] : ffa::czero());
         for (int l = 0; l < jb; ++l) {
-          float4 d0 = a[(size_t)i0 * N + j0 + l];
-          float4 d1 = ok1 ? a[(size_t)(i0 + 1) * N + j0 + l] : ffa::czero();
-          if (i0 == j0 + l) d0 = ffa::pack(ffa::add(ffa::re(d0), ffa::make(-1.f, 0.f)), ffa::im(d0));
-          if (i0 + 1 == j0 + l) d1 = ffa::pack(ffa::add(ffa::re(d1), ffa::make(-1.f, 0.f)), ffa::im(d1));
+          float4 d = a[(size_t)i * N + j0 + l];
+          if (i == j0 + l) d = ffa::pack(ffa::add(ffa::re(d), ffa::make(-1.f, 0.f)), ffa::im(d));
           const float4 tA = tmp[(size_t)l * N + rA];
           const float4 tB = okB ? tmp[(size_t)l * N + rB] : ffa::czero();
-          ffa::cacc_fma(x00, d0, tA);
-          ffa::cacc_fma(x01, d0, tB);
-          ffa::cacc_fma(x10, d1, tA);
-          ffa::cacc_fma(x11, d1, tB);
+          ffa::cacc_fma(xA, d, tA);
+          ffa::cacc_fma(xB, d, tB);
         }
-        a[(size_t)i0 * N + cA] = ffa::cacc_get(x00);
-        if (okB) a[(size_t)i0 * N + cB] = ffa::cacc_get(x01);
-        if (ok1) a[(size_t)(i0 + 1) * N + cA] = ffa::cacc_get(x10);
-        if (ok1 && okB) a[(size_t)(i0 + 1) * N + cB] = ffa::cacc_get(x11);
+        a[(size_t)i * N + cA] = ffa::cacc_get(xA);
+        if (okB) a[(size_t)i * N + cB] = ffa::cacc_get(xB);
       }
     }
     __syncthreads();
   }
-  const int singular = s_sing;
+  const int singular = singular_l;
   double lg = 0.0, an = 0.0;
   if (!singular)
-    for (int i = tid; i < N; i += GJ_THREADS) {
+    for (int i = tid; i < N; i += GJB_THREADS) {
       const double2 v = piv[i];
       lg += 0.5 * log(v.x * v.x + v.y * v.y);
       an += atan2(v.y, v.x);
@@ -480,20 +506,20 @@ __global__ void __launch_bounds__(GJ_THREADS)
   const size_t ps = (size_t)N * Np;
   __half* o = out + (size_t)b * 4 * ps;
   if (singular) {
-    for (int e = tid; e < N * N; e += GJ_THREADS) mixed::put4f(o, ps, (size_t)(e / N) * Np + e % N, 0.f, 0.f);
+    for (int e = tid; e < N * N; e += GJB_THREADS) mixed::put4f(o, ps, (size_t)(e / N) * Np + e % N, 0.f, 0.f);
     if (tid == 0) s_out[b] = 1.f;
     return;
   }
-  for (int c = tid; c < N; c += GJ_THREADS) iperm[perm[c]] = c;
+  for (int c = tid; c < N; c += GJB_THREADS) iperm[perm[c]] = c;
   float m = 0.f;
-  for (int e = tid; e < N * N; e += GJ_THREADS) {
+  for (int e = tid; e < N * N; e += GJB_THREADS) {
     const float4 v = a[e];
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.z)));
   }
   m = block_max_f(m, s_redf);   // its barriers also publish iperm
   const float sc = mixed::pow2_scale((double)m);
   if (tid == 0) s_out[b] = sc;
-  for (int e = tid; e < N * N; e += GJ_THREADS) {
+  for (int e = tid; e < N * N; e += GJB_THREADS) {
     const int i = e / N, c = e % N;
     const float4 v = a[(size_t)c * N + iperm[i]];
     mixed::put4f(o, ps, (size_t)i * Np + c, v.x * sc, v.z * sc);
@@ -539,7 +565,7 @@ cudaError_t invert(float4* Sff, int WS, int N, zc* logdet, int* sing, int* flags
     const size_t bytes = ((size_t)N * N + (size_t)GJB * N) * sizeof(float4) + gj_smem_bytes(N, false);
     if (bytes <= SMEM_LIMIT) {
       if ((e = set_smem(gjb_ff_kernel<true>, bytes)) != cudaSuccess) return e;
-      gjb_ff_kernel<true><<<WS, GJ_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
+      gjb_ff_kernel<true><<<WS, GJB_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
       return cudaGetLastError();
     }
   }
@@ -547,7 +573,7 @@ cudaError_t invert(float4* Sff, int WS, int N, zc* logdet, int* sing, int* flags
     const size_t bytes = (size_t)GJB * N * sizeof(float4) + gj_smem_bytes(N, false);
     if (bytes <= SMEM_LIMIT) {
       if ((e = set_smem(gjb_ff_kernel<false>, bytes)) != cudaSuccess) return e;
-      gjb_ff_kernel<false><<<WS, GJ_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
+      gjb_ff_kernel<false><<<WS, GJB_THREADS, bytes, st>>>(Sff, N, logdet, sing, flags, out, Np, s_out);
       return cudaGetLastError();
     }
   }
