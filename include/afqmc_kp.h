@@ -541,6 +541,26 @@ typedef enum {
  */
 afqmc_status afqmc_kp_gemm_tuning(afqmc_kp_t h, int* depth, double* ms2, double* ms3, int* count);
 
+/*
+ * afqmc_kp_gemm_form -- the tile form of one GEMM of a mixed handle.  *pair = 1: the CTA-pair
+ * form (tcgen05 cta_group::2), where two SMs of a cluster compute 256-row tiles and each
+ * stages its own 128 rows of A and one half (real or imaginary planes) of the paired B
+ * operand, so the B operand is read from shared memory once per pair; *pair = 0: 128-row
+ * tiles on one SM.  Only the Taylor-term GEMM (Sec. 3.2 step 3, more than one row tile per
+ * walker) has the pair form: at create the library times it at the tuned ring depth and keeps
+ * it when faster by more than 2%.  *ms_pair = that per-launch time in ms (0 if not timed, -1
+ * if the device refused the cluster launch).  Both forms compute every output element with
+ * the same products in the same order.  AFQMC_ERR_INVALID for NULL pointers or gemm out of
+ * range; an FP64 handle reports 0.
+ */
+afqmc_status afqmc_kp_gemm_form(afqmc_kp_t h, int gemm, int* pair, double* ms_pair);
+/*
+ * afqmc_kp_set_gemm_form -- override the form chosen at create (pair 0 or 1).
+ * AFQMC_ERR_UNSUPPORTED for pair = 1 on a GEMM or handle without the pair form (FP64, or
+ * one row tile per walker), AFQMC_ERR_INVALID for other arguments out of range.
+ */
+afqmc_status afqmc_kp_set_gemm_form(afqmc_kp_t h, int gemm, int pair);
+
 /* Static, NUL-terminated description of a status code. */
 const char* afqmc_status_string(afqmc_status s);
 

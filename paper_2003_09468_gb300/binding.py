@@ -51,6 +51,8 @@ SIGNATURES = {
     "afqmc_kp_group_set_shared": [_VP, _I],
     "afqmc_kp_group_shared": [_VP, ctypes.POINTER(_I)],
     "afqmc_kp_gemm_tuning": [_VP, _VP, _VP, _VP, ctypes.POINTER(_I)],
+    "afqmc_kp_gemm_form": [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)],
+    "afqmc_kp_set_gemm_form": [_VP, _I, _I],
     "afqmc_philox4x32_10": [_VP, ctypes.c_ulonglong, _VP, ctypes.c_size_t, _VP],
     "afqmc_kp_fields": [_VP, ctypes.c_ulonglong, _VP, _VP, _VP],
     "afqmc_kp_comb": [_VP, _VP, _VP, ctypes.c_ulonglong, _VP, _VP, _VP],
@@ -322,8 +324,25 @@ class KPointAFQMC:
         cnt = ctypes.c_int(0)
         _check(self.lib.afqmc_kp_gemm_tuning(self.handle, depth, ms2, ms3, ctypes.byref(cnt)),
                "afqmc_kp_gemm_tuning")
-        return {self.GEMMS[i]: {"ring_depth": depth[i], "ms_2_stages": ms2[i], "ms_3_stages": ms3[i]}
-                for i in range(cnt.value)}
+        out = {self.GEMMS[i]: {"ring_depth": depth[i], "ms_2_stages": ms2[i], "ms_3_stages": ms3[i]}
+               for i in range(cnt.value)}
+        for name in out:
+            pair, ms = self.gemm_form(name)
+            out[name]["cta_pair"] = pair
+            if ms != 0.0:
+                out[name]["ms_cta_pair"] = ms
+        return out
+
+    def gemm_form(self, gemm: str):
+        """(pair, ms_pair): whether the GEMM runs in the CTA-pair form, and its ms at create."""
+        pair, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(self.lib.afqmc_kp_gemm_form(self.handle, self.GEMMS.index(gemm), ctypes.byref(pair), ctypes.byref(ms)),
+               "afqmc_kp_gemm_form")
+        return bool(pair.value), ms.value
+
+    def set_gemm_form(self, gemm: str, pair: bool):
+        _check(self.lib.afqmc_kp_set_gemm_form(self.handle, self.GEMMS.index(gemm), 1 if pair else 0),
+               "afqmc_kp_set_gemm_form")
 
 
 def _ptr_array(ptrs):

@@ -745,6 +745,23 @@ afqmc_status afqmc_kp_gemm_tuning(afqmc_kp_t h, int* depth, double* ms2, double*
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_kp_gemm_form(afqmc_kp_t h, int gemm, int* pair, double* ms_pair) {
+  if (!h || !pair || !ms_pair || gemm < 0 || gemm >= AFQMC_NGEMMS) return AFQMC_ERR_INVALID;
+  if (!h->mixed) {
+    *pair = 0;
+    *ms_pair = 0.0;
+    return AFQMC_OK;
+  }
+  mixed::gemm_form(h, gemm, pair, ms_pair);
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kp_set_gemm_form(afqmc_kp_t h, int gemm, int pair) {
+  if (!h || gemm < 0 || gemm >= AFQMC_NGEMMS || (pair != 0 && pair != 1)) return AFQMC_ERR_INVALID;
+  if (!h->mixed) return pair ? AFQMC_ERR_UNSUPPORTED : AFQMC_OK;
+  return mixed::set_gemm_form(h, gemm, pair) ? AFQMC_OK : AFQMC_ERR_UNSUPPORTED;
+}
+
 afqmc_status afqmc_kp_launch_count(afqmc_kp_t h, int* launches) {
   if (!h || !launches) return AFQMC_ERR_INVALID;
   *launches = h->launches;

@@ -77,6 +77,11 @@ struct MixedState {
   // and the per-launch times measured for two and three stages (0 where not tuned)
   int ring[AFQMC_NGEMMS] = {0};
   float tune_ms[AFQMC_NGEMMS][2] = {};
+  // Taylor GEMM in the CTA-pair form (chosen at create when it times faster), its B map (one
+  // of the re / im halves per box) and the per-launch ms of the pair form at create
+  int taylor_pair = 0;
+  float taylor_pair_ms = 0.f;
+  CUtensorMap m_vp;
   CUtensorMap m_sinvt, m_phi, m_gsum, m_lh, m_y, m_lt, m_t[2], m_v, m_g, m_z, m_zall;
   CUtensorMap m_phi_a, m_sinvt_b, m_t0_b;  // the same buffers boxed for the other operand slot
   std::vector<void*> allocs;
@@ -185,15 +190,16 @@ static cudaError_t map5(CUtensorMap* m, void* base, std::initializer_list<uint64
 // re_hi, re_lo, im_hi, im_lo in memory) are addressed as the two dimensions (re/im, hi/lo),
 // so the staged box holds them as re_hi, im_hi, re_lo, im_lo; d0, d1 and the batch dimension
 // keep their element strides e0 (rows) and eb.
+// halves = 1: the box holds one of re / im (the CTA-pair form, each CTA staging its half).
 static cudaError_t map5_pair(CUtensorMap* m, void* base, uint64_t d0, uint64_t d1, uint64_t batch, uint64_t e0,
-                             uint64_t ps, uint64_t eb, uint32_t rows) {
+                             uint64_t ps, uint64_t eb, uint32_t rows, uint32_t halves = 2) {
   tcg::MapSpec s;
   s.dims[0] = d0; s.dims[1] = d1; s.dims[2] = 2; s.dims[3] = 2; s.dims[4] = batch;
   s.strides[0] = e0 * sizeof(__half);
   s.strides[1] = 2 * ps * sizeof(__half);   // re -> im
   s.strides[2] = ps * sizeof(__half);       // hi -> lo
   s.strides[3] = eb * sizeof(__half);
-  s.box[0] = 32; s.box[1] = rows; s.box[2] = 2; s.box[3] = 2; s.box[4] = 1;
+  s.box[0] = 32; s.box[1] = rows; s.box[2] = halves; s.box[3] = 2; s.box[4] = 1;
   return tcg::make_map(m, base, s);
 }
 
@@ -1487,6 +1493,15 @@ static TaylorP taylor_params(const afqmc_kp* h, int j, int nxt) {
   p.s_t = m->s_t; p.p32 = m->p32; p.corr = reinterpret_cast<float4*>(m->acc); p.t_next = m->t_sp[nxt];
   return p;
 }
+// The same term in the CTA-pair form: mt_n counts pairs of 128-row tiles.
+static TaylorP taylor_params_pair(const afqmc_kp* h, int j, int nxt) {
+  TaylorP p = taylor_params(h, j, nxt);
+  p.mt_n = cdiv(p.mt_n, 2);
+  p.tiles = h->W * p.mt_n * p.nt_n;
+  return p;
+}
+// One Taylor-term GEMM in the form chosen at create.
+static cudaError_t taylor_gemm(afqmc_kp* h, int j, int cur, int nxt, cudaStream_t st);
 static ExchangeP exchange_params(const afqmc_kp* h) {
   const MixedState* m = h->mixed;
   ExchangeP p;
@@ -1549,6 +1564,26 @@ static cudaError_t autotune(afqmc_kp* h, cudaStream_t st) {
   if (e == cudaSuccess) e = tune_gemm(h, m->m_lh, m->m_gsum, force_bias_params(h), st, e0, e1);
   if (e == cudaSuccess) e = tune_gemm(h, m->m_lt, m->m_y, vhs_params(h), st, e0, e1);
   if (e == cudaSuccess) e = tune_gemm(h, m->m_t[0], m->m_v, taylor_params(h, 2, 1), st, e0, e1);
+  if (e == cudaSuccess && taylor_params(h, 2, 1).mt_n > 1) {
+    // the CTA-pair form at the tuned ring depth: kept when faster by more than 2%
+    // (a launch the device refuses, e.g. a cluster it cannot place, leaves the single form)
+    float t = 0.f;
+    m->taylor_pair = 1;
+    cudaError_t ep = taylor_gemm(h, 2, 0, 1, st);
+    if (ep == cudaSuccess) ep = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && ep == cudaSuccess; ++r) ep = taylor_gemm(h, 2, 0, 1, st);
+    if (ep == cudaSuccess) ep = cudaEventRecord(e1, st);
+    if (ep == cudaSuccess) ep = cudaEventSynchronize(e1);
+    if (ep == cudaSuccess) ep = cudaEventElapsedTime(&t, e0, e1);
+    const int id = AFQMC_GEMM_TAYLOR;
+    m->taylor_pair_ms = ep == cudaSuccess ? t / 3.f : -1.f;
+    m->taylor_pair = (ep == cudaSuccess && t / 3.f < 0.98f * m->tune_ms[id][m->ring[id] - 2]) ? 1 : 0;
+    if (ep == cudaErrorInvalidConfiguration || ep == cudaErrorLaunchOutOfResources ||
+        ep == cudaErrorInvalidValue || ep == cudaErrorNotSupported)
+      (void)cudaGetLastError();   // a refused launch: not sticky
+    else
+      e = ep;
+  }
   if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_z, exchange_params(h), st, e0, e1);
   if (e == cudaSuccess) e = tune_gemm(h, m->m_g, m->m_zall, adjoint_params(h), st, e0, e1);
   // the QR GEMMs write the caller's walkers: they keep their defaults
@@ -1746,6 +1781,8 @@ static cudaError_t create_impl(afqmc_kp* h, cudaStream_t st) {
               {(uint64_t)NMp, (uint64_t)2 * N * NMp, (uint64_t)4 * 2 * N * NMp, (uint64_t)W * 4 * 2 * N * NMp}, 128));
   MTRY(map5_pair(&m->m_v, m->v_sp, (uint64_t)NMp, (uint64_t)NM, (uint64_t)W, (uint64_t)NMp, (uint64_t)NM * NMp,
                  (uint64_t)4 * NM * NMp, BN));
+  MTRY(map5_pair(&m->m_vp, m->v_sp, (uint64_t)NMp, (uint64_t)NM, (uint64_t)W, (uint64_t)NMp, (uint64_t)NM * NMp,
+                 (uint64_t)4 * NM * NMp, BN, 1));
   MTRY(map5(&m->m_g, m->g_sp, {(uint64_t)nMp, (uint64_t)WS, 4, (uint64_t)nk, (uint64_t)nk},
             {(uint64_t)nMp, (uint64_t)nk * nk * WS * nMp, (uint64_t)WS * nMp, (uint64_t)nk * WS * nMp}, 128));
   // the exchange reads the canonical rows, the adjoint every row
@@ -1777,6 +1814,18 @@ void gemm_tuning(const afqmc_kp* h, int* depth, double* ms2, double* ms3) {
     ms2[i] = m->tune_ms[i][0];
     ms3[i] = m->tune_ms[i][1];
   }
+}
+
+void gemm_form(const afqmc_kp* h, int gemm, int* pair, double* ms_pair) {
+  const MixedState* m = h->mixed;
+  const bool t = gemm == AFQMC_GEMM_TAYLOR;
+  *pair = t ? m->taylor_pair : 0;
+  *ms_pair = t ? m->taylor_pair_ms : 0.0;
+}
+bool set_gemm_form(afqmc_kp* h, int gemm, int pair) {
+  if (pair && (gemm != AFQMC_GEMM_TAYLOR || taylor_params(h, 2, 1).mt_n < 2)) return false;
+  if (gemm == AFQMC_GEMM_TAYLOR) h->mixed->taylor_pair = pair;
+  return true;
 }
 
 afqmc_status create(afqmc_kp* h, cudaStream_t st) {
@@ -1932,18 +1981,24 @@ static cudaError_t taylor_post(afqmc_kp* h, zc* phi, cudaStream_t st) {
   return cudaGetLastError();
 }
 static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
-  MixedState* m = h->mixed;
   MTRY(taylor_pre(h, phi, st));
   // Horner: u = phi'; u <- phi' + V u / j for j = order .. 1
   for (int j = h->order, step = 0; j >= 1; --j, ++step) {
     const int cur = step & 1, nxt = (step + 1) & 1;
-    const TaylorP p = taylor_params(h, j, nxt);
     prof_begin(h, AFQMC_STAGE_TAYLOR, st);   // one interval per term: the GEMM launch alone
-    MTRY(run_gemm(h, m->m_t[cur], m->m_v, p, h->flags + 1, st));
+    MTRY(taylor_gemm(h, j, cur, nxt, st));
     prof_end(h, st);
     AFQMC_LAUNCHED(h);
   }
   return taylor_post(h, phi, st);
+}
+static cudaError_t taylor_gemm(afqmc_kp* h, int j, int cur, int nxt, cudaStream_t st) {
+  MixedState* m = h->mixed;
+  if (!m->taylor_pair) return run_gemm(h, m->m_t[cur], m->m_v, taylor_params(h, j, nxt), h->flags + 1, st);
+  const TaylorP p = taylor_params_pair(h, j, nxt);
+  const int r = m->ring[AFQMC_GEMM_TAYLOR];
+  return (r ? r : TaylorP::kStages) == 2 ? tcg::launch_precise_pair<2>(m->m_t[cur], m->m_vp, p, h->flags + 1, st)
+                                         : tcg::launch_precise_pair<3>(m->m_t[cur], m->m_vp, p, h->flags + 1, st);
 }
 
 cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr, cudaStream_t st) {

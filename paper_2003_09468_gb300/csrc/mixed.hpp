@@ -31,4 +31,8 @@ cudaError_t group_step(afqmc_kp* const* hs, int n, zc* const* phi, const double*
                        cudaStream_t st);
 // ring depth of every GEMM and the per-launch ms timed for two and three stages at create
 void gemm_tuning(const afqmc_kp* h, int* depth, double* ms2, double* ms3);
+// The Taylor GEMM's CTA-pair form: whether it is used, its ms at create, and whether the
+// handle has it at all (more than one 128-row tile per walker).
+void gemm_form(const afqmc_kp* h, int gemm, int* pair, double* ms_pair);
+bool set_gemm_form(afqmc_kp* h, int gemm, int pair);
 }  // namespace mixed

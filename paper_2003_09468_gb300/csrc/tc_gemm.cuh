@@ -174,10 +174,17 @@ struct LayoutP {
   static constexpr uint32_t TMEM_COLS = 512;
 };
 
-template <int STAGES, class P>
+// PAIR: the CTAs run in clusters of two and every MMA is a cta_group::2 MMA of 256 rows issued
+// by the even CTA: each CTA stages its own 128 rows of A and half of the paired B (the real
+// planes in the even CTA, the imaginary ones in the odd CTA, through a B map whose box holds one
+// of the two), so the pair reads each B element from shared memory once where two CTAs would
+// read it twice.  Tile t of the policy is then a pair of row tiles: CTA r takes row tile
+// 2 mt + r.  Each CTA drains and stores its own rows as in the single form.
+template <int STAGES, class P, bool PAIR = false>
 __global__ void __launch_bounds__(THREADS, 1)
     cgemm_precise_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const __grid_constant__ P p, int* err) {
+  static_assert(!PAIR || (PairB<P>::value && !Grouped<P>::value), "pair form: paired B, one problem");
   // Persistent: CTA i handles tiles i, i + grid, i + 2 grid, ...  The TMA ring and the
   // two TMEM accumulator sets run continuously across tile boundaries.  One drain per 32-wide k
   // chunk: per accumulator the four small cross products of the chunk go first, then
@@ -194,6 +201,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? tc::cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
@@ -201,24 +210,31 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&accf[s], 1);
-      tc::mbar_init(&acce[s], 4);
+      tc::mbar_init(&acce[s], PAIR ? 8 : 4);   // the drain warps of both CTAs in the pair form
     }
     *abort = 0;
     tc::fence_mbar_init();
   }
   if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, Lay::TMEM_COLS);
-    tc::tmem_relinquish();
+    if constexpr (PAIR) {
+      tc::tmem_alloc_pair(tmem_slot, Lay::TMEM_COLS);
+      tc::tmem_relinquish_pair();
+    } else {
+      tc::tmem_alloc(tmem_slot, Lay::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
+  if constexpr (PAIR) tc::cluster_sync();   // the peer's barriers are initialised
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
   // tile t runs on CTA t mod gridDim.x: the tiles in flight at any moment are
   // consecutive, so the operands they share (one walker's rows, one Cholesky block)
   // are read from HBM once and served from L2 to the others
-  const int t0 = blockIdx.x, tstep = gridDim.x;
+  const int t0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int tstep = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   constexpr int DC = DrainChunks<P>::value;
   static_assert(DC >= 1 && (DC == 1 || !ChunkScaled<P>::value), "one chunk factor per drained partial");
 
@@ -248,9 +264,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             failed = true;
             break;
           }
+          uint8_t* sa = smem + s * Lay::STAGE_BYTES;
+          if constexpr (PAIR) {
+            // both CTAs' copies complete on the even CTA's full barrier
+            if (leader) tc::mbar_arrive_expect_tx(&full[s], 2 * (Lay::A_BYTES + Lay::B_BYTES / 2));
+            Coords c = p.coords(b, 2 * mt + (int)rank, nt, kc);
+            c.b[2] += (int)rank;   // re planes in the even CTA, im planes in the odd one
+            const uint32_t fb = tc::mapa_shared(tc::smem_u32(&full[s]), 0);
+            tc::tma_load_5d_pair(sa, ma, fb, c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
+            tc::tma_load_5d_pair(sa + Lay::A_BYTES, mb, fb, c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
+            continue;
+          }
           tc::mbar_arrive_expect_tx(&full[s], Lay::STAGE_BYTES);
           const Coords c = p.coords(b, mt, nt, kc);
-          uint8_t* sa = smem + s * Lay::STAGE_BYTES;
           tc::tma_load_5d(sa, ma, &full[s], c.a[0], c.a[1], c.a[2], c.a[3], c.a[4]);
           if (stream)
             tc::tma_load_5d_hint(sa + Lay::A_BYTES, mb, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4],
@@ -259,8 +285,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::tma_load_5d(sa + Lay::A_BYTES, mb, &full[s], c.b[0], c.b[1], c.b[2], c.b[3], c.b[4]);
         }
       }
-      // every issued copy must land before the CTA may exit
-      for (long q = (g > STAGES ? g - STAGES : 0); q < g; ++q) {
+      // every issued copy must land before the CTA may exit (in the pair form the even CTA's
+      // full barriers count both CTAs' copies, and the final cluster barrier holds the odd CTA)
+      for (long q = (g > STAGES ? g - STAGES : 0); q < g && leader; ++q) {
         const int s = (int)(q % STAGES);
         const uint32_t ph = (uint32_t)((q / STAGES) & 1);
         int zero = 0;
@@ -268,7 +295,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {   // the pair form's MMAs are issued by the even CTA alone
       constexpr uint32_t id = tc::idesc_f16(BM, BNP, false);
       long g = 0;   // k chunks (TMA ring)
       long a = 0;   // drained partials (accumulator sets), one per D chunks
@@ -306,7 +333,28 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) A[pl][kk] = tc::desc_kmajor_sw64(sa + pl * BM * 64 + kk * 32);
-          if constexpr (PairB<P>::value) {
+          if constexpr (PAIR) {
+            // Each CTA holds [B_hi; B_lo] of its half (re in the even CTA, im in the odd one),
+            // 64 rows each: the pair's B operand rows 0..127 are [Br_hi; Bi_hi] (or _lo).
+            constexpr uint32_t idp = tc::idesc_f16(2 * BM, 2 * BNP, false);
+            uint64_t Bh[2], Bl[2];
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              Bh[kk] = tc::desc_kmajor_sw64(sb + kk * 32);
+              Bl[kk] = tc::desc_kmajor_sw64(sb + BNP * 64 + kk * 32);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const uint32_t dq = d + q * 2 * BNP;
+              const int ah = 2 * q;
+              tc::mma_f16_pair(dq, A[ah + 1][0], Bh[0], idp, acc0);
+              tc::mma_f16_pair(dq, A[ah][0], Bl[0], idp, 1);
+              tc::mma_f16_pair(dq, A[ah + 1][1], Bh[1], idp, 1);
+              tc::mma_f16_pair(dq, A[ah][1], Bl[1], idp, 1);
+              tc::mma_f16_pair(dq, A[ah][0], Bh[0], idp, 1);
+              tc::mma_f16_pair(dq, A[ah][1], Bh[1], idp, 1);
+            }
+          } else if constexpr (PairB<P>::value) {
             // B rows 0..127 = [Br_hi; Bi_hi], rows 128..255 = [Br_lo; Bi_lo].  Accumulators:
             // Ar [Br | Bi] -> P_rr (0), P_ri (64); Ai [Br | Bi] -> P_ir (128), P_ii (192).
             constexpr uint32_t id2 = tc::idesc_f16(BM, 2 * BNP, false);
@@ -348,11 +396,19 @@ __global__ void __launch_bounds__(THREADS, 1)
               tc::mma_f16(dq, A[ah][1], B[bh][1], id, 1);
             }
           }
-          if (close) {
-            tc::mma_commit(&accf[set]);
-            ++a;
+          if constexpr (PAIR) {
+            if (close) {
+              tc::mma_commit_pair(&accf[set]);
+              ++a;
+            }
+            tc::mma_commit_pair(&empty[s]);
+          } else {
+            if (close) {
+              tc::mma_commit(&accf[set]);
+              ++a;
+            }
+            tc::mma_commit(&empty[s]);
           }
-          tc::mma_commit(&empty[s]);
         }
       }
       if (a > 0) {  // our own MMAs must complete before TMEM is freed
@@ -426,7 +482,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&acce[set]);
+        if (lane == 0) {
+          if (PAIR && !leader)
+            tc::mbar_arrive_remote(tc::mapa_shared(tc::smem_u32(&acce[set]), 0));
+          else
+            tc::mbar_arrive(&acce[set]);
+        }
       }
       if (ntile > 0) asm volatile("bar.sync 3, 256;" ::: "memory");   // previous tile stored
 #pragma unroll
@@ -442,16 +503,22 @@ __global__ void __launch_bounds__(THREADS, 1)
       int b, mt, nt;
       p.tile(t, b, mt, nt);
       asm volatile("bar.sync 2, 256;" ::: "memory");
-      if (!*abort) p.store_tile(b, mt, nt, tile_buf, tid, ew, lane);
+      if (!*abort) p.store_tile(b, PAIR ? 2 * mt + (int)rank : mt, nt, tile_buf, tid, ew, lane);
       __threadfence_block();
       asm volatile("bar.arrive 3, 256;" ::: "memory");
     }
   }
   tc::fence_before_sync();
   __syncthreads();
+  // pair form: the peer's copies, MMAs and remote arrivals are all done before either CTA
+  // frees its tensor memory or exits
+  if constexpr (PAIR) tc::cluster_sync();
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, Lay::TMEM_COLS);
+    if constexpr (PAIR)
+      tc::tmem_dealloc_pair(tmem, Lay::TMEM_COLS);
+    else
+      tc::tmem_dealloc(tmem, Lay::TMEM_COLS);
   }
 }
 
@@ -514,6 +581,34 @@ cudaError_t launch_precise(const CUtensorMap& a, const CUtensorMap& b, const P& 
   const int grid = p.tiles < sms ? p.tiles : sms;
   fn<<<grid, THREADS, Lay::SMEM, st>>>(a, b, p, err);
   return cudaGetLastError();
+}
+
+// The pair form: clusters of two CTAs, p.tiles counting pairs of row tiles, `b` the B map whose
+// box holds one of the two (re, im) halves of the paired B operand.
+template <int STAGES, class P>
+cudaError_t launch_precise_pair(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
+  using Lay = LayoutP<STAGES>;
+  auto fn = cgemm_precise_kernel<STAGES, P, true>;
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(fn), Lay::SMEM);
+  if (e != cudaSuccess) return e;
+  if (p.tiles <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int pairs = sms / 2 > 0 ? sms / 2 : 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * (p.tiles < pairs ? p.tiles : pairs));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = Lay::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, a, b, p, err);
 }
 
 }  // namespace tcg

@@ -288,3 +288,51 @@ def test_gemm_autotuning(case):
         if v["ring_depth"] != fast:   # the default kept within the 2% margin
             assert min(v["ms_2_stages"], v["ms_3_stages"]) >= 0.98 * max(v["ms_2_stages"], v["ms_3_stages"]) - 1e-9
 
+
+
+def test_taylor_cta_pair_form():
+    """The Taylor GEMM's CTA-pair form (256-row tiles over a cluster of two SMs, each staging half
+    of the paired B operand) gives bit for bit the single form's walkers, weights and energies;
+    the form chosen at create is the faster one (the single form unless the pair form is more
+    than 2% faster), and the override is refused where the pair form does not exist."""
+    from paper_2003_09468_gb300 import AfqmcError
+    # N = 80 occupied orbitals per spin: R = 2N = 160 rows per walker, two row tiles
+    spec = gen.SystemSpec(grid=(2, 2, 2), M=12, nocc=10, nchol=16, nwalkers=8, random_trial=True, seed=41)
+    sys_, osys = make(spec, "mixed")
+    chosen, ms_pair = sys_.gemm_form("taylor")
+    t = sys_.gemm_tuning()["taylor"]
+    assert ms_pair > 0.0 and t["ms_cta_pair"] == ms_pair and t["cta_pair"] == chosen
+    single = t["ms_2_stages"] if t["ring_depth"] == 2 else t["ms_3_stages"]   # at the tuned depth
+    assert chosen == (ms_pair < 0.98 * single)
+    phi0 = gen.near_trial_walkers(spec)
+    outs = []
+    for pair in (False, True):
+        sys_.set_gemm_form("taylor", pair)
+        assert sys_.gemm_form("taylor")[0] == pair
+        phi, w = dev(phi0), dev(np.linspace(0.8, 1.2, spec.nwalkers))
+        el = torch.empty((spec.nwalkers, 3), dtype=torch.complex128, device="cuda")
+        for s in range(3):
+            sys_.step(phi, dev(gen.fields(spec, s)), w, el, do_qr=(s == 1), reuse=s > 0)
+        outs.append((host(phi), host(w), host(el)))
+        assert sys_.last_error() == (0, 0)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    pn, _, _, _, _ = ok.propagate_walker(osys, phi0[0], gen.fields(spec, 0)[0], 1.0)
+    sys_.set_gemm_form("taylor", True)
+    phi = dev(phi0)
+    sys_.step(phi, dev(gen.fields(spec, 0)), dev(np.ones(spec.nwalkers)), reuse=False)
+    assert rel(host(phi)[0], pn) < TOL_PHI
+    with pytest.raises(AfqmcError):
+        sys_.set_gemm_form("exchange", True)
+    sys_.close()
+    # one row tile per walker (2N = 8): no pair form
+    small, _ = make(SPECS["2x2x2"], "mixed")
+    assert small.gemm_form("taylor") == (False, 0.0)
+    with pytest.raises(AfqmcError):
+        small.set_gemm_form("taylor", True)
+    small.close()
+    fp64, _ = make(SPECS["2x2x2"], "fp64")
+    assert fp64.gemm_form("taylor") == (False, 0.0)
+    with pytest.raises(AfqmcError):
+        fp64.set_gemm_form("taylor", True)
+    fp64.close()
