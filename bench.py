@@ -673,12 +673,12 @@ def run_dense(args):
 
 
 def run_group(args):
-    """Eight uneven systems (1024 walkers) advanced as one group.  Every GEMM kind of a group
-    step is one persistent launch over the tiles of all eight members (shared GEMMs); the small
-    kernels between them run on one stream per member.  Timed on the same inputs as: a captured
-    graph of two group steps (the headline), eager group steps, the same two forms with
-    per-member GEMM launches on the member streams, and the members stepped one after another
-    on one stream (what the group is measured against)."""
+    """Eight uneven systems (1024 walkers) advanced as one group, in each of the group's modes:
+    the Taylor-term GEMMs shared (one persistent launch per term over all members' tiles, the
+    rest of each member's step on its own stream; the default), every GEMM kind shared, and
+    every member on its own launches.  Each mode is timed as a captured graph of two group
+    steps (the headline is the default mode's) and as eager group steps; the members stepped
+    one after another on one stream are what the group is measured against."""
     import torch
     import torch.distributed as dist
     from paper_2003_09468_gb300 import KPointAFQMC, KPointGroup
@@ -733,22 +733,22 @@ def run_group(args):
             if launches is not None:
                 launches[0] += grp.launch_count()
 
-    def eager(shared):
-        grp.shared = shared
+    def eager(mode, name):
+        grp.shared = mode
         restart()
         group_steps(0, args.warmup)
         launches = [0]
         # an NVTX range names the timed steps for a profiler's launch filter
-        torch.cuda.nvtx.range_push("eager_shared" if shared else "eager_per_member")
+        torch.cuda.nvtx.range_push("eager_" + name)
         ms = timed(lambda: group_steps(args.warmup, nsteps, launches))
         torch.cuda.nvtx.range_pop()
         return ms, launches[0], all(bool(torch.isfinite(e).all()) for e in els)
 
     pairs = max(1, args.steps // 2)
 
-    def graph(shared):
+    def graph(mode):
         """A captured graph of two group steps, replayed with each step's fields copied in."""
-        grp.shared = shared
+        grp.shared = mode
         restart()
         group_steps(0, 1)
         xa = [torch.empty_like(x) for x in xs[0]]
@@ -772,13 +772,22 @@ def run_group(args):
         del g
         return ms
 
+    modes = {"shared_taylor": KPointGroup.SHARED_TAYLOR, "shared_all": KPointGroup.SHARED_ALL,
+             "per_member": KPointGroup.PER_MEMBER}
+    default = next(k for k, v in modes.items() if v == shared_default)
+    order = [default] + [k for k in modes if k != default]
     clocks = Clocks(local)
     clocks.start()
-    ms_group, launches, finite = eager(shared_default)
-    ms_graph = graph(shared_default)
-    clk = clocks.stop()
-    ms_group_streams, launches_streams, finite_streams = eager(False)
-    ms_graph_streams = graph(False)
+    measured, finite = {}, True
+    for name in order:
+        ms_e, launches, fin = eager(modes[name], name)
+        ms_g = graph(modes[name])
+        finite = finite and fin
+        measured[name] = {"graph": {"value": world * nw * 2 * pairs / (ms_g * 1e-3), "ms_per_step": ms_g / (2 * pairs)},
+                          "eager": {"value": world * nw * args.steps / (ms_e * 1e-3),
+                                    "ms_per_step": ms_e / args.steps, "gpu_launches": launches}}
+        if name == default:
+            clk = clocks.stop()
 
     # the same steps, members one after another on one stream
     restart()
@@ -794,30 +803,23 @@ def run_group(args):
     for s_ in systems:
         s_.close()
     if rank == 0:
-        per_graph = ms_graph / (2 * pairs)
-        value = world * nw * 2 * pairs / (ms_graph * 1e-3)
+        per_graph = measured[default]["graph"]["ms_per_step"]
+        seq = ms_seq / args.steps
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 2 * pairs,
-            "warmup": args.warmup, "ms_per_step": per_graph, "higher_is_better": True,
+            "metric": METRIC, "value": measured[default]["graph"]["value"], "unit": UNIT, "n_gpus": world,
+            "steps": 2 * pairs, "warmup": args.warmup, "ms_per_step": per_graph, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16x2-split/f32-acc + f64", "data": "synthetic",
             "config": {"workload": GROUP_WORKLOAD, "systems": [
                 {"grid": list(s.grid), "M": s.M, "nocc": s.nocc, "nchol": s.nchol, "walkers": s.nwalkers}
                 for s in specs], "walkers_per_gpu": nw, "taylor_order": 6, "qr_period": QR_PERIOD,
-                "precision": "mixed", "parallelism": f"replicas x{world}", "shared_gemms": shared_default,
+                "precision": "mixed", "parallelism": f"replicas x{world}", "group_mode": default,
                 "timing": "CUDA graph of two group steps, replayed; fields copied in before each replay"},
-            "eager_group": {"value": world * nw * args.steps / (ms_group * 1e-3), "ms_per_step": ms_group / args.steps,
-                            "gpu_launches": launches},
-            "per_member_gemms": {
-                "graph": {"value": world * nw * 2 * pairs / (ms_graph_streams * 1e-3),
-                          "ms_per_step": ms_graph_streams / (2 * pairs)},
-                "eager": {"value": world * nw * args.steps / (ms_group_streams * 1e-3),
-                          "ms_per_step": ms_group_streams / args.steps, "gpu_launches": launches_streams}},
-            "sequential_members": {"value": world * nw * args.steps / (ms_seq * 1e-3),
-                                   "ms_per_step": ms_seq / args.steps},
-            "speedup_graph_over_sequential": (ms_seq / args.steps) / per_graph,
-            "speedup_shared_over_per_member_gemms": (ms_graph_streams / (2 * pairs)) / per_graph,
-            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
-            "clocks": clk, "finite": finite and finite_streams,
+            "modes": measured,
+            "sequential_members": {"value": world * nw * args.steps / (ms_seq * 1e-3), "ms_per_step": seq},
+            "speedup_graph_over_sequential": {k: seq / v["graph"]["ms_per_step"] for k, v in measured.items()},
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": measured[default]["eager"]["gpu_launches"],
+            "clocks": clk, "finite": finite,
             "autotune": {"ring_depth_per_member": [{k: v["ring_depth"] for k, v in t.items()} for t in tunings]},
         }
         print(json.dumps(out))

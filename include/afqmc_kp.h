@@ -497,20 +497,26 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
 afqmc_status afqmc_kp_group_launch_count(afqmc_kp_group_t g, int* launches);
 
 /*
- * afqmc_kp_group_set_shared -- shared GEMM launches for group_step and group_block
- * (Sec. 3.2: all walkers of all systems in one batched operation).  With shared = 1
- * every tensor-core GEMM of a step (the Green's function, the force bias, vHS, each
- * Taylor term, the exchange) is one persistent launch on `stream` over the tiles of
- * every member, each tile with its own member's operands, sizes and tensor maps; the
- * small kernels between the GEMMs run on the member streams.  With shared = 0 every
- * member launches its own GEMMs on its own stream.  Either way each member computes
- * bit for bit what it computes alone.  A group of 1..8 mixed handles with one Taylor
- * order starts shared; shared = 1 on any other group is AFQMC_ERR_UNSUPPORTED.
- * GEMM time-outs of a shared launch are reported by the first member's
- * afqmc_kp_last_error.
+ * afqmc_kp_group_set_shared -- GEMM launches shared by the members in group_step and
+ * group_block (Sec. 3.2: all walkers of all systems in one batched operation).
+ *   AFQMC_GROUP_PER_MEMBER     every member launches its own GEMMs on its own stream;
+ *   AFQMC_GROUP_SHARED_ALL     every tensor-core GEMM of a step (the Green's function, the
+ *                              force bias, vHS, each Taylor term, the exchange) is one
+ *                              persistent launch on `stream` over the tiles of every member,
+ *                              each tile with its own member's operands, sizes and tensor maps;
+ *                              the small kernels between the GEMMs run on the member streams;
+ *   AFQMC_GROUP_SHARED_TAYLOR  only the six Taylor-term GEMMs are shared launches; the rest of
+ *                              each member's step runs on its stream.
+ * Either way each member computes bit for bit what it computes alone.  A group of 1..8 mixed
+ * handles with one Taylor order starts with AFQMC_GROUP_SHARED_TAYLOR, any other group with
+ * AFQMC_GROUP_PER_MEMBER; a shared mode on any other group is AFQMC_ERR_UNSUPPORTED.  GEMM
+ * time-outs of a shared launch are reported by the first member's afqmc_kp_last_error.
  */
+#define AFQMC_GROUP_PER_MEMBER 0
+#define AFQMC_GROUP_SHARED_ALL 1
+#define AFQMC_GROUP_SHARED_TAYLOR 2
 afqmc_status afqmc_kp_group_set_shared(afqmc_kp_group_t g, int shared);
-/* Whether the group uses the shared GEMM launches (1) or not (0). */
+/* The group's mode (AFQMC_GROUP_*). */
 afqmc_status afqmc_kp_group_shared(afqmc_kp_group_t g, int* shared);
 
 /*

@@ -389,8 +389,12 @@ class DenseAFQMC(KPointAFQMC):
 
 
 class KPointGroup:
-    """Several KPointAFQMC systems advanced together, one CUDA stream per member; groups of up
-    to 8 mixed systems of one Taylor order share every GEMM launch (`shared`)."""
+    """Several KPointAFQMC systems advanced together, one CUDA stream per member.  Groups of up
+    to 8 mixed systems of one Taylor order can share GEMM launches (`shared`): PER_MEMBER (0),
+    SHARED_ALL (1, every GEMM kind one launch over all members' tiles) or SHARED_TAYLOR (2, the
+    Taylor-term GEMMs only; the default where allowed)."""
+
+    PER_MEMBER, SHARED_ALL, SHARED_TAYLOR = 0, 1, 2
 
     def __init__(self, systems):
         self.lib = load_library()
@@ -453,14 +457,14 @@ class KPointGroup:
         return n.value
 
     @property
-    def shared(self) -> bool:
+    def shared(self) -> int:
         n = ctypes.c_int(0)
         _check(self.lib.afqmc_kp_group_shared(self.group, ctypes.byref(n)), "afqmc_kp_group_shared")
-        return bool(n.value)
+        return n.value
 
     @shared.setter
-    def shared(self, on: bool):
-        _check(self.lib.afqmc_kp_group_set_shared(self.group, 1 if on else 0), "afqmc_kp_group_set_shared")
+    def shared(self, mode: int):
+        _check(self.lib.afqmc_kp_group_set_shared(self.group, int(mode)), "afqmc_kp_group_set_shared")
 
 
 def philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

@@ -153,16 +153,17 @@ cudaError_t block_impl(afqmc_kp* h, void* phi, double* weight, double* x, void* 
 // A group of handles stepped together: one stream per member, forked from and joined
 // back to the caller's stream, so that a whole group call captures as one CUDA graph
 // whose branches run concurrently.
-// With `shared` set (mixed members of one Taylor order, at most mixed::GROUP_MAX of them),
-// every tensor-core GEMM of a step is one persistent launch over the tiles of all members on
-// the caller's stream, and only the small kernels between the GEMMs run on member streams.
+// With `shared` set (mixed members of one Taylor order, at most mixed::GROUP_MAX of them), the
+// Taylor-term GEMMs (AFQMC_GROUP_SHARED_TAYLOR) or every tensor-core GEMM of a step
+// (AFQMC_GROUP_SHARED_ALL) are each one persistent launch over the tiles of all members on
+// the caller's stream, and the rest of the step runs on the member streams.
 struct afqmc_kp_group {
   std::vector<afqmc_kp*> members;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
   int launches = 0;
-  bool shared = false;
+  int shared = AFQMC_GROUP_PER_MEMBER;
 };
 
 namespace {
@@ -231,7 +232,7 @@ cudaError_t group_step_shared(afqmc_kp_group* g, void* const* phi, const double*
   }
   const mixed::ForEach each = [&](const mixed::MemberFn& fn) { return fork_join(g, st, fn); };
   const cudaError_t e = mixed::group_step(g->members.data(), (int)n, ph.data(), x, weight, el.data(), ld.data(),
-                                          do_qr, reuse.data(), each, st);
+                                          do_qr, reuse.data(), g->shared == AFQMC_GROUP_SHARED_ALL, each, st);
   if (e == cudaSuccess)
     for (size_t i = 0; i < n; ++i) {
       g->members[i]->green_valid = true;
@@ -651,7 +652,7 @@ afqmc_status afqmc_kp_group_create(const afqmc_kp_t* systems, int nsys, afqmc_kp
       group_free(g);
       return from_cuda(e);
     }
-    g->shared = group_shareable(g);
+    g->shared = group_shareable(g) ? AFQMC_GROUP_SHARED_TAYLOR : AFQMC_GROUP_PER_MEMBER;
   } catch (...) {
     group_free(g);
     return AFQMC_ERR_OOM;
@@ -715,15 +716,15 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
 }
 
 afqmc_status afqmc_kp_group_set_shared(afqmc_kp_group_t g, int shared) {
-  if (!g || (shared != 0 && shared != 1)) return AFQMC_ERR_INVALID;
-  if (shared && !group_shareable(g)) return AFQMC_ERR_UNSUPPORTED;
-  g->shared = shared != 0;
+  if (!g || shared < AFQMC_GROUP_PER_MEMBER || shared > AFQMC_GROUP_SHARED_TAYLOR) return AFQMC_ERR_INVALID;
+  if (shared != AFQMC_GROUP_PER_MEMBER && !group_shareable(g)) return AFQMC_ERR_UNSUPPORTED;
+  g->shared = shared;
   return AFQMC_OK;
 }
 
 afqmc_status afqmc_kp_group_shared(afqmc_kp_group_t g, int* shared) {
   if (!g || !shared) return AFQMC_ERR_INVALID;
-  *shared = g->shared ? 1 : 0;
+  *shared = g->shared;
   return AFQMC_OK;
 }
 

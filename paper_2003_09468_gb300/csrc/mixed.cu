@@ -2179,7 +2179,8 @@ cudaError_t step(afqmc_kp* h, zc* phi, const double* x, double* w, zc* eloc, zc*
 // ---------------------------------------------------------------------------
 // One launch of policy P over the tiles of every listed handle (tcg::GroupP): mk(h) gives a
 // handle's parameters, maps(h) its (A, B) tensor maps.  Time-outs land in the first handle's
-// flags.  The TMA ring takes the policy's default depth: the depth changes no arithmetic.
+// flags.  The TMA ring takes the depth the member with the most tiles chose at create (the
+// depth changes no arithmetic).
 template <class P, class MK, class MAPS>
 static cudaError_t group_gemm(afqmc_kp* const* hs, int n, MK mk, MAPS maps, cudaStream_t st) {
   constexpr int NMAX = GROUP_MAX;
@@ -2199,13 +2200,35 @@ static cudaError_t group_gemm(afqmc_kp* const* hs, int n, MK mk, MAPS maps, cuda
   for (int i = n + 1; i <= NMAX; ++i) g.start[i] = g.start[n];
   g.tiles = g.start[n];
   g.kchunks = 0;
+  int big = 0;
+  for (int i = 1; i < n; ++i)
+    if (g.m[i].tiles > g.m[big].tiles) big = i;
+  const int r = hs[big]->mixed->ring[GemmIdOf<P>::value];
   const auto mp0 = maps(hs[0]);
   AFQMC_LAUNCHED(hs[0]);
-  return tcg::launch_precise<P::kStages>(*mp0.first, *mp0.second, g, hs[0]->flags + 1, st);
+  return (r ? r : P::kStages) == 2 ? tcg::launch_precise<2>(*mp0.first, *mp0.second, g, hs[0]->flags + 1, st)
+                                   : tcg::launch_precise<3>(*mp0.first, *mp0.second, g, hs[0]->flags + 1, st);
+}
+
+// The step's tail on one member after its propagated walkers' Green's function GEMM:
+// the QR where asked, the log-det bookkeeping.
+static cudaError_t group_member_tail(afqmc_kp* h, zc* phi, zc* eloc, zc* logdet, int do_qr, cudaStream_t s) {
+  if (eloc) MTRY(ex_reduce(h, eloc, s));
+  if (do_qr) {
+    MixedState* m = h->mixed;
+    MTRY(cholqr2(h, phi, m->logr, s));
+    ld_shift_kernel<<<cdiv(m->WS, 128), 128, 0, s>>>(h->ld_new, m->logr, h->sing_new, m->WS);
+    AFQMC_LAUNCHED(h);
+    MTRY(cudaGetLastError());
+    if (logdet) MTRY(cudaMemcpyAsync(logdet, h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, s));
+  }
+  std::swap(h->ld_old, h->ld_new);
+  std::swap(h->sing_old, h->sing_new);
+  return cudaSuccess;
 }
 
 cudaError_t group_step(afqmc_kp* const* hs, int n, zc* const* phi, const double* const* x, double* const* w,
-                       zc* const* eloc, zc* const* logdet, int do_qr, const int* reuse, const ForEach& each,
+                       zc* const* eloc, zc* const* logdet, int do_qr, const int* reuse, bool all, const ForEach& each,
                        cudaStream_t st) {
   using MP = std::pair<const CUtensorMap*, const CUtensorMap*>;
   // force bias of the current walkers (their Green's function first where not reused), y
@@ -2215,17 +2238,33 @@ cudaError_t group_step(afqmc_kp* const* hs, int n, zc* const* phi, const double*
       MTRY(cholesky_trace(h, s));
     }
     MTRY(fp64::force_bias(h, x[i], h->xbar, s));
-    return vhs_pre(h, s);
+    if (all) return vhs_pre(h, s);
+    MTRY(vhs(h, s));
+    return taylor_pre(h, phi[i], s);
   }));
-  MTRY(group_gemm<VhsP>(hs, n, [](const afqmc_kp* h) { return vhs_params(h); },
-                        [](const afqmc_kp* h) { return MP(&h->mixed->m_lt, &h->mixed->m_y); }, st));
-  MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) { return taylor_pre(h, phi[i], s); }));
+  if (all) {
+    MTRY(group_gemm<VhsP>(hs, n, [](const afqmc_kp* h) { return vhs_params(h); },
+                          [](const afqmc_kp* h) { return MP(&h->mixed->m_lt, &h->mixed->m_y); }, st));
+    MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) { return taylor_pre(h, phi[i], s); }));
+  }
   const int order = hs[0]->order;
   for (int j = order, step = 0; j >= 1; --j, ++step) {
     const int cur = step & 1, nxt = (step + 1) & 1;
     MTRY(group_gemm<TaylorP>(hs, n, [&](const afqmc_kp* h) { return taylor_params(h, j, nxt); },
                              [&](const afqmc_kp* h) { return MP(&h->mixed->m_t[cur], &h->mixed->m_v); }, st));
   }
+  if (!all)   // the rest of the step on each member's own launches
+    return each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
+      MTRY(taylor_post(h, phi[i], s));
+      MTRY(green(h, phi[i], h->ld_new, h->sing_new, s));
+      MTRY(cholesky_trace(h, s));
+      MTRY(fp64::weight_only(h, x[i], w[i], do_qr ? nullptr : logdet[i], s));
+      if (eloc[i]) {
+        MTRY(e1_ec(h, eloc[i], s));
+        MTRY(exchange(h, s));
+      }
+      return group_member_tail(h, phi[i], eloc[i], logdet[i], do_qr, s);
+    });
   // the propagated walkers' Green's function, the Cholesky trace, the weights
   MTRY(each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
     MTRY(taylor_post(h, phi[i], s));
@@ -2248,20 +2287,8 @@ cudaError_t group_step(afqmc_kp* const* hs, int n, zc* const* phi, const double*
   if (!ex.empty())
     MTRY(group_gemm<ExchangeP>(ex.data(), (int)ex.size(), [](const afqmc_kp* h) { return exchange_params(h); },
                                [](const afqmc_kp* h) { return MP(&h->mixed->m_g, &h->mixed->m_z); }, st));
-  return each([&](int i, afqmc_kp* h, cudaStream_t s) -> cudaError_t {
-    if (eloc[i]) MTRY(ex_reduce(h, eloc[i], s));
-    if (do_qr) {
-      MixedState* m = h->mixed;
-      MTRY(cholqr2(h, phi[i], m->logr, s));
-      ld_shift_kernel<<<cdiv(m->WS, 128), 128, 0, s>>>(h->ld_new, m->logr, h->sing_new, m->WS);
-      AFQMC_LAUNCHED(h);
-      MTRY(cudaGetLastError());
-      if (logdet[i])
-        MTRY(cudaMemcpyAsync(logdet[i], h->ld_new, sizeof(zc) * 2 * h->W, cudaMemcpyDeviceToDevice, s));
-    }
-    std::swap(h->ld_old, h->ld_new);
-    std::swap(h->sing_old, h->sing_new);
-    return cudaSuccess;
+  return each([&](int i, afqmc_kp* h, cudaStream_t s) {
+    return group_member_tail(h, phi[i], eloc[i], logdet[i], do_qr, s);
   });
 }
 

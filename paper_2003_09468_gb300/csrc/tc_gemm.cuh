@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc::tma_prefetch(&tmB);
       }
       bool stream = false;
-      if constexpr (StreamB<P>::value) stream = p.stream_b();
-      const uint64_t stream_pol = stream ? tc::l2_evict_first_policy() : 0;
+      if constexpr (StreamB<P>::value && !Grouped<P>::value) stream = p.stream_b();
+      const uint64_t stream_pol = StreamB<P>::value ? tc::l2_evict_first_policy() : 0;
       long g = 0;
       bool failed = false;
       for (int t = t0; t < p.tiles && !failed; t += tstep) {
@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int KC = kchunks_of(p, b);
         const CUtensorMap* ma = map_a_of(p, b, &tmA);
         const CUtensorMap* mb = map_b_of(p, b, &tmB);
+        if constexpr (StreamB<P>::value && Grouped<P>::value) stream = p.stream_b_of(b);   // per member
         for (int kc = 0; kc < KC; ++kc, ++g) {
           const int s = (int)(g % STAGES);
           const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -533,6 +534,7 @@ struct GroupP {
   static constexpr bool kConjA = P::kConjA;
   static constexpr bool kPairB = PairB<P>::value;
   static constexpr bool kGrouped = true;
+  static constexpr bool kStreamB = StreamB<P>::value;
   static constexpr int kStages = P::kStages;
   static_assert(!ChunkScaled<P>::value && DrainChunks<P>::value == 1, "plain policies only");
   int tiles, kchunks;   // kchunks unused: per member
@@ -552,6 +554,12 @@ struct GroupP {
     m[b >> 20].store_tile(b & 0xFFFFF, mt, nt, tile, tid, ew, lane);
   }
   __device__ int kchunks_of(int b) const { return m[b >> 20].kchunks; }
+  __device__ bool stream_b_of(int b) const {
+    if constexpr (StreamB<P>::value)
+      return m[b >> 20].stream_b();
+    else
+      return false;
+  }
   __device__ const CUtensorMap* map_a(int b) const { return &ma[b >> 20]; }
   __device__ const CUtensorMap* map_b(int b) const { return &mb[b >> 20]; }
 };

@@ -2,7 +2,7 @@
 
 Each member of a group computes what the same call on the member alone computes, bit for
 bit, whether the group places the members' kernels on concurrent streams or (all members
-mixed) launches each GEMM kind once over the tiles of every member.  That holds for eager
+mixed) launches the Taylor-term GEMMs, or every GEMM kind, once over the tiles of every member.  That holds for eager
 group calls, for a group step captured in a CUDA graph and for the group block.  The energy
 each member returns inside the group is also checked against the oracle on the walker the
 GPU propagated, at the per-path bars of test_gpu_step.
@@ -107,28 +107,34 @@ def test_group_steps_equal_members_alone_and_graph():
 
 
 def test_shared_gemm_group_steps_equal_members_alone_and_graph():
+    from paper_2003_09468_gb300 import KPointGroup as G
     alone = run_steps("alone", MIXED)
     check_equal([alone, run_steps("group", MIXED), run_steps("graph", MIXED),
-                 run_steps("group", MIXED, shared=False)])
+                 run_steps("group", MIXED, shared=G.SHARED_ALL), run_steps("graph", MIXED, shared=G.SHARED_ALL),
+                 run_steps("group", MIXED, shared=G.PER_MEMBER)])
 
 
 def test_shared_gemms_only_for_mixed_groups_of_one_order():
     from paper_2003_09468_gb300 import KPointGroup, AfqmcError
     sys_ = [make(spec, prec)[0] for spec, prec in MEMBERS]
     grp = KPointGroup(sys_)               # an FP64 member: per-member streams
-    assert not grp.shared
+    assert grp.shared == KPointGroup.PER_MEMBER
+    for mode in (KPointGroup.SHARED_ALL, KPointGroup.SHARED_TAYLOR):
+        with pytest.raises(AfqmcError):
+            grp.shared = mode
     with pytest.raises(AfqmcError):
-        grp.shared = True
+        grp.shared = 3
     grp.close()
     mixed = [s_ for s_, (_, prec) in zip(sys_, MEMBERS) if prec == "mixed"]
     grp = KPointGroup(mixed)
-    assert grp.shared
-    grp.shared = False
-    assert not grp.shared
+    assert grp.shared == KPointGroup.SHARED_TAYLOR
+    for mode in (KPointGroup.PER_MEMBER, KPointGroup.SHARED_ALL, KPointGroup.SHARED_TAYLOR):
+        grp.shared = mode
+        assert grp.shared == mode
     grp.close()
     other = make(MIXED[3][0], "mixed", taylor_order=4)[0]
     grp = KPointGroup(mixed + [other])    # two Taylor orders
-    assert not grp.shared
+    assert grp.shared == KPointGroup.PER_MEMBER
     grp.close()
     for s_ in sys_ + [other]:
         s_.close()
@@ -156,7 +162,8 @@ def test_group_energies_match_oracle(members):
         s_.close()
 
 
-@pytest.mark.parametrize("members,shared", [(MEMBERS, False), (MIXED, True)], ids=["streams", "shared"])
+@pytest.mark.parametrize("members,shared", [(MEMBERS, 0), (MIXED, 2), (MIXED, 1)],
+                         ids=["streams", "shared_taylor", "shared_all"])
 def test_group_block_equals_member_blocks(members, shared):
     from paper_2003_09468_gb300 import KPointGroup
     nsteps, seed = 4, 99
@@ -169,7 +176,7 @@ def test_group_block_equals_member_blocks(members, shared):
         cs = [torch.tensor([7 * i], dtype=torch.int64, device="cuda") for i in range(len(members))]
         if grouped:
             grp = KPointGroup(sys_)
-            assert grp.shared == shared
+            grp.shared = shared
             grp.block([p for p, _ in st], [w for _, w in st], xs, eh, cs, seed, nsteps, qr_period=2,
                       energy_period=2)
             grp.close()
