@@ -1565,7 +1565,8 @@ static cudaError_t autotune(afqmc_kp* h, cudaStream_t st) {
   if (e == cudaSuccess) e = tune_gemm(h, m->m_lt, m->m_y, vhs_params(h), st, e0, e1);
   if (e == cudaSuccess) e = tune_gemm(h, m->m_t[0], m->m_v, taylor_params(h, 2, 1), st, e0, e1);
   if (e == cudaSuccess && taylor_params(h, 2, 1).mt_n > 1) {
-    // the CTA-pair form at the tuned ring depth: kept when faster by more than 2%
+    // the CTA-pair form (four stages): kept when faster than the single form at its tuned ring
+    // depth by more than 2%
     // (a launch the device refuses, e.g. a cluster it cannot place, leaves the single form)
     float t = 0.f;
     m->taylor_pair = 1;
@@ -1995,10 +1996,9 @@ static cudaError_t taylor(afqmc_kp* h, zc* phi, cudaStream_t st) {
 static cudaError_t taylor_gemm(afqmc_kp* h, int j, int cur, int nxt, cudaStream_t st) {
   MixedState* m = h->mixed;
   if (!m->taylor_pair) return run_gemm(h, m->m_t[cur], m->m_v, taylor_params(h, j, nxt), h->flags + 1, st);
-  const TaylorP p = taylor_params_pair(h, j, nxt);
-  const int r = m->ring[AFQMC_GEMM_TAYLOR];
-  return (r ? r : TaylorP::kStages) == 2 ? tcg::launch_precise_pair<2>(m->m_t[cur], m->m_vp, p, h->flags + 1, st)
-                                         : tcg::launch_precise_pair<3>(m->m_t[cur], m->m_vp, p, h->flags + 1, st);
+  // a pair stage holds half of B (40 KB), so four stages fit beside the staged tile: the
+  // deeper ring covers the cross-SM completion of each stage
+  return tcg::launch_precise_pair<4>(m->m_t[cur], m->m_vp, taylor_params_pair(h, j, nxt), h->flags + 1, st);
 }
 
 cudaError_t propagate(afqmc_kp* h, zc* phi, const double* x, double* w, zc* logdet, int do_qr, cudaStream_t st) {

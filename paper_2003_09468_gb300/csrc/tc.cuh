@@ -107,8 +107,11 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// Arrive on an mbarrier of the peer CTA.  The default (CTA-scope) release: what it must order
+// before the arrival are this thread's tensor-memory loads, which tcgen05.fence::before_thread_sync
+// already orders; a cluster-scope release would add a full memory barrier per arrival.
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 // 5-D tiled load into this CTA's shared memory whose completion is counted on an mbarrier of
 // either CTA of the pair (`bar_cluster`, a shared::cluster address).

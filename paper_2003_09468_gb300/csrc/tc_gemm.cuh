@@ -163,10 +163,11 @@ constexpr int DRAIN_COLS = 8;
 // entries so that row-per-thread and column-per-thread accesses both avoid bank conflicts.
 constexpr int STAGE_LD = BNP + 1;
 
-template <int STAGES>
+// PAIR: a stage holds one half (re or im planes) of the paired B tile.
+template <int STAGES, bool PAIR = false>
 struct LayoutP {
   static constexpr int A_BYTES = NPLANE * BM * 64;
-  static constexpr int B_BYTES = NPLANE * BNP * 64;
+  static constexpr int B_BYTES = NPLANE * BNP * 64 / (PAIR ? 2 : 1);
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TILE_BYTES = BM * STAGE_LD * 8;
   static constexpr int BAR_BYTES = 256;
@@ -185,11 +186,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     cgemm_precise_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const __grid_constant__ P p, int* err) {
   static_assert(!PAIR || (PairB<P>::value && !Grouped<P>::value), "pair form: paired B, one problem");
+  static_assert(LayoutP<STAGES, PAIR>::SMEM <= 232448, "shared memory per CTA");
   // Persistent: CTA i handles tiles i, i + grid, i + 2 grid, ...  The TMA ring and the
   // two TMEM accumulator sets run continuously across tile boundaries.  One drain per 32-wide k
   // chunk: per accumulator the four small cross products of the chunk go first, then
   // the two hi*hi products, so a drained partial carries two full-magnitude truncations.
-  using Lay = LayoutP<STAGES>;
+  using Lay = LayoutP<STAGES, PAIR>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float2* tile_buf = reinterpret_cast<float2*>(smem + STAGES * Lay::STAGE_BYTES);
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint8_t* sa = smem + s * Lay::STAGE_BYTES;
           if constexpr (PAIR) {
             // both CTAs' copies complete on the even CTA's full barrier
-            if (leader) tc::mbar_arrive_expect_tx(&full[s], 2 * (Lay::A_BYTES + Lay::B_BYTES / 2));
+            if (leader) tc::mbar_arrive_expect_tx(&full[s], 2 * Lay::STAGE_BYTES);
             Coords c = p.coords(b, 2 * mt + (int)rank, nt, kc);
             c.b[2] += (int)rank;   // re planes in the even CTA, im planes in the odd one
             const uint32_t fb = tc::mapa_shared(tc::smem_u32(&full[s]), 0);
@@ -595,7 +597,7 @@ cudaError_t launch_precise(const CUtensorMap& a, const CUtensorMap& b, const P& 
 // box holds one of the two (re, im) halves of the paired B operand.
 template <int STAGES, class P>
 cudaError_t launch_precise_pair(const CUtensorMap& a, const CUtensorMap& b, const P& p, int* err, cudaStream_t st) {
-  using Lay = LayoutP<STAGES>;
+  using Lay = LayoutP<STAGES, true>;
   auto fn = cgemm_precise_kernel<STAGES, P, true>;
   cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void*>(fn), Lay::SMEM);
   if (e != cudaSuccess) return e;
