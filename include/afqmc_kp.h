@@ -553,8 +553,8 @@ afqmc_status afqmc_kp_gemm_tuning(afqmc_kp_t h, int* depth, double* ms2, double*
  * stages its own 128 rows of A and one half (real or imaginary planes) of the paired B
  * operand, so the B operand is read from shared memory once per pair; *pair = 0: 128-row
  * tiles on one SM.  Only the Taylor-term GEMM (Sec. 3.2 step 3, more than one row tile per
- * walker) has the pair form: at create the library times it at the tuned ring depth and keeps
- * it when faster by more than 2%.  *ms_pair = that per-launch time in ms (0 if not timed, -1
+ * walker) has the pair form: at create the library times it (four-stage ring) and keeps it
+ * when it beats the single form at its tuned ring depth by more than 2%.  *ms_pair = that per-launch time in ms (0 if not timed, -1
  * if the device refused the cluster launch).  Both forms compute every output element with
  * the same products in the same order.  AFQMC_ERR_INVALID for NULL pointers or gemm out of
  * range; an FP64 handle reports 0.
