@@ -680,13 +680,17 @@ afqmc_status afqmc_kp_group_step(afqmc_kp_group_t g, void* const* phi, const dou
     if (!phi[i] || !x[i] || !weight[i] || !al16(phi[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr))
       return AFQMC_ERR_INVALID;
   cudaStream_t st = as_stream(stream);
-  return from_cuda(group_run(g, [&] {
-    if (g->shared) return group_step_shared(g, phi, x, weight, eloc, logdet, do_qr, flags, st);
-    return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t s) {
-      return step_impl(h, phi[i], x[i], weight[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr, do_qr,
-                       flags, s);
-    });
-  }));
+  try {   // the shared path's host arrays may fail to allocate
+    return from_cuda(group_run(g, [&] {
+      if (g->shared) return group_step_shared(g, phi, x, weight, eloc, logdet, do_qr, flags, st);
+      return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t s) {
+        return step_impl(h, phi[i], x[i], weight[i], eloc ? eloc[i] : nullptr, logdet ? logdet[i] : nullptr, do_qr,
+                         flags, s);
+      });
+    }));
+  } catch (...) {
+    return AFQMC_ERR_OOM;
+  }
 }
 
 afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* const* weight, double* const* x,
@@ -703,16 +707,20 @@ afqmc_status afqmc_kp_group_block(afqmc_kp_group_t g, void* const* phi, double* 
     if (comb && rng::comb_smem_bytes(g->members[i]->W) > 227 * 1024) return AFQMC_ERR_UNSUPPORTED;
   }
   cudaStream_t st = as_stream(stream);
-  return from_cuda(group_run(g, [&] {
-    if (g->shared)
-      return group_block_shared(g, phi, weight, x, eloc_hist, weight_hist, logdet, nsteps, qr_period, energy_period,
-                                flags, comb, seed, counter, st);
-    return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t s) {
-      return block_impl(h, phi[i], weight[i], x[i], eloc_hist[i], weight_hist ? weight_hist[i] : nullptr,
-                        logdet ? logdet[i] : nullptr, nsteps, qr_period, energy_period, flags, comb, seed,
-                        counter[i], nullptr, s);
-    });
-  }));
+  try {   // the shared path's host arrays may fail to allocate
+    return from_cuda(group_run(g, [&] {
+      if (g->shared)
+        return group_block_shared(g, phi, weight, x, eloc_hist, weight_hist, logdet, nsteps, qr_period,
+                                  energy_period, flags, comb, seed, counter, st);
+      return fork_join(g, st, [&](int i, afqmc_kp* h, cudaStream_t s) {
+        return block_impl(h, phi[i], weight[i], x[i], eloc_hist[i], weight_hist ? weight_hist[i] : nullptr,
+                          logdet ? logdet[i] : nullptr, nsteps, qr_period, energy_period, flags, comb, seed,
+                          counter[i], nullptr, s);
+      });
+    }));
+  } catch (...) {
+    return AFQMC_ERR_OOM;
+  }
 }
 
 afqmc_status afqmc_kp_group_set_shared(afqmc_kp_group_t g, int shared) {
