@@ -841,6 +841,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the local-energy adjoint")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time one step of the FP64 path (N=1)")
     ap.add_argument("--windows", type=int, default=WINDOWS, help="timed windows of --steps steps (median)")
+    ap.add_argument("--taylor-form", choices=["auto", "single", "pair"], default="auto",
+                    help="the Taylor GEMM's tile form: the autotuner's choice, 128-row tiles, or CTA pairs")
     args = ap.parse_args()
     if args.workload == DENSE_WORKLOAD:
         if args.impl == "reference":
@@ -883,7 +885,10 @@ def main():
     if sys_ is None:
         precision = "fp64"
         sys_ = KPointAFQMC(spec.grid, L, h1, A, spec.nwalkers, spec.dt, precision="fp64")
-    # TMA ring depth per GEMM, picked at create by the library's autotuner (timed per launch)
+    # TMA ring depth per GEMM and the Taylor GEMM's form, picked at create by the library's
+    # autotuner (timed per launch); --taylor-form overrides the form
+    if precision == "mixed" and args.taylor_form != "auto":
+        sys_.set_gemm_form("taylor", args.taylor_form == "pair")
     autotune = sys_.gemm_tuning() if precision == "mixed" else None
 
     # walkers and fields: independent replicas per rank (disjoint walker indices); the walkers
